@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark: overdecomposed 3D 7-point FP64 Jacobi on GB300.
+
+Default workload: 512^3 interior (every cell U[0,1), seed 2), 4096 chares of
+32^3, persistent path, 100 timed iterations after warm-up.  A "step" is one
+Jacobi iteration over the whole grid (compute + face delivery for every
+chare).  The two parity buffers (2 x 2.3 GB) are far larger than the 129 MB
+L2, so no flush is needed between iterations.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores instead (the only reference this workload has).  Under
+torchrun each rank runs an independent replica on its own GPU (the solve has
+no cross-GPU exchange on a one-GPU-per-box pool: weak scaling, replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt updates/s & HBM GB/s vs ODF (fused vs per-chare); p50/p99 job latency"
+UNIT = "grid-pt updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--odf", type=int, default=4096)
+    ap.add_argument("--edge", type=int, default=512)
+    ap.add_argument("--path", default="persistent",
+                    choices=["per_chare", "fused", "graph", "persistent"])
+    ap.add_argument("--baseline-steps", type=int, default=3,
+                    help="timed steps of the per-chare-launch baseline at the same ODF (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time every path at ODF 1, 8, 64, 512, 4096 (adds a 'sweep' key)")
+    ap.add_argument("--tune", action="store_true", help="autotune the tiling at create")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--cpt", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--tile-z", type=int, default=0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms in a thread."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_cpu_baseline(edge: int, target_s: float = 12.0):
+    """Time the CPU oracle's monolithic sweep (its OpenMP z-plane split) on a
+    bounded sample of the same workload: the full edge^3 field, as many
+    iterations as fit in about target_s seconds."""
+    import oracle
+    from paper_2605_12734_gb300 import inputs
+    oracle.build()
+    threads = oracle.max_threads()
+    P = oracle.init_padded(edge, edge, edge, 2, inputs.INIT_UNIFORM)
+    t0 = time.perf_counter()
+    oracle.sweep(P, 1, threads)
+    one = time.perf_counter() - t0
+    iters = max(1, min(50, int(target_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.sweep(P, iters, threads)
+    dt = time.perf_counter() - t0
+    ups = edge ** 3 * iters / dt
+    return {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{edge}^3 field (U[0,1), seed 2), {iters} Jacobi iterations of the "
+                      f"undecomposed C oracle sweep on {threads} OpenMP threads ({dt:.1f} s)"}
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    edge = args.edge
+    import oracle
+    from paper_2605_12734_gb300 import inputs
+    oracle.build()
+    threads = oracle.max_threads()
+    P = oracle.init_padded(edge, edge, edge, 2, inputs.INIT_UNIFORM)
+    # each "step" is one oracle iteration over the full grid; a bounded
+    # number of them keeps the run to a few minutes
+    k = min(args.steps, 10)
+    w = min(args.warmup, 1)
+    if w:
+        P = oracle.sweep(P, w, threads)
+    t0 = time.perf_counter()
+    P = oracle.sweep(P, k, threads)
+    dt = time.perf_counter() - t0
+    ups = edge ** 3 * k / dt
+    line = {"impl": "reference", "metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": k, "warmup": w, "ms_per_step": dt * 1e3 / k, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"jacobi3d-{edge}^3-odf{args.odf}", "nx": edge, "ny": edge, "nz": edge,
+                       "odf": args.odf, "note": "CPU oracle (undecomposed sweep; same bits for any ODF)"},
+            "cpu_baseline": {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{edge}^3 field, {k} iterations on {threads} threads"},
+            "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- our arm
+
+def time_path(pkg, edge, odf, path, steps, warmup, stream, tune_kw):
+    """Device-resident timing of `steps` iterations; returns (ms/step, stats)."""
+    import torch
+    p = round(odf ** (1 / 3))
+    s = pkg.Jacobi3D(edge, edge, edge, split=(p, p, p), seed=2, init_mode=1, path=path,
+                     stream=stream.cuda_stream, **tune_kw)
+    try:
+        s.step(warmup)
+        s.sync()
+        st0 = s.stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        st1 = s.stats()
+    finally:
+        s.close()
+    return ms / steps, st0, st1
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2605_12734_gb300 as pkg
+    from paper_2605_12734_gb300 import build as od_build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    od_build.build()
+    dev = local
+    edge, odf = args.edge, args.odf
+    p = round(odf ** (1 / 3))
+    if p ** 3 != odf:
+        raise SystemExit("--odf must be a cube")
+    stream = torch.cuda.Stream(device=dev)
+    tune_kw = dict(threads=args.threads, cells_per_thread=args.cpt, stages=args.stages,
+                   tile_y=args.tile_y, tile_z=args.tile_z, autotune=args.tune, device=dev)
+
+    solver = pkg.Jacobi3D(edge, edge, edge, split=(p, p, p), seed=2, init_mode=1, path=args.path,
+                          stream=stream.cuda_stream, **tune_kw)
+    plan = solver.stats()["plan"]
+    solver.step(args.warmup)
+    solver.sync()
+    st0 = solver.stats()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st1 = solver.stats()
+    if world > 1:
+        t = torch.tensor([ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    updates_step = plan["cells"]
+    value = updates_step * world / (ms_step * 1e-3)
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
+
+    # roofline: the tile kernel does all of the step's HBM traffic
+    peak, peak_kind = measured_peaks()
+    bytes_step = plan["bytes_per_step"]
+    achieved = bytes_step / (ms_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "note": f"algorithmic bytes/step {bytes_step:.4g} (16 B/cell + 16 B per internal ghost "
+                        f"cell + 8 B per Dirichlet ghost cell); peak {peak_kind}"}
+
+    # end to end through the public API with pinned host buffers: each e2e
+    # step is a whole solve of the config's 100 iterations: write the initial
+    # field (H2D), iterate, read the result (D2H)
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        n = plan["cells"]
+        host_in = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        host_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        solver.read(host_in.numpy())       # a valid field to feed back in
+        iters_job = 100
+        reps = 2
+        solver.write(host_in.numpy())
+        solver.step(iters_job)
+        solver.read(host_out.numpy())      # warm-up job
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            solver.write(host_in.numpy())
+            solver.step(iters_job)
+            solver.read(host_out.numpy())
+        dt = time.perf_counter() - t0
+        e2e = {"value": n * iters_job * reps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
+               "iters_per_step": iters_job,
+               "note": "e2e step = od_write(pinned host field) + od_step(100) + od_read(pinned host)"}
+    solver.close()
+
+    baseline = None
+    if args.baseline_steps > 0 and rank == 0:
+        ms_b, b0, b1 = time_path(pkg, edge, odf, "per_chare", args.baseline_steps, 1, stream,
+                                 dict(device=dev))
+        baseline = {"path": "per_chare", "ms_per_step": ms_b, "value": updates_step / (ms_b * 1e-3),
+                    "steps": args.baseline_steps,
+                    "api_calls_per_step": (b1["api_calls"] - b0["api_calls"]) / args.baseline_steps,
+                    "kernels_per_step": (b1["kernel_launches"] - b0["kernel_launches"]) / args.baseline_steps}
+
+    sweep = None
+    if args.sweep and rank == 0:
+        sweep = []
+        for o in (1, 8, 64, 512, 4096):
+            for path in ("fused", "persistent", "graph", "per_chare"):
+                k = args.steps if path in ("fused", "persistent") else max(2, min(10, args.steps))
+                if path in ("graph", "per_chare") and o >= 4096:
+                    k = 2
+                ms_p, _, _ = time_path(pkg, edge, o, path, k, 2, stream, dict(device=dev))
+                info = pkg.plan(edge, edge, edge, split=(round(o ** (1 / 3)),) * 3)
+                sweep.append({"odf": o, "path": path, "ms_per_step": ms_p, "steps": k,
+                              "updates_per_s": info["cells"] / (ms_p * 1e-3),
+                              "eff_GBps": 16 * info["cells"] / (ms_p * 1e-3) / 1e9,
+                              "alg_GBps": info["bytes_per_step"] / (ms_p * 1e-3) / 1e9})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_cpu_baseline(edge)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"jacobi3d-{edge}^3-odf{odf}", "nx": edge, "ny": edge, "nz": edge,
+                           "odf": odf, "chare_edge": edge // p, "path": args.path, "seed": 2,
+                           "init": "U[0,1) everywhere, Dirichlet shell fixed",
+                           "l2": "no flush: 2 parity buffers of ~2.3 GB each exceed the 129 MB L2",
+                           "parallelism": f"replicas x{world}",
+                           "tiling": {k: plan[k] for k in ("threads", "cells_per_thread", "stages",
+                                                           "smem_bytes", "ntiles")}},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "eff_GBps": 16 * updates_step / (ms_step * 1e-3) / 1e9,
+                "per_chare_baseline": baseline}
+        if sweep is not None:
+            line["sweep"] = sweep
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

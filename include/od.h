@@ -1,0 +1,220 @@
+/*
+ * od.h -- C ABI of libod: an overdecomposed 3D 7-point FP64 Jacobi solver on
+ * one GPU (sm_103a).
+ *
+ * The method (the paper's Sec. III "Managing Overdecomposition" and Sec. V
+ * "jacobi2d"): the grid is cut into many more blocks ("chares") than there are
+ * GPUs; every Jacobi iteration each chare packs its boundary faces, delivers
+ * them to its neighbours (Sec. IV, intra-process transfer: device-to-device),
+ * the neighbours unpack them into their ghost layers, and each chare updates
+ * its block.  Iterations run a fixed count with no convergence check.  In this
+ * library all chares share one GPU; four execution paths run the same
+ * arithmetic:
+ *
+ *   OD_PATH_PER_CHARE   one stream per chare (pooled), pack kernel, one
+ *                       cudaMemcpyAsync D2D per face into the neighbour's
+ *                       receive slot, unpack kernel, compute kernel, events
+ *                       between neighbours (the runtime-level flow of Sec. III
+ *                       "non-blocking streams", transport of Sec. IV item 1);
+ *   OD_PATH_FUSED       one kernel per iteration over every (chare, tile);
+ *                       pack+deliver+unpack are fused into compute: each new
+ *                       boundary value is stored straight into the neighbour's
+ *                       ghost layer (its "mailbox"); the kernel boundary is the
+ *                       step barrier (kernel fusion, Sec. I, prior work);
+ *   OD_PATH_GRAPH       the per-chare flow for two iterations captured once as
+ *                       a CUDA graph and replayed (CUDA Graphs, Sec. I);
+ *   OD_PATH_PERSISTENT  one launch for all iterations: CTAs take (step, tile)
+ *                       tickets from a device queue and wait (bounded) on the
+ *                       per-tile step counters of the tiles they read.
+ *
+ * Arithmetic (every path, bit-identical to an undecomposed sweep):
+ *   u'[i,j,k] = (((((u[i-1]+u[i+1]) + u[j-1]) + u[j+1]) + u[k-1]) + u[k+1]) / 6.0
+ * in IEEE binary64 round-to-nearest, no FMA contraction, on the nx*ny*nz
+ * interior; a one-cell Dirichlet shell around it stays fixed.
+ *
+ * Initial field: the value of padded global cell L = gx + (nx+2)*(gy + (ny+2)*gz)
+ * (gx in [0,nx+1], ...) is the (L+1)-th output of a SplitMix64 stream seeded
+ * with `seed`, top 53 bits times 2^-53.  init_mode 0: interior 0, shell random;
+ * init_mode 1: every cell random.
+ *
+ * Conventions for every function:
+ *   - returns OD_OK or an error code; never aborts the process; the message of
+ *     the last error on the calling thread is od_last_error();
+ *   - device pointers are plain CUDA device addresses of the context's device;
+ *     host pointers are ordinary (pageable or pinned) host memory;
+ *   - the caller owns every buffer it passes; the library owns everything it
+ *     allocates and frees it in od_destroy;
+ *   - work is enqueued on the context's stream; od_read, od_sync and od_stats
+ *     synchronise that stream and report device-side errors (OD_ETIMEOUT for a
+ *     bounded wait that ran out, OD_ECUDA for a CUDA error).
+ */
+#ifndef OD_H
+#define OD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* every entry point is exported from libod.so (built with hidden default
+ * visibility) */
+#if defined(__GNUC__)
+#define OD_API __attribute__((visibility("default")))
+#else
+#define OD_API
+#endif
+
+typedef enum {
+    OD_OK = 0,
+    OD_EINVAL = 1,    /* bad argument or decomposition */
+    OD_ENOMEM = 2,    /* device or host allocation failed, or arena too small */
+    OD_ECUDA = 3,     /* a CUDA call or kernel failed */
+    OD_ETIMEOUT = 4,  /* a bounded device-side wait ran out (no hang) */
+    OD_EBUDGET = 5,   /* serving: job larger than the HBM budget */
+    OD_ESTATE = 6,    /* call not valid in the object's current state */
+    OD_ENOTFOUND = 7  /* serving: unknown job id */
+} od_status;
+
+typedef enum {
+    OD_PATH_PER_CHARE = 0,
+    OD_PATH_FUSED = 1,
+    OD_PATH_GRAPH = 2,
+    OD_PATH_PERSISTENT = 3
+} od_path;
+
+#define OD_INIT_ZERO_INTERIOR 0
+#define OD_INIT_UNIFORM 1
+
+/* Problem, decomposition and execution settings.  Fill with
+ * od_config_default() first, then set fields. */
+typedef struct od_config {
+    int64_t nx, ny, nz;          /* interior cells per axis, each >= 1 */
+    int32_t px, py, pz;          /* chares per axis for a balanced split: the
+                                    first n mod p blocks get ceil(n/p) cells,
+                                    the rest floor(n/p); ignored on an axis
+                                    whose cut list is given */
+    const int32_t *cuts_x;       /* optional explicit block edges per axis:   */
+    const int32_t *cuts_y;       /* ncuts+1 strictly ascending values from 0 */
+    const int32_t *cuts_z;       /* to n (host memory, read during the call) */
+    int32_t ncuts_x, ncuts_y, ncuts_z; /* blocks on that axis when cuts given */
+    uint64_t seed;               /* initial-field seed */
+    int32_t init_mode;           /* OD_INIT_ZERO_INTERIOR or OD_INIT_UNIFORM */
+    int32_t path;                /* od_path */
+    int32_t autotune;            /* 1: time candidate tilings at od_create and
+                                    keep the fastest (the field is initialised
+                                    after tuning, so results do not change) */
+    int32_t tile_y;              /* max rows per tile (0 = planner default) */
+    int32_t tile_z;              /* planes per tile (0 = planner default) */
+    int32_t threads;             /* threads per CTA: 128, 256 or 512 (0 = 256) */
+    int32_t cells_per_thread;    /* 1, 2, 4 or 8 (0 = planner default) */
+    int32_t stages;              /* TMA plane stages in flight, 3..8 (0 = 4) */
+    int32_t order;               /* persistent path task order: 0 linear every
+                                    step, 1 reversed on odd steps */
+    int32_t stream_pool;         /* per-chare path: streams (0 = min(nchares,32)) */
+    int32_t device;              /* CUDA device ordinal */
+    void *stream;                /* cudaStream_t to enqueue on; NULL = the
+                                    library creates a non-blocking stream */
+    void *arena;                 /* optional caller-owned device memory for all
+                                    chare state (size from od_plan); NULL = the
+                                    library allocates with cudaMalloc */
+    uint64_t arena_bytes;        /* size of `arena` in bytes */
+    uint64_t spin_limit_ns;      /* device-side wait limit (0 = 2 000 000 000) */
+} od_config;
+
+/* Host-only summary of a configuration's decomposition and memory. */
+typedef struct od_plan_info {
+    int64_t nchares;
+    int64_t ntiles;                /* compute tasks per iteration */
+    int64_t cells;                 /* interior cells (updates per iteration) */
+    int64_t face_cells_internal;   /* ghost cells fed by a neighbour, summed
+                                      over chares (each shared face twice) */
+    int64_t face_cells_dirichlet;  /* ghost cells on the domain shell */
+    uint64_t arena_bytes;          /* device bytes od_create needs */
+    double bytes_per_step;         /* algorithmic HBM bytes per iteration:
+                                      16*cells + 16*face_internal + 8*face_dirichlet */
+    int32_t tile_y, tile_z, threads, cells_per_thread, stages;
+    int32_t smem_bytes;            /* dynamic shared memory per CTA */
+} od_plan_info;
+
+typedef struct od_stats {
+    int64_t steps_done;            /* iterations completed so far */
+    int64_t kernel_launches;       /* kernels this context launched in od_step */
+    int64_t api_calls;             /* CUDA stream operations issued by od_step
+                                      (launches, copies, event records/waits,
+                                      graph launches) */
+    int64_t graph_launches;
+    int32_t path;
+    int32_t persistent_grid;       /* CTAs of the last persistent launch */
+    od_plan_info plan;
+} od_stats;
+
+typedef struct od_ctx od_ctx;
+
+/* Fill *cfg with defaults (a 1-chare 64^3 problem, fused path). */
+OD_API void od_config_default(od_config *cfg);
+
+/* Decompose and size a configuration without touching a GPU.  Errors:
+ * OD_EINVAL for an impossible decomposition (a block thinner than one cell,
+ * cut lists not ascending, more than 2^31 tiles). */
+OD_API od_status od_plan(const od_config *cfg, od_plan_info *out);
+
+/* Chare boxes of a configuration, host-only: for chare c (x fastest:
+ * c = cx + px*(cy + py*cz)) writes box[6c..6c+5] = x0,bx,y0,by,z0,bz and
+ * nbr[6c..6c+5] = neighbour chare on the x-,x+,y-,y+,z-,z+ side or -1 on the
+ * domain boundary.  `capacity` = chares the arrays hold. */
+OD_API od_status od_decompose(const od_config *cfg, int64_t *box, int32_t *nbr, int64_t capacity);
+
+/* Allocate device state on cfg->device, build the chare/tile tables, tune if
+ * asked, and write the initial field (u^0) including every ghost layer.
+ * Synchronous.  *out is NULL on error. */
+OD_API od_status od_create(od_ctx **out, const od_config *cfg);
+
+/* Enqueue `iters` >= 0 Jacobi iterations on the context's stream with its
+ * current path.  Asynchronous: returns once the work is enqueued.  No
+ * allocation and no host synchronisation happen inside (the graph path
+ * captures its graph on the first call). */
+OD_API od_status od_step(od_ctx *ctx, int32_t iters);
+
+/* Select the execution path for later od_step calls (any path continues the
+ * same iteration sequence). */
+OD_API od_status od_set_path(od_ctx *ctx, int32_t path);
+
+/* Wait for all enqueued work; reports device-side errors. */
+OD_API od_status od_sync(od_ctx *ctx);
+
+/* Copy the current field u^{steps_done} (interior only, x fastest,
+ * nx*ny*nz doubles) to dst.  dst_is_device != 0: dst is device memory of the
+ * context's device; otherwise host memory (a device staging buffer of
+ * nx*ny*nz doubles is allocated on the first host read or write and kept).
+ * Synchronises the stream. */
+OD_API od_status od_read(od_ctx *ctx, double *dst, int32_t dst_is_device);
+
+/* Replace the current field's interior with src (nx*ny*nz doubles, x fastest;
+ * device or host as for od_read) and refresh every internal ghost layer; the
+ * Dirichlet shell is kept.  Used to import a checkpoint or a user field.
+ * Enqueued on the stream (host sources are copied before return). */
+OD_API od_status od_write(od_ctx *ctx, const double *src, int32_t src_is_device);
+
+/* Counters and the plan; synchronises and reports device-side errors. */
+OD_API od_status od_stats_get(od_ctx *ctx, od_stats *out);
+
+/* Fault injection for tests: on the persistent path, tile `tile` never
+ * publishes its step counter, so the tiles that wait on it run into the wait
+ * limit and od_sync returns OD_ETIMEOUT.  -1 switches it off. */
+OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
+
+/* Free everything the context owns (synchronises first).  NULL is allowed. */
+OD_API od_status od_destroy(od_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+OD_API const char *od_last_error(void);
+
+/* Library version string. */
+OD_API const char *od_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OD_H */

@@ -1,0 +1,601 @@
+// od_api.cu -- the C ABI of libod (see include/od.h): context lifetime and
+// the four execution paths.
+//
+// No call below allocates device memory or synchronises the host inside
+// od_step: every buffer, stream and event is created in od_create (Sec. III
+// "Using Kokkos": persistent views, preallocated scratch, no implicit fences,
+// execution spaces created once), and every path only enqueues work.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "od.h"
+#include "od_internal.h"
+#include "od_kernels.h"
+#include "od_plan.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+od_status fail(od_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+od_status cuda_fail(cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(OD_ECUDA, m);
+}
+
+#define OD_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+constexpr uint64_t kDefaultSpinNs = 2000000000ull;
+
+}  // namespace
+
+struct od_ctx {
+    od_config cfg{};
+    od::Plan plan;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char *arena = nullptr;
+    bool own_arena = false;
+    ChareDev *d_ch = nullptr;
+    TileDev *d_tiles = nullptr;
+    ErrDev *d_err = nullptr;
+    int32_t *d_queue = nullptr, *d_epoch = nullptr, *d_dep_ptr = nullptr, *d_dep_idx = nullptr,
+            *d_order = nullptr;
+    std::vector<ChareDev> h_ch;       // host copy (device pointers)
+    double *d_stage = nullptr;        // lazily allocated host-transfer staging
+    int path = OD_PATH_FUSED;
+    int64_t steps = 0;
+    int64_t launches = 0, api_calls = 0, graph_launches = 0;
+    int persistent_grid = 0;
+    int64_t stall_tile = -1;
+    uint64_t spin_ns = kDefaultSpinNs;
+    bool failed = false;
+    // per-chare path
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> ev;      // ev[2*c + slot]: chare c delivered its faces
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    // graph path
+    cudaGraphExec_t g2 = nullptr, g1[2] = {nullptr, nullptr};
+    int64_t g2_kernels = 0, g1_kernels[2] = {0, 0};
+    int64_t g2_calls = 0, g1_calls[2] = {0, 0};
+};
+
+namespace {
+
+KArgs base_args(const od_ctx *c) {
+    KArgs a;
+    memset(&a, 0, sizeof a);
+    a.ch = c->d_ch;
+    a.tiles = c->d_tiles;
+    a.err = c->d_err;
+    a.queue = c->d_queue;
+    a.epoch = c->d_epoch;
+    a.dep_ptr = c->d_dep_ptr;
+    a.dep_idx = c->d_dep_idx;
+    a.order = c->d_order;
+    a.ntiles = (int32_t)c->plan.tiles.size();
+    a.order_mode = c->cfg.order;
+    a.stages = c->plan.stages;
+    a.stage_doubles = c->plan.stage_doubles;
+    a.stall_tile = c->stall_tile;
+    a.spin_ns = c->spin_ns;
+    return a;
+}
+
+// --- fused path: one kernel per step over all tiles
+od_status enqueue_fused(od_ctx *c, int32_t iters) {
+    const od::Plan &p = c->plan;
+    for (int32_t s = 0; s < iters; ++s) {
+        KArgs a = base_args(c);
+        a.tile_begin = 0;
+        a.parity = (int32_t)(c->steps & 1);
+        OD_CUDA(od::launch_tiles(a, (int)p.tiles.size(), p.threads, p.cpt, true, p.smem_bytes, c->stream));
+        c->steps++;
+        c->launches++;
+        c->api_calls++;
+    }
+    return OD_OK;
+}
+
+// --- persistent path: one launch for many steps
+od_status enqueue_persistent(od_ctx *c, int32_t iters) {
+    const od::Plan &p = c->plan;
+    const int64_t nt = (int64_t)p.tiles.size();
+    int bps = 0;
+    OD_CUDA(od::persistent_occupancy(p.threads, p.cpt, p.smem_bytes, &bps));
+    if (bps < 1) return fail(OD_EINVAL, "persistent kernel does not fit on an SM with this tiling");
+    int grid = (int)std::min<int64_t>(nt, (int64_t)bps * c->num_sms);
+    c->persistent_grid = grid;
+    // keep tickets inside int32
+    int32_t chunk_max = (int32_t)std::max<int64_t>(1, (INT32_MAX - 65536) / nt);
+    int32_t done = 0;
+    while (done < iters) {
+        int32_t n = std::min(iters - done, chunk_max);
+        OD_CUDA(cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), c->stream));
+        OD_CUDA(cudaMemsetAsync(c->d_epoch, 0, (size_t)nt * sizeof(int32_t), c->stream));
+        KArgs a = base_args(c);
+        a.iters = n;
+        a.t0 = (int32_t)(c->steps & 0x7fffffff);
+        OD_CUDA(od::launch_persistent(a, grid, p.threads, p.cpt, p.smem_bytes, c->stream));
+        c->steps += n;
+        c->launches++;
+        c->api_calls += 3;
+        done += n;
+    }
+    return OD_OK;
+}
+
+// --- per-chare path (also what the graph path captures)
+// Step t, chare c on stream pool[c % P]:
+//   phase A: compute (own tiles, no push) -> pack new faces -> one D2D copy per
+//            face into the neighbour's receive slot t&1 -> record ev[c][t&1]
+//   phase B: wait for each neighbour's ev[n][t&1] -> unpack into ghosts.
+// Receive slots alternate by step, so a sender at step t+2 overwrites slot
+// t&1 only after its own stream has waited (in phase B of step t+1) for the
+// receiver's step t+1 delivery, which its stream issued after the receiver's
+// step-t unpack.
+od_status enqueue_per_chare_steps(od_ctx *c, int64_t t_first, int32_t iters, int64_t *kernels,
+                                  int64_t *calls) {
+    const od::Plan &p = c->plan;
+    const int P = (int)c->pool.size();
+    const int nch = (int)p.ch.size();
+    OD_CUDA(cudaEventRecord(c->fork, c->stream));
+    (*calls)++;
+    for (int i = 0; i < P; ++i) {
+        OD_CUDA(cudaStreamWaitEvent(c->pool[i], c->fork, 0));
+        (*calls)++;
+    }
+    for (int32_t s = 0; s < iters; ++s) {
+        const int64_t t = t_first + s;
+        const int sp = (int)(t & 1), dp = sp ^ 1, slot = (int)(t & 1);
+        for (int ci = 0; ci < nch; ++ci) {
+            const od::HostChare &h = p.ch[(size_t)ci];
+            cudaStream_t st = c->pool[ci % P];
+            KArgs a = base_args(c);
+            a.tile_begin = h.tile_begin;
+            a.parity = sp;
+            OD_CUDA(od::launch_tiles(a, h.tile_end - h.tile_begin, p.threads, p.cpt, false, p.smem_bytes, st));
+            OD_CUDA(od::launch_pack(c->d_ch, ci, dp, h.foff[6], st));
+            (*kernels) += 2;
+            (*calls) += 2;
+            for (int f = 0; f < 6; ++f) {
+                const int n = h.nbr[f];
+                if (n < 0) continue;
+                const int opp = f ^ 1;
+                const ChareDev &dn = c->h_ch[(size_t)n];
+                const ChareDev &me = c->h_ch[(size_t)ci];
+                size_t bytes = (size_t)(h.foff[f + 1] - h.foff[f]) * sizeof(double);
+                OD_CUDA(cudaMemcpyAsync(dn.recv[slot] + dn.foff[opp], me.send + me.foff[f], bytes,
+                                        cudaMemcpyDeviceToDevice, st));
+                (*calls)++;
+            }
+            OD_CUDA(cudaEventRecord(c->ev[2 * (size_t)ci + slot], st));
+            (*calls)++;
+        }
+        for (int ci = 0; ci < nch; ++ci) {
+            const od::HostChare &h = p.ch[(size_t)ci];
+            cudaStream_t st = c->pool[ci % P];
+            bool any = false;
+            for (int f = 0; f < 6; ++f) {
+                const int n = h.nbr[f];
+                if (n < 0) continue;
+                any = true;
+                OD_CUDA(cudaStreamWaitEvent(st, c->ev[2 * (size_t)n + slot], 0));
+                (*calls)++;
+            }
+            if (any) {
+                OD_CUDA(od::launch_unpack(c->d_ch, ci, dp, slot, h.foff[6], st));
+                (*kernels)++;
+                (*calls)++;
+            }
+        }
+    }
+    for (int i = 0; i < P; ++i) {
+        OD_CUDA(cudaEventRecord(c->join[i], c->pool[i]));
+        OD_CUDA(cudaStreamWaitEvent(c->stream, c->join[i], 0));
+        (*calls) += 2;
+    }
+    return OD_OK;
+}
+
+od_status enqueue_per_chare(od_ctx *c, int32_t iters) {
+    int64_t k = 0, calls = 0;
+    od_status s = enqueue_per_chare_steps(c, c->steps, iters, &k, &calls);
+    c->launches += k;
+    c->api_calls += calls;
+    if (s == OD_OK) c->steps += iters;
+    return s;
+}
+
+od_status capture(od_ctx *c, int64_t t_first, int32_t iters, cudaGraphExec_t *out, int64_t *kernels,
+                  int64_t *calls) {
+    cudaGraph_t g = nullptr;
+    OD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    od_status s = enqueue_per_chare_steps(c, t_first, iters, kernels, calls);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (s != OD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return OD_OK;
+}
+
+od_status enqueue_graph(od_ctx *c, int32_t iters) {
+    if (iters <= 0) return OD_OK;
+    if (!c->g2) {
+        // captured once: two steps from an even step, and one step from each parity
+        od_status s = capture(c, 0, 2, &c->g2, &c->g2_kernels, &c->g2_calls);
+        if (s == OD_OK) s = capture(c, 0, 1, &c->g1[0], &c->g1_kernels[0], &c->g1_calls[0]);
+        if (s == OD_OK) s = capture(c, 1, 1, &c->g1[1], &c->g1_kernels[1], &c->g1_calls[1]);
+        if (s != OD_OK) return s;
+    }
+    int32_t left = iters;
+    if (c->steps & 1) {
+        OD_CUDA(cudaGraphLaunch(c->g1[1], c->stream));
+        c->launches += c->g1_kernels[1];
+        c->graph_launches++;
+        c->api_calls++;
+        c->steps++;
+        left--;
+    }
+    while (left >= 2) {
+        OD_CUDA(cudaGraphLaunch(c->g2, c->stream));
+        c->launches += c->g2_kernels;
+        c->graph_launches++;
+        c->api_calls++;
+        c->steps += 2;
+        left -= 2;
+    }
+    if (left == 1) {
+        OD_CUDA(cudaGraphLaunch(c->g1[0], c->stream));
+        c->launches += c->g1_kernels[0];
+        c->graph_launches++;
+        c->api_calls++;
+        c->steps++;
+    }
+    return OD_OK;
+}
+
+od_status check_device_error(od_ctx *c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->failed = true;
+        return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    ErrDev h;
+    e = cudaMemcpy(&h, c->d_err, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        c->failed = true;
+        return cuda_fail(e, "cudaMemcpy(error record)");
+    }
+    if (h.code != 0) {
+        c->failed = true;
+        char buf[200];
+        if (h.code == OD_ERR_TMA_TIMEOUT || h.code == OD_ERR_DEP_TIMEOUT) {
+            snprintf(buf, sizeof buf, "device wait ran out (%s) at tile %d, step %d",
+                     h.code == OD_ERR_TMA_TIMEOUT ? "bulk copy" : "neighbour step counter", h.tile, h.step);
+            return fail(OD_ETIMEOUT, buf);
+        }
+        snprintf(buf, sizeof buf, "kernel reported error %d", h.code);
+        return fail(OD_ECUDA, buf);
+    }
+    return OD_OK;
+}
+
+od_status ensure_stage(od_ctx *c) {
+    if (c->d_stage) return OD_OK;
+    size_t bytes = (size_t)c->plan.cells * sizeof(double);
+    cudaError_t e = cudaMalloc(&c->d_stage, bytes);
+    if (e != cudaSuccess) {
+        c->d_stage = nullptr;
+        cudaGetLastError();
+        return fail(OD_ENOMEM, "cannot allocate the host-transfer staging buffer");
+    }
+    return OD_OK;
+}
+
+void release(od_ctx *c) {
+    if (!c) return;
+    if (c->g2) cudaGraphExecDestroy(c->g2);
+    for (auto &g : c->g1)
+        if (g) cudaGraphExecDestroy(g);
+    for (auto e : c->ev) cudaEventDestroy(e);
+    for (auto e : c->join) cudaEventDestroy(e);
+    if (c->fork) cudaEventDestroy(c->fork);
+    for (auto s : c->pool) cudaStreamDestroy(s);
+    if (c->d_stage) cudaFree(c->d_stage);
+    if (c->own_arena && c->arena) cudaFree(c->arena);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *od_last_error(void) { return g_last_error.c_str(); }
+
+const char *od_version(void) { return "libod 0.1 (sm_103a)"; }
+
+void od_config_default(od_config *cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->nx = cfg->ny = cfg->nz = 64;
+    cfg->px = cfg->py = cfg->pz = 1;
+    cfg->seed = 1;
+    cfg->init_mode = OD_INIT_UNIFORM;
+    cfg->path = OD_PATH_FUSED;
+}
+
+od_status od_plan(const od_config *cfg, od_plan_info *out) {
+    if (!cfg || !out) return fail(OD_EINVAL, "null argument");
+    od::Plan p;
+    std::string err;
+    od_status s = od::build_plan(cfg, &p, &err);
+    if (s != OD_OK) return fail(s, err);
+    od::plan_info(p, out);
+    return OD_OK;
+}
+
+od_status od_decompose(const od_config *cfg, int64_t *box, int32_t *nbr, int64_t capacity) {
+    if (!cfg || !box || !nbr) return fail(OD_EINVAL, "null argument");
+    od::Plan p;
+    std::string err;
+    od_status s = od::build_plan(cfg, &p, &err);
+    if (s != OD_OK) return fail(s, err);
+    if ((int64_t)p.ch.size() > capacity) return fail(OD_EINVAL, "capacity smaller than the chare count");
+    for (size_t c = 0; c < p.ch.size(); ++c) {
+        const od::HostChare &h = p.ch[c];
+        int64_t *b = box + 6 * c;
+        b[0] = h.x0; b[1] = h.bx; b[2] = h.y0; b[3] = h.by; b[4] = h.z0; b[5] = h.bz;
+        for (int f = 0; f < 6; ++f) nbr[6 * c + f] = h.nbr[f];
+    }
+    return OD_OK;
+}
+
+od_status od_create(od_ctx **out, const od_config *cfg) {
+    if (!out || !cfg) return fail(OD_EINVAL, "null argument");
+    *out = nullptr;
+    od_ctx *c = new od_ctx();
+    c->cfg = *cfg;
+    c->cfg.cuts_x = c->cfg.cuts_y = c->cfg.cuts_z = nullptr;  // not kept past the call
+    std::string err;
+    od_status s = od::build_plan(cfg, &c->plan, &err);
+    if (s != OD_OK) {
+        release(c);
+        return fail(s, err);
+    }
+    od::Plan &p = c->plan;
+    c->device = cfg->device;
+    c->path = cfg->path;
+    c->spin_ns = cfg->spin_limit_ns ? cfg->spin_limit_ns : kDefaultSpinNs;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) {
+        release(c);
+        return fail(OD_ECUDA, "cannot select the CUDA device");
+    }
+#define OD_TRY(call)                                      \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) {                          \
+            od_status r_ = cuda_fail(e_, #call);          \
+            release(c);                                   \
+            return r_;                                    \
+        }                                                 \
+    } while (0)
+    OD_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (!od::tile_shape_supported(p.threads, p.cpt)) {
+        release(c);
+        return fail(OD_EINVAL, "unsupported threads / cells_per_thread");
+    }
+    if (cfg->stream) {
+        c->stream = (cudaStream_t)cfg->stream;
+    } else {
+        OD_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    if (cfg->arena) {
+        if (cfg->arena_bytes < p.arena_bytes || ((uintptr_t)cfg->arena & 255u)) {
+            release(c);
+            return fail(OD_ENOMEM, "caller arena too small or not 256-byte aligned (size it with od_plan)");
+        }
+        c->arena = (char *)cfg->arena;
+    } else {
+        cudaError_t e = cudaMalloc(&c->arena, p.arena_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->arena = nullptr;
+            release(c);
+            return fail(OD_ENOMEM, "cudaMalloc of the chare arena failed");
+        }
+        c->own_arena = true;
+    }
+    char *A = c->arena;
+    c->d_err = (ErrDev *)(A + p.off_err);
+    c->d_queue = (int32_t *)(A + p.off_queue);
+    c->d_epoch = (int32_t *)(A + p.off_epoch);
+    c->d_ch = (ChareDev *)(A + p.off_chares);
+    c->d_tiles = (TileDev *)(A + p.off_tiles);
+    c->d_dep_ptr = (int32_t *)(A + p.off_dep_ptr);
+    c->d_dep_idx = (int32_t *)(A + p.off_dep_idx);
+    c->d_order = (int32_t *)(A + p.off_order);
+    c->h_ch.resize(p.ch.size());
+    for (size_t i = 0; i < p.ch.size(); ++i) {
+        const od::HostChare &h = p.ch[i];
+        ChareDev &d = c->h_ch[i];
+        memset(&d, 0, sizeof d);
+        d.bx = h.bx; d.by = h.by; d.bz = h.bz; d.pitch = h.pitch; d.xgp = h.xgp;
+        for (int f = 0; f < 6; ++f) d.nbr[f] = h.nbr[f];
+        for (int f = 0; f < 7; ++f) d.foff[f] = h.foff[f];
+        d.x0 = h.x0; d.y0 = h.y0; d.z0 = h.z0;
+        for (int s2 = 0; s2 < 2; ++s2) {
+            d.A[s2] = (double *)(A + h.offA[s2]);
+            for (int sd = 0; sd < 2; ++sd) d.XG[s2][sd] = (double *)(A + h.offXG[s2][sd]);
+            d.recv[s2] = (double *)(A + h.offRecv[s2]);
+        }
+        d.send = (double *)(A + h.offSend);
+    }
+    OD_TRY(cudaMemsetAsync(A, 0, p.off_chares, c->stream));  // error record, queue, epochs
+    OD_TRY(cudaMemcpyAsync(c->d_ch, c->h_ch.data(), c->h_ch.size() * sizeof(ChareDev),
+                           cudaMemcpyHostToDevice, c->stream));
+    OD_TRY(cudaMemcpyAsync(c->d_tiles, p.tiles.data(), p.tiles.size() * sizeof(TileDev),
+                           cudaMemcpyHostToDevice, c->stream));
+    OD_TRY(cudaMemcpyAsync(c->d_dep_ptr, p.dep_ptr.data(), p.dep_ptr.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, c->stream));
+    if (!p.dep_idx.empty())
+        OD_TRY(cudaMemcpyAsync(c->d_dep_idx, p.dep_idx.data(), p.dep_idx.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, c->stream));
+    OD_TRY(cudaMemcpyAsync(c->d_order, p.order.data(), p.order.size() * sizeof(int32_t),
+                           cudaMemcpyHostToDevice, c->stream));
+    OD_TRY(od::prepare_tile_kernels(p.threads, p.cpt, p.smem_bytes));
+    // per-chare path resources
+    int P = cfg->stream_pool > 0 ? cfg->stream_pool : 32;
+    P = (int)std::min<int64_t>(P, (int64_t)p.ch.size());
+    c->pool.resize((size_t)P, nullptr);
+    c->join.resize((size_t)P, nullptr);
+    for (int i = 0; i < P; ++i) {
+        OD_TRY(cudaStreamCreateWithFlags(&c->pool[i], cudaStreamNonBlocking));
+        OD_TRY(cudaEventCreateWithFlags(&c->join[i], cudaEventDisableTiming));
+    }
+    OD_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
+    c->ev.resize(2 * p.ch.size(), nullptr);
+    for (auto &e : c->ev) OD_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    OD_TRY(od::launch_init(c->d_ch, (int)p.ch.size(), p.nx, p.ny, p.nz, cfg->seed, cfg->init_mode, c->stream));
+    OD_TRY(cudaStreamSynchronize(c->stream));
+#undef OD_TRY
+    *out = c;
+    return OD_OK;
+}
+
+od_status od_step(od_ctx *c, int32_t iters) {
+    if (!c) return fail(OD_EINVAL, "null context");
+    if (iters < 0) return fail(OD_EINVAL, "iters must be >= 0");
+    if (c->failed) return fail(OD_ESTATE, "context failed earlier; destroy it");
+    if (iters == 0) return OD_OK;
+    DeviceGuard dg(c->device);
+    switch (c->path) {
+        case OD_PATH_FUSED: return enqueue_fused(c, iters);
+        case OD_PATH_PERSISTENT: return enqueue_persistent(c, iters);
+        case OD_PATH_PER_CHARE: return enqueue_per_chare(c, iters);
+        case OD_PATH_GRAPH: return enqueue_graph(c, iters);
+        default: return fail(OD_EINVAL, "unknown path");
+    }
+}
+
+od_status od_set_path(od_ctx *c, int32_t path) {
+    if (!c) return fail(OD_EINVAL, "null context");
+    if (path < OD_PATH_PER_CHARE || path > OD_PATH_PERSISTENT) return fail(OD_EINVAL, "unknown path");
+    c->path = path;
+    return OD_OK;
+}
+
+od_status od_sync(od_ctx *c) {
+    if (!c) return fail(OD_EINVAL, "null context");
+    DeviceGuard dg(c->device);
+    return check_device_error(c);
+}
+
+od_status od_read(od_ctx *c, double *dst, int32_t dst_is_device) {
+    if (!c || !dst) return fail(OD_EINVAL, "null argument");
+    DeviceGuard dg(c->device);
+    od_status s = check_device_error(c);
+    if (s != OD_OK) return s;
+    const od::Plan &p = c->plan;
+    const int par = (int)(c->steps & 1);
+    if (dst_is_device) {
+        OD_CUDA(od::launch_gather(c->d_ch, (int)p.ch.size(), par, p.nx, p.ny, dst, c->stream));
+    } else {
+        s = ensure_stage(c);
+        if (s != OD_OK) return s;
+        OD_CUDA(od::launch_gather(c->d_ch, (int)p.ch.size(), par, p.nx, p.ny, c->d_stage, c->stream));
+        OD_CUDA(cudaMemcpyAsync(dst, c->d_stage, (size_t)p.cells * sizeof(double), cudaMemcpyDeviceToHost,
+                                c->stream));
+    }
+    OD_CUDA(cudaStreamSynchronize(c->stream));
+    return OD_OK;
+}
+
+od_status od_write(od_ctx *c, const double *src, int32_t src_is_device) {
+    if (!c || !src) return fail(OD_EINVAL, "null argument");
+    if (c->failed) return fail(OD_ESTATE, "context failed earlier; destroy it");
+    DeviceGuard dg(c->device);
+    const od::Plan &p = c->plan;
+    const int par = (int)(c->steps & 1);
+    const double *g = src;
+    if (!src_is_device) {
+        od_status s = ensure_stage(c);
+        if (s != OD_OK) return s;
+        OD_CUDA(cudaMemcpyAsync(c->d_stage, src, (size_t)p.cells * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream));
+        g = c->d_stage;
+    }
+    OD_CUDA(od::launch_scatter(c->d_ch, (int)p.ch.size(), par, p.nx, p.ny, p.nz, g, c->stream));
+    if (!src_is_device) OD_CUDA(cudaStreamSynchronize(c->stream));
+    return OD_OK;
+}
+
+od_status od_stats_get(od_ctx *c, od_stats *out) {
+    if (!c || !out) return fail(OD_EINVAL, "null argument");
+    DeviceGuard dg(c->device);
+    memset(out, 0, sizeof *out);
+    od_status s = check_device_error(c);
+    out->steps_done = c->steps;
+    out->kernel_launches = c->launches;
+    out->api_calls = c->api_calls;
+    out->graph_launches = c->graph_launches;
+    out->path = c->path;
+    out->persistent_grid = c->persistent_grid;
+    od::plan_info(c->plan, &out->plan);
+    return s;
+}
+
+od_status od_debug_stall_tile(od_ctx *c, int64_t tile) {
+    if (!c) return fail(OD_EINVAL, "null context");
+    if (tile < -1 || tile >= (int64_t)c->plan.tiles.size()) return fail(OD_EINVAL, "tile out of range");
+    c->stall_tile = tile;
+    return OD_OK;
+}
+
+od_status od_destroy(od_ctx *c) {
+    if (!c) return OD_OK;
+    {
+        DeviceGuard dg(c->device);
+        cudaStreamSynchronize(c->stream);
+        release(c);
+    }
+    return OD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// od_internal.h -- structures shared by the host planner and the CUDA kernels
+// of libod (overdecomposed 3D 7-point FP64 Jacobi on one GPU).
+//
+// Memory layout of one chare (block) in HBM, per parity p in {0,1}:
+//   A[p]   : (bz+2) planes x (by+2) rows x pitch doubles, pitch = bx rounded
+//            up to 4 (rows start 32-byte aligned).  Plane 0 / bz+1 are the
+//            z-ghost planes, row 0 / by+1 of every plane the y-ghost rows,
+//            columns [0,bx) the cells; columns [bx,pitch) are padding.
+//            Interior cell (i,j,k) is A[p][((k+1)*(by+2) + (j+1))*pitch + i].
+//   XG[p][s]: x-ghost columns kept apart (s=0: left of i=0, s=1: right of
+//            i=bx-1) as bz rows of xgp doubles, xgp = by rounded up to 2;
+//            ghost of row j, plane k at XG[p][s][k*xgp + j].
+// Keeping x-ghosts out of the rows lets a whole tile of rows (with its y-halo
+// rows) be one contiguous run, fetched by a single 1D bulk copy (TMA), and
+// keeps interior rows aligned.  Edge and corner ghost cells of the padded box
+// exist in A but are never read by a 7-point stencil.
+//
+// A neighbour "delivers" a face by storing straight into these ghost cells
+// (the chare's mailbox).  Faces on the domain boundary hold the Dirichlet
+// shell in both parities and are never written after initialisation.
+#pragma once
+#include <stdint.h>
+
+#define OD_FACE_XLO 0
+#define OD_FACE_XHI 1
+#define OD_FACE_YLO 2
+#define OD_FACE_YHI 3
+#define OD_FACE_ZLO 4
+#define OD_FACE_ZHI 5
+
+#define OD_ERR_TMA_TIMEOUT 1    // a bulk-copy wait ran out
+#define OD_ERR_DEP_TIMEOUT 2    // a dependency (step counter) wait ran out
+#define OD_ERR_BAD_LAUNCH 3     // kernel saw an inconsistent launch shape
+
+// One chare as the kernels see it (device table, one entry per chare).
+struct ChareDev {
+    int32_t bx, by, bz;     // interior extents
+    int32_t pitch;          // row stride of A, doubles
+    int32_t xgp;            // row stride of XG, doubles
+    int32_t nbr[6];         // neighbour per face or -1 (Dirichlet)
+    int32_t foff[7];        // face offsets inside send/recv buffers (doubles)
+    int64_t x0, y0, z0;     // global interior offset of cell (0,0,0)
+    double *A[2];
+    double *XG[2][2];       // [parity][side]
+    double *send;           // per-chare path: packed new faces
+    double *recv[2];        // per-chare path: faces from neighbours, 2 slots
+};
+
+// One compute task: rows [j0,j0+nj) x planes [k0,k0+nk) of chare c, all bx
+// columns.
+struct TileDev {
+    int32_t c, j0, nj, k0, nk;
+    int32_t pad[3];
+};
+
+// Error record written by kernels (first error wins).
+struct ErrDev {
+    int32_t code;
+    int32_t tile;
+    int32_t step;
+    int32_t pad[13];
+};
+
+// Arguments of the tile kernels (passed by value).
+struct KArgs {
+    const ChareDev *ch;
+    const TileDev *tiles;
+    ErrDev *err;
+    int32_t *queue;          // persistent: ticket counter (zeroed per launch)
+    int32_t *epoch;          // persistent: steps finished per tile in this launch
+    const int32_t *dep_ptr;  // persistent: CSR of the tiles each tile reads
+    const int32_t *dep_idx;
+    const int32_t *order;    // persistent: tile of each queue position
+    int32_t tile_begin;      // static launch: tile of blockIdx.x == 0
+    int32_t ntiles;          // tiles per step
+    int32_t parity;          // static launch: parity of the source buffer
+    int32_t iters;           // persistent: steps in this launch
+    int32_t t0;              // persistent: absolute step of the first one
+    int32_t order_mode;      // persistent: 1 = reverse order on odd steps
+    int32_t stages;          // TMA ring depth
+    int32_t stage_doubles;   // doubles per ring slot
+    int64_t stall_tile;      // fault injection (-1 = off)
+    uint64_t spin_ns;        // bound on every device-side wait
+};

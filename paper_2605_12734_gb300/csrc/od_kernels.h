@@ -1,0 +1,36 @@
+// od_kernels.h -- launch wrappers for libod's device kernels (host side).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "od_internal.h"
+
+namespace od {
+
+// Tile kernels are instantiated for threads in {128,256,512} and cells per
+// thread in {1,2,4,8}.
+bool tile_shape_supported(int threads, int cpt);
+
+// Raise the dynamic shared-memory limit of the tile kernels of one shape.
+cudaError_t prepare_tile_kernels(int threads, int cpt, int smem_bytes);
+
+// One CTA per tile, tiles [a.tile_begin, a.tile_begin + grid).  push = 1 also
+// stores each new boundary value into the neighbour's ghost layer.
+cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, bool push, int smem_bytes,
+                         cudaStream_t s);
+
+// Persistent ticket kernel over a.iters steps.
+cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, int smem_bytes,
+                              cudaStream_t s);
+cudaError_t persistent_occupancy(int threads, int cpt, int smem_bytes, int *blocks_per_sm);
+
+cudaError_t launch_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
+                        int mode, cudaStream_t s);
+cudaError_t launch_pack(const ChareDev *ch, int c, int parity, int elems, cudaStream_t s);
+cudaError_t launch_unpack(const ChareDev *ch, int c, int parity, int slot, int elems, cudaStream_t s);
+cudaError_t launch_gather(const ChareDev *ch, int nch, int parity, int64_t nx, int64_t ny, double *g,
+                          cudaStream_t s);
+cudaError_t launch_scatter(const ChareDev *ch, int nch, int parity, int64_t nx, int64_t ny, int64_t nz,
+                           const double *g, cudaStream_t s);
+
+}  // namespace od

@@ -1,0 +1,309 @@
+// od_plan.cpp -- decomposition, tiling, dependency lists and arena layout.
+//
+// Decompose (A1 of the hot path): the paper's runtime pre-fills a location
+// table so that a sender knows where each destination chare lives (Sec. IV);
+// here every chare lives on the same GPU, so the "location table" is a static
+// neighbour table plus the device addresses of each neighbour's ghost layers,
+// built once here and copied to the device by od_create.
+#include "od_plan.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+namespace od {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int32_t kMaxSmem = 232448;  // 227 KB opt-in per CTA on sm_100/sm_103
+constexpr int32_t kSmemHeader = 128;  // mbarriers + ticket slot
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+int32_t round_up(int32_t v, int32_t a) { return (v + a - 1) / a * a; }
+
+bool edges_from(int64_t n, int32_t p, const int32_t *cuts, int32_t ncuts, const char *axis,
+                std::vector<int64_t> *e, std::string *err) {
+    e->clear();
+    if (cuts) {
+        if (ncuts < 1) {
+            *err = std::string("cut list on axis ") + axis + " needs at least one block";
+            return false;
+        }
+        for (int32_t b = 0; b <= ncuts; ++b) e->push_back(cuts[b]);
+        if ((*e)[0] != 0 || (*e)[ncuts] != n) {
+            *err = std::string("cut list on axis ") + axis + " must start at 0 and end at n";
+            return false;
+        }
+        for (int32_t b = 0; b < ncuts; ++b)
+            if ((*e)[b + 1] <= (*e)[b]) {
+                *err = std::string("cut list on axis ") + axis + " must be strictly ascending";
+                return false;
+            }
+        return true;
+    }
+    if (p < 1 || p > n) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "cannot split %lld cells on axis %s into %d blocks",
+                 (long long)n, axis, p);
+        *err = buf;
+        return false;
+    }
+    // balanced split: the first n mod p blocks are one cell longer
+    int64_t q = n / p, r = n % p, at = 0;
+    e->push_back(0);
+    for (int32_t b = 0; b < p; ++b) {
+        at += q + (b < r ? 1 : 0);
+        e->push_back(at);
+    }
+    return true;
+}
+
+struct Box {
+    int64_t lo[3], hi[3];
+};
+
+Box tile_box(const HostChare &c, const TileDev &t) {
+    Box b;
+    b.lo[0] = c.x0;           b.hi[0] = c.x0 + c.bx;
+    b.lo[1] = c.y0 + t.j0;    b.hi[1] = b.lo[1] + t.nj;
+    b.lo[2] = c.z0 + t.k0;    b.hi[2] = b.lo[2] + t.nk;
+    return b;
+}
+
+// Tiles whose cells a 7-point update of `a` reads, or that read `a`'s cells:
+// the same tile, or boxes that touch along one axis and overlap on the other
+// two.
+bool adjacent_or_same(const Box &a, const Box &b) {
+    int overlap = 0, touch = 0;
+    for (int d = 0; d < 3; ++d) {
+        if (a.lo[d] < b.hi[d] && b.lo[d] < a.hi[d]) ++overlap;
+        else if (a.hi[d] == b.lo[d] || b.hi[d] == a.lo[d]) ++touch;
+    }
+    return overlap == 3 || (overlap == 2 && touch == 1);
+}
+
+// split n into parts of at most `cap`, balanced
+void balanced_parts(int32_t n, int32_t cap, std::vector<int32_t> *starts, std::vector<int32_t> *lens) {
+    int32_t parts = (n + cap - 1) / cap;
+    int32_t q = n / parts, r = n % parts, at = 0;
+    starts->clear();
+    lens->clear();
+    for (int32_t b = 0; b < parts; ++b) {
+        int32_t l = q + (b < r ? 1 : 0);
+        starts->push_back(at);
+        lens->push_back(l);
+        at += l;
+    }
+}
+
+}  // namespace
+
+int32_t stage_doubles_for(int32_t nj, int32_t pitch) {
+    int32_t rows = (nj + 2) * pitch;           // tile rows + the two y-halo rows
+    int32_t xg = round_up(nj + 2, 2);          // one x-ghost slot (16-byte aligned span)
+    return round_up(rows + 2 * xg, 16);        // keep stages 128-byte aligned
+}
+
+od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
+    Plan &p = *P;
+    p = Plan();
+    if (!cfg) { *err = "null config"; return OD_EINVAL; }
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1 || cfg->nx > (1 << 30) || cfg->ny > (1 << 30) ||
+        cfg->nz > (1 << 30)) {
+        *err = "grid extents must be in [1, 2^30]";
+        return OD_EINVAL;
+    }
+    if (cfg->init_mode != OD_INIT_ZERO_INTERIOR && cfg->init_mode != OD_INIT_UNIFORM) {
+        *err = "init_mode must be 0 or 1";
+        return OD_EINVAL;
+    }
+    if (cfg->path < OD_PATH_PER_CHARE || cfg->path > OD_PATH_PERSISTENT) {
+        *err = "unknown path";
+        return OD_EINVAL;
+    }
+    p.threads = cfg->threads ? cfg->threads : 256;
+    p.cpt = cfg->cells_per_thread ? cfg->cells_per_thread : 4;
+    p.stages = cfg->stages ? cfg->stages : 4;
+    p.tile_y = cfg->tile_y;
+    p.tile_z = cfg->tile_z;
+    if (p.threads != 128 && p.threads != 256 && p.threads != 512) {
+        *err = "threads must be 128, 256 or 512";
+        return OD_EINVAL;
+    }
+    if (p.cpt != 1 && p.cpt != 2 && p.cpt != 4 && p.cpt != 8) {
+        *err = "cells_per_thread must be 1, 2, 4 or 8";
+        return OD_EINVAL;
+    }
+    if (p.stages < 2 || p.stages > 8) {
+        *err = "stages must be in [2, 8]";
+        return OD_EINVAL;
+    }
+    if (p.tile_y < 0 || p.tile_z < 0) {
+        *err = "tile sizes must be >= 0";
+        return OD_EINVAL;
+    }
+    p.nx = cfg->nx; p.ny = cfg->ny; p.nz = cfg->nz;
+    if (!edges_from(cfg->nx, cfg->px, cfg->cuts_x, cfg->ncuts_x, "x", &p.ex, err) ||
+        !edges_from(cfg->ny, cfg->py, cfg->cuts_y, cfg->ncuts_y, "y", &p.ey, err) ||
+        !edges_from(cfg->nz, cfg->pz, cfg->cuts_z, cfg->ncuts_z, "z", &p.ez, err))
+        return OD_EINVAL;
+    p.px = (int32_t)p.ex.size() - 1;
+    p.py = (int32_t)p.ey.size() - 1;
+    p.pz = (int32_t)p.ez.size() - 1;
+    int64_t nch = (int64_t)p.px * p.py * p.pz;
+    if (nch > (1ll << 24)) {
+        *err = "more than 2^24 chares";
+        return OD_EINVAL;
+    }
+    for (int64_t e = 1; e < (int64_t)p.ex.size(); ++e)
+        if (p.ex[e] - p.ex[e - 1] > (int64_t)p.threads * p.cpt) {
+            char buf[200];
+            snprintf(buf, sizeof buf,
+                     "block row of %lld cells exceeds threads*cells_per_thread = %d; "
+                     "use more chares along x or a larger CTA",
+                     (long long)(p.ex[e] - p.ex[e - 1]), p.threads * p.cpt);
+            *err = buf;
+            return OD_EINVAL;
+        }
+
+    // chares, x fastest
+    p.ch.resize((size_t)nch);
+    for (int32_t cz = 0; cz < p.pz; ++cz)
+        for (int32_t cy = 0; cy < p.py; ++cy)
+            for (int32_t cx = 0; cx < p.px; ++cx) {
+                int64_t c = cx + (int64_t)p.px * (cy + (int64_t)p.py * cz);
+                HostChare &h = p.ch[(size_t)c];
+                h.cx = cx; h.cy = cy; h.cz = cz;
+                h.x0 = p.ex[cx]; h.bx = (int32_t)(p.ex[cx + 1] - p.ex[cx]);
+                h.y0 = p.ey[cy]; h.by = (int32_t)(p.ey[cy + 1] - p.ey[cy]);
+                h.z0 = p.ez[cz]; h.bz = (int32_t)(p.ez[cz + 1] - p.ez[cz]);
+                h.pitch = round_up(h.bx, 4);
+                h.xgp = round_up(h.by, 2);
+                h.nbr[OD_FACE_XLO] = cx > 0 ? (int32_t)(c - 1) : -1;
+                h.nbr[OD_FACE_XHI] = cx < p.px - 1 ? (int32_t)(c + 1) : -1;
+                h.nbr[OD_FACE_YLO] = cy > 0 ? (int32_t)(c - p.px) : -1;
+                h.nbr[OD_FACE_YHI] = cy < p.py - 1 ? (int32_t)(c + p.px) : -1;
+                h.nbr[OD_FACE_ZLO] = cz > 0 ? (int32_t)(c - (int64_t)p.px * p.py) : -1;
+                h.nbr[OD_FACE_ZHI] = cz < p.pz - 1 ? (int32_t)(c + (int64_t)p.px * p.py) : -1;
+                int32_t fs[6] = {h.by * h.bz, h.by * h.bz, h.bx * h.bz, h.bx * h.bz, h.bx * h.by, h.bx * h.by};
+                h.foff[0] = 0;
+                for (int f = 0; f < 6; ++f) h.foff[f + 1] = h.foff[f] + fs[f];
+                for (int f = 0; f < 6; ++f) {
+                    if (h.nbr[f] >= 0) p.face_internal += fs[f];
+                    else p.face_dirichlet += fs[f];
+                }
+            }
+    p.cells = cfg->nx * cfg->ny * cfg->nz;
+    p.bytes_per_step = 16.0 * (double)p.cells + 16.0 * (double)p.face_internal +
+                       8.0 * (double)p.face_dirichlet;
+
+    // tiles: full rows, balanced row slabs and plane chunks
+    std::vector<int32_t> js, jl, ks, kl;
+    int32_t max_stage = 0;
+    for (size_t c = 0; c < p.ch.size(); ++c) {
+        HostChare &h = p.ch[c];
+        int32_t nj_cap = (p.threads * p.cpt) / h.bx;
+        if (p.tile_y > 0) nj_cap = std::min(nj_cap, p.tile_y);
+        nj_cap = std::max(1, std::min(nj_cap, h.by));
+        int32_t tz = p.tile_z > 0 ? p.tile_z : 32;
+        tz = std::min(tz, h.bz);
+        balanced_parts(h.by, nj_cap, &js, &jl);
+        balanced_parts(h.bz, tz, &ks, &kl);
+        h.tile_begin = (int32_t)p.tiles.size();
+        for (size_t a = 0; a < ks.size(); ++a)
+            for (size_t b = 0; b < js.size(); ++b) {
+                TileDev t;
+                memset(&t, 0, sizeof t);
+                t.c = (int32_t)c;
+                t.j0 = js[b]; t.nj = jl[b];
+                t.k0 = ks[a]; t.nk = kl[a];
+                p.tiles.push_back(t);
+                max_stage = std::max(max_stage, stage_doubles_for(t.nj, h.pitch));
+                if (p.tiles.size() > (size_t)0x7fffffff) {
+                    *err = "too many tiles";
+                    return OD_EINVAL;
+                }
+            }
+        h.tile_end = (int32_t)p.tiles.size();
+    }
+    p.stage_doubles = max_stage;
+    int64_t smem = kSmemHeader + (int64_t)p.stages * p.stage_doubles * 8;
+    if (smem > kMaxSmem) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "tile needs %lld bytes of shared memory (> %d); lower tile_y, "
+                 "cells_per_thread or stages",
+                 (long long)smem, kMaxSmem);
+        *err = buf;
+        return OD_EINVAL;
+    }
+    p.smem_bytes = (int32_t)smem;
+
+    // dependency lists (tiles of the chare itself and its six neighbours)
+    p.dep_ptr.assign(p.tiles.size() + 1, 0);
+    p.dep_idx.clear();
+    for (size_t ti = 0; ti < p.tiles.size(); ++ti) {
+        const TileDev &t = p.tiles[ti];
+        const HostChare &h = p.ch[(size_t)t.c];
+        Box a = tile_box(h, t);
+        int32_t cand[7] = {t.c, h.nbr[0], h.nbr[1], h.nbr[2], h.nbr[3], h.nbr[4], h.nbr[5]};
+        for (int q = 0; q < 7; ++q) {
+            if (cand[q] < 0) continue;
+            const HostChare &g = p.ch[(size_t)cand[q]];
+            for (int32_t u = g.tile_begin; u < g.tile_end; ++u)
+                if (adjacent_or_same(a, tile_box(g, p.tiles[(size_t)u]))) p.dep_idx.push_back(u);
+        }
+        p.dep_ptr[ti + 1] = (int32_t)p.dep_idx.size();
+    }
+    p.order.resize(p.tiles.size());
+    for (size_t ti = 0; ti < p.tiles.size(); ++ti) p.order[ti] = (int32_t)ti;
+
+    // arena layout
+    size_t at = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = at;
+        at = align_up(at + bytes, kAlign);
+        return o;
+    };
+    p.off_err = take(sizeof(ErrDev));
+    p.off_queue = take(64);
+    p.off_epoch = take(p.tiles.size() * sizeof(int32_t));
+    p.off_chares = take(p.ch.size() * sizeof(ChareDev));
+    p.off_tiles = take(p.tiles.size() * sizeof(TileDev));
+    p.off_dep_ptr = take(p.dep_ptr.size() * sizeof(int32_t));
+    p.off_dep_idx = take(std::max<size_t>(1, p.dep_idx.size()) * sizeof(int32_t));
+    p.off_order = take(p.order.size() * sizeof(int32_t));
+    for (auto &h : p.ch) {
+        size_t a_bytes = (size_t)(h.bz + 2) * (size_t)(h.by + 2) * (size_t)h.pitch * 8;
+        size_t xg_bytes = (size_t)h.bz * (size_t)h.xgp * 8;
+        size_t f_bytes = (size_t)h.foff[6] * 8;
+        for (int s = 0; s < 2; ++s) h.offA[s] = take(a_bytes);
+        for (int s = 0; s < 2; ++s)
+            for (int d = 0; d < 2; ++d) h.offXG[s][d] = take(xg_bytes);
+        h.offSend = take(f_bytes);
+        h.offRecv[0] = take(f_bytes);
+        h.offRecv[1] = take(f_bytes);
+    }
+    p.arena_bytes = at;
+    return OD_OK;
+}
+
+void plan_info(const Plan &p, od_plan_info *o) {
+    memset(o, 0, sizeof *o);
+    o->nchares = (int64_t)p.ch.size();
+    o->ntiles = (int64_t)p.tiles.size();
+    o->cells = p.cells;
+    o->face_cells_internal = p.face_internal;
+    o->face_cells_dirichlet = p.face_dirichlet;
+    o->arena_bytes = p.arena_bytes;
+    o->bytes_per_step = p.bytes_per_step;
+    o->tile_y = p.tile_y;
+    o->tile_z = p.tile_z;
+    o->threads = p.threads;
+    o->cells_per_thread = p.cpt;
+    o->stages = p.stages;
+    o->smem_bytes = p.smem_bytes;
+}
+
+}  // namespace od

@@ -1,0 +1,201 @@
+"""GPU parity: every execution path of libod against the CPU oracle, bit for
+bit (the method promises the undecomposed answer for any decomposition).
+
+Small cases run the oracle's full sweep; full-size workloads (512^3 at ODF 1
+and 4096, the uneven 768x512x512 grid, 1024^3 at ODF 4096) are checked on
+sampled cells that the oracle computes one by one on their dependency cone,
+plus the discrete maximum principle on every cell."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_12734_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PATHS = ["per_chare", "fused", "graph", "persistent"]
+
+
+@pytest.fixture(scope="module")
+def od():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_12734_gb300 import build
+    build.build()
+    import paper_2605_12734_gb300 as pkg
+    return pkg
+
+
+def bits(a):
+    return np.ascontiguousarray(a).view(np.uint64)
+
+
+def assert_bitexact(got, want, what=""):
+    g, w = bits(got), bits(want)
+    if not np.array_equal(g, w):
+        bad = np.flatnonzero(g != w)
+        i = int(bad[0])
+        raise AssertionError(f"{what}: {bad.size} cells differ; first at {i}: "
+                             f"got {got[i]!r} want {want[i]!r}")
+
+
+CASES = {
+    # name: (nx, ny, nz, decomposition kwargs, seed, init_mode, iters)
+    "cfg1_64_2x2x2": (64, 64, 64, dict(split=(2, 2, 2)), 1, 0, 10),
+    "odf1_ragged": (40, 36, 33, dict(split=(1, 1, 1)), 5, 1, 7),
+    "uneven_cuts": (70, 45, 38, dict(cuts=([0, 13, 40, 70], [0, 24, 45], [0, 5, 6, 38])), 8, 1, 9),
+    "one_wide": (6, 5, 7, dict(cuts=([0, 1, 2, 3, 4, 5, 6], [0, 1, 5], [0, 3, 4, 7])), 11, 1, 6),
+    "small_tiles": (64, 48, 40, dict(split=(2, 3, 2), tile_y=5, tile_z=7), 3, 1, 8),
+    "balanced_odd": (50, 31, 29, dict(split=(3, 3, 2)), 21, 0, 11),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("path", PATHS)
+def test_path_matches_oracle(od, path, case):
+    nx, ny, nz, dec, seed, mode, iters = CASES[case]
+    want = oracle.solve(nx, ny, nz, seed, mode, iters)
+    with od.Jacobi3D(nx, ny, nz, seed=seed, init_mode=mode, path=path, **dec) as s:
+        first = iters // 3
+        s.step(first)            # two calls: the step count carries over
+        s.step(iters - first)
+        got = s.read()
+        st = s.stats()
+    assert st["steps_done"] == iters
+    assert st["kernel_launches"] >= 1
+    assert_bitexact(got, want, f"{path}/{case}")
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_zero_iterations_is_initial_field(od, path):
+    nx, ny, nz = 33, 20, 17
+    want = oracle.solve(nx, ny, nz, 4, 1, 0)
+    with od.Jacobi3D(nx, ny, nz, split=(2, 2, 3), seed=4, init_mode=1, path=path) as s:
+        s.step(0)
+        assert_bitexact(s.read(), want, "iters=0")
+
+
+def test_switching_paths_mid_run(od):
+    nx, ny, nz = 48, 40, 36
+    want = oracle.solve(nx, ny, nz, 9, 1, 13)
+    with od.Jacobi3D(nx, ny, nz, split=(2, 2, 3), seed=9, init_mode=1, path="fused") as s:
+        for path, n in [("fused", 3), ("per_chare", 2), ("persistent", 4), ("graph", 3), ("fused", 1)]:
+            s.set_path(path)
+            s.step(n)
+        assert_bitexact(s.read(), want, "mixed paths")
+
+
+def test_checkpoint_restore(od):
+    nx, ny, nz = 40, 36, 30
+    want = oracle.solve(nx, ny, nz, 12, 1, 10)
+    with od.Jacobi3D(nx, ny, nz, split=(2, 3, 2), seed=12, init_mode=1, path="fused") as a:
+        a.step(4)
+        ckpt = a.read()
+    # a fresh context (same seed: same Dirichlet shell) resumes from the checkpoint
+    with od.Jacobi3D(nx, ny, nz, split=(3, 2, 1), seed=12, init_mode=1, path="persistent") as b:
+        b.write(ckpt)
+        b.step(6)
+        assert_bitexact(b.read(), want, "restored")
+
+
+def test_device_read_and_write(od):
+    import torch
+    nx, ny, nz = 32, 32, 32
+    want = oracle.solve(nx, ny, nz, 2, 1, 5)
+    with od.Jacobi3D(nx, ny, nz, split=(2, 2, 2), seed=2, init_mode=1, path="fused") as s:
+        s.step(5)
+        t = torch.empty(nx * ny * nz, dtype=torch.float64, device="cuda:0")
+        s.read(t)
+        assert_bitexact(t.cpu().numpy(), want, "device read")
+        # writing the field back leaves it unchanged
+        s.write(t)
+        assert_bitexact(s.read(), want, "device write")
+
+
+@pytest.mark.parametrize("shape", [
+    dict(threads=128, cells_per_thread=1), dict(threads=128, cells_per_thread=8),
+    dict(threads=256, cells_per_thread=2), dict(threads=512, cells_per_thread=4),
+    dict(threads=512, cells_per_thread=8, stages=2), dict(threads=256, cells_per_thread=4, stages=8),
+    dict(threads=256, cells_per_thread=4, tile_y=3, tile_z=1),
+])
+@pytest.mark.parametrize("path", ["fused", "persistent"])
+def test_launch_shapes(od, path, shape):
+    nx, ny, nz = 96, 40, 44
+    want = oracle.solve(nx, ny, nz, 17, 1, 6)
+    with od.Jacobi3D(nx, ny, nz, split=(1, 2, 2), seed=17, init_mode=1, path=path, **shape) as s:
+        s.step(6)
+        assert_bitexact(s.read(), want, f"{path} {shape}")
+
+
+def test_persistent_reversed_order(od):
+    nx, ny, nz = 64, 64, 64
+    want = oracle.solve(nx, ny, nz, 6, 1, 9)
+    with od.Jacobi3D(nx, ny, nz, split=(4, 4, 4), seed=6, init_mode=1, path="persistent", order=1) as s:
+        s.step(9)
+        assert_bitexact(s.read(), want, "order=1")
+
+
+def test_stalled_tile_times_out_without_hanging(od):
+    # A tile that never publishes its step counter: the tiles that read it hit
+    # the (short) wait limit; the kernel returns, the error surfaces on sync,
+    # and the GPU context stays usable.
+    with od.Jacobi3D(32, 32, 32, split=(2, 2, 2), seed=1, path="persistent",
+                     spin_limit_ns=200_000_000) as s:
+        s.stall_tile(0)
+        s.step(3)
+        with pytest.raises(od.ODError) as ei:
+            s.sync()
+        assert ei.value.status == od._native.OD_ETIMEOUT
+        with pytest.raises(od.ODError) as ei:
+            s.step(1)
+        assert ei.value.status == od._native.OD_ESTATE
+    want = oracle.solve(32, 32, 32, 1, 1, 2)
+    with od.Jacobi3D(32, 32, 32, split=(2, 2, 2), seed=1, path="persistent") as s:
+        s.step(2)
+        assert_bitexact(s.read(), want, "after a timeout")
+
+
+# ------------------------------------------------------------------ full size
+
+def sample_points(nx, ny, nz, box, rng, n_random):
+    pts = {(0, 0, 0), (nx - 1, ny - 1, nz - 1), (nx // 2, ny // 2, nz // 2), (0, ny - 1, nz // 3)}
+    # cells on chare faces and corners, where delivery bugs would show
+    for (x0, bx, y0, by, z0, bz) in box[rng.choice(len(box), size=min(len(box), 6), replace=False)]:
+        pts.add((int(x0), int(y0), int(z0)))
+        pts.add((int(x0 + bx - 1), int(y0 + by // 2), int(z0 + bz - 1)))
+    for _ in range(n_random):
+        pts.add((int(rng.integers(nx)), int(rng.integers(ny)), int(rng.integers(nz))))
+    return sorted(pts)
+
+
+def check_sampled(od, w, path, iters, n_random=4, **kw):
+    box, _ = od.decompose(w.nx, w.ny, w.nz, **({"cuts": w.cuts} if w.cuts else {"split": w.split}))
+    with od.Jacobi3D(w.nx, w.ny, w.nz, seed=w.seed, init_mode=w.init_mode, path=path,
+                     **({"cuts": w.cuts} if w.cuts else {"split": w.split}), **kw) as s:
+        s.step(iters)
+        u = s.read()
+    # maximum principle: every value stays within [0, 1) like its inputs
+    assert float(u.min()) >= 0.0 and float(u.max()) < 1.0
+    rng = np.random.default_rng(w.seed)
+    for (x, y, z) in sample_points(w.nx, w.ny, w.nz, box, rng, n_random):
+        want = oracle.point(w.nx, w.ny, w.nz, w.seed, w.init_mode, iters, x, y, z)
+        got = u[x + w.nx * (y + w.ny * z)]
+        assert bits(np.array([got]))[0] == bits(np.array([want]))[0], (path, x, y, z, got, want)
+
+
+@pytest.mark.parametrize("odf", [1, 4096])
+@pytest.mark.parametrize("path", ["fused", "persistent"])
+def test_full_512_sampled(od, path, odf):
+    w = inputs.odf_sweep_512(odf)
+    check_sampled(od, w, path, w.iters)
+
+
+def test_full_uneven_768_sampled(od):
+    w = inputs.uneven_768()
+    check_sampled(od, w, "persistent", 60)
+
+
+def test_full_1024_odf4096_sampled(od):
+    w = inputs.ceiling_1024()
+    check_sampled(od, w, "persistent", w.iters, n_random=2)
