@@ -143,7 +143,7 @@ def oracle_cpu_baseline(edge: int, target_s: float = 12.0):
     t0 = time.perf_counter()
     oracle.sweep(P, 1, threads)
     one = time.perf_counter() - t0
-    iters = max(1, min(50, int(target_s / max(one, 1e-3))))
+    iters = max(1, min(1000, int(target_s / max(one, 1e-3))))
     t0 = time.perf_counter()
     oracle.sweep(P, iters, threads)
     dt = time.perf_counter() - t0
