@@ -108,7 +108,12 @@ typedef struct od_config {
     int32_t tile_z;              /* planes per tile (0 = planner default) */
     int32_t threads;             /* threads per CTA: 128, 256 or 512 (0 = 256) */
     int32_t cells_per_thread;    /* 1, 2, 4 or 8 (0 = planner default) */
-    int32_t stages;              /* TMA plane stages in flight, 3..8 (0 = 4) */
+    int32_t stages;              /* TMA plane stages in flight, 2..8 (0 = 4) */
+    int32_t arith;               /* where the update's operations run (the bits
+                                    never change): 0 all on the FP64 pipe;
+                                    1 division by 6 on the integer pipes;
+                                    1+k (k = 1..5) also the first k adds on the
+                                    integer pipes; -1 = library default (1) */
     int32_t order;               /* persistent path task order: 0 linear every
                                     step, 1 reversed on odd steps */
     int32_t stream_pool;         /* per-chare path: streams (0 = min(nchares,32)) */
@@ -133,7 +138,8 @@ typedef struct od_plan_info {
     uint64_t arena_bytes;          /* device bytes od_create needs */
     double bytes_per_step;         /* algorithmic HBM bytes per iteration:
                                       16*cells + 16*face_internal + 8*face_dirichlet */
-    int32_t tile_y, tile_z, threads, cells_per_thread, stages;
+    int32_t tile_y, tile_z;        /* largest tile used: rows, planes */
+    int32_t threads, cells_per_thread, stages, arith;
     int32_t smem_bytes;            /* dynamic shared memory per CTA */
 } od_plan_info;
 
@@ -203,6 +209,16 @@ OD_API od_status od_stats_get(od_ctx *ctx, od_stats *out);
  * publishes its step counter, so the tiles that wait on it run into the wait
  * limit and od_sync returns OD_ETIMEOUT.  -1 switches it off. */
 OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
+
+/* Self-test of the exact integer-pipe arithmetic the kernels use (a
+ * correctly rounded division by 6 and a correctly rounded addition, written
+ * from the IEEE 754 binary64 definition).  op 0: out[i] = a[i] / 6.0;
+ * op 1: out[i] = a[i] + b[i] (b unused for op 0); op 2 / 3: the same on the
+ * FP64 pipe (device only).  od_arith_host runs the routines on the host CPU
+ * over host arrays; od_arith_device runs them in a kernel over device arrays
+ * of the current device and synchronises.  n >= 0 elements. */
+OD_API od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n);
+OD_API od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n);
 
 /* Free everything the context owns (synchronises first).  NULL is allowed. */
 OD_API od_status od_destroy(od_ctx *ctx);

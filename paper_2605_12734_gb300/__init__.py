@@ -21,7 +21,8 @@ import numpy as np
 from . import _native
 from ._native import ODError, PATHS, check, lib, od_config, od_plan_info, od_stats
 
-__all__ = ["Jacobi3D", "ODError", "PATHS", "make_config", "plan", "decompose", "lib"]
+__all__ = ["Jacobi3D", "ODError", "PATHS", "make_config", "plan", "decompose", "lib", "arith_host",
+           "arith_device"]
 
 
 def _cuts_array(cuts):
@@ -34,7 +35,7 @@ def _cuts_array(cuts):
 def make_config(nx: int, ny: int, nz: int, *, split=(1, 1, 1), cuts=None, seed: int = 1,
                 init_mode: int = 1, path: str | int = "fused", autotune: bool = False,
                 tile_y: int = 0, tile_z: int = 0, threads: int = 0, cells_per_thread: int = 0,
-                stages: int = 0, order: int = 0, stream_pool: int = 0, device: int = 0,
+                stages: int = 0, arith: int = -1, order: int = 0, stream_pool: int = 0, device: int = 0,
                 stream: int | None = None, arena: int | None = None, arena_bytes: int = 0,
                 spin_limit_ns: int = 0):
     """Build an od_config (returns (config, keepalive) -- keep both alive while
@@ -57,6 +58,7 @@ def make_config(nx: int, ny: int, nz: int, *, split=(1, 1, 1), cuts=None, seed: 
     cfg.autotune = int(bool(autotune))
     cfg.tile_y, cfg.tile_z, cfg.threads = int(tile_y), int(tile_z), int(threads)
     cfg.cells_per_thread, cfg.stages, cfg.order = int(cells_per_thread), int(stages), int(order)
+    cfg.arith = int(arith)
     cfg.stream_pool, cfg.device = int(stream_pool), int(device)
     cfg.stream = stream
     cfg.arena = arena
@@ -82,6 +84,27 @@ def decompose(nx, ny, nz, **kw):
     check(lib().od_decompose(ctypes.byref(cfg), box.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                              nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n), "od_decompose")
     return box, nbr
+
+
+def arith_host(op: int, a: np.ndarray, b: np.ndarray | None = None) -> np.ndarray:
+    """Run the kernels' exact integer-pipe arithmetic on the host: op 0
+    a/6, op 1 a+b (float64 arrays)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = a if b is None else np.ascontiguousarray(b, dtype=np.float64)
+    out = np.empty_like(a)
+    check(lib().od_arith_host(int(op), a.ctypes.data, b.ctypes.data, out.ctypes.data, a.size), "od_arith_host")
+    return out
+
+
+def arith_device(op: int, a, b=None):
+    """Same on the device (torch CUDA float64 tensors); ops 2/3 use the FP64
+    pipe's IEEE division / add."""
+    import torch
+    b = a if b is None else b
+    out = torch.empty_like(a)
+    check(lib().od_arith_device(int(op), a.data_ptr(), b.data_ptr(), out.data_ptr(), a.numel()),
+          "od_arith_device")
+    return out
 
 
 class Jacobi3D:

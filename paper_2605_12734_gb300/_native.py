@@ -31,7 +31,7 @@ class od_config(ctypes.Structure):
         ("seed", _u64),
         ("init_mode", _i32), ("path", _i32), ("autotune", _i32),
         ("tile_y", _i32), ("tile_z", _i32), ("threads", _i32), ("cells_per_thread", _i32),
-        ("stages", _i32), ("order", _i32), ("stream_pool", _i32), ("device", _i32),
+        ("stages", _i32), ("arith", _i32), ("order", _i32), ("stream_pool", _i32), ("device", _i32),
         ("stream", _vp), ("arena", _vp), ("arena_bytes", _u64), ("spin_limit_ns", _u64),
     ]
 
@@ -42,7 +42,7 @@ class od_plan_info(ctypes.Structure):
         ("face_cells_internal", _i64), ("face_cells_dirichlet", _i64),
         ("arena_bytes", _u64), ("bytes_per_step", ctypes.c_double),
         ("tile_y", _i32), ("tile_z", _i32), ("threads", _i32), ("cells_per_thread", _i32),
-        ("stages", _i32), ("smem_bytes", _i32),
+        ("stages", _i32), ("arith", _i32), ("smem_bytes", _i32),
     ]
 
 
@@ -74,6 +74,8 @@ SIGNATURES = {
     "od_write": (_i32, [_vp, _vp, _i32]),
     "od_stats_get": (_i32, [_vp, ctypes.POINTER(od_stats)]),
     "od_debug_stall_tile": (_i32, [_vp, _i64]),
+    "od_arith_host": (_i32, [_i32, _vp, _vp, _vp, _i64]),
+    "od_arith_device": (_i32, [_i32, _vp, _vp, _vp, _i64]),
     "od_destroy": (_i32, [_vp]),
     "od_last_error": (ctypes.c_char_p, []),
     "od_version": (ctypes.c_char_p, []),

@@ -26,7 +26,10 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-f
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
 
 SOURCES = ["od_kernels.cu", "od_api.cu", "od_plan.cpp"]
-HEADERS = ["od_internal.h", "od_kernels.h", "od_plan.h"]
+# the tile kernels, compiled once per arithmetic mode (-DOD_AMODE=m)
+TILE_SOURCE = "od_tiles.cu"
+AMODES = range(7)
+HEADERS = ["od_internal.h", "od_kernels.h", "od_plan.h", "od_tile.cuh", "od_arith.cuh"]
 
 
 def _nvcc() -> str:
@@ -47,17 +50,20 @@ def _stale(target: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     """Compile (if needed) and return the path of libod.so."""
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "od.h")]
-    srcs = [os.path.join(CSRC, s) for s in SOURCES]
+    srcs = [os.path.join(CSRC, s) for s in SOURCES + [TILE_SOURCE]]
     if not force and not ptxas_info and not _stale(LIB, srcs + hdrs + [__file__]):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     procs, objs = [], []
-    for src in srcs:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    units = [(os.path.join(CSRC, s), [], os.path.basename(s)) for s in SOURCES]
+    units += [(os.path.join(CSRC, TILE_SOURCE), [f"-DOD_AMODE={m}"], f"od_tiles_am{m}")
+              for m in AMODES]
+    for src, defs, stem in units:
+        obj = os.path.join(BUILD, stem + ".o")
         objs.append(obj)
         if src.endswith(".cu"):
-            cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")
         else:

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "od.h"
+#include "od_arith.cuh"
 #include "od_internal.h"
 #include "od_kernels.h"
 #include "od_plan.h"
@@ -117,7 +118,7 @@ od_status enqueue_fused(od_ctx *c, int32_t iters) {
         KArgs a = base_args(c);
         a.tile_begin = 0;
         a.parity = (int32_t)(c->steps & 1);
-        OD_CUDA(od::launch_tiles(a, (int)p.tiles.size(), p.threads, p.cpt, true, p.smem_bytes, c->stream));
+        OD_CUDA(od::launch_tiles(a, (int)p.tiles.size(), p.threads, p.cpt, p.amode, true, p.smem_bytes, c->stream));
         c->steps++;
         c->launches++;
         c->api_calls++;
@@ -130,7 +131,7 @@ od_status enqueue_persistent(od_ctx *c, int32_t iters) {
     const od::Plan &p = c->plan;
     const int64_t nt = (int64_t)p.tiles.size();
     int bps = 0;
-    OD_CUDA(od::persistent_occupancy(p.threads, p.cpt, p.smem_bytes, &bps));
+    OD_CUDA(od::persistent_occupancy(p.threads, p.cpt, p.amode, p.smem_bytes, &bps));
     if (bps < 1) return fail(OD_EINVAL, "persistent kernel does not fit on an SM with this tiling");
     int grid = (int)std::min<int64_t>(nt, (int64_t)bps * c->num_sms);
     c->persistent_grid = grid;
@@ -144,7 +145,7 @@ od_status enqueue_persistent(od_ctx *c, int32_t iters) {
         KArgs a = base_args(c);
         a.iters = n;
         a.t0 = (int32_t)(c->steps & 0x7fffffff);
-        OD_CUDA(od::launch_persistent(a, grid, p.threads, p.cpt, p.smem_bytes, c->stream));
+        OD_CUDA(od::launch_persistent(a, grid, p.threads, p.cpt, p.amode, p.smem_bytes, c->stream));
         c->steps += n;
         c->launches++;
         c->api_calls += 3;
@@ -182,7 +183,7 @@ od_status enqueue_per_chare_steps(od_ctx *c, int64_t t_first, int32_t iters, int
             KArgs a = base_args(c);
             a.tile_begin = h.tile_begin;
             a.parity = sp;
-            OD_CUDA(od::launch_tiles(a, h.tile_end - h.tile_begin, p.threads, p.cpt, false, p.smem_bytes, st));
+            OD_CUDA(od::launch_tiles(a, h.tile_end - h.tile_begin, p.threads, p.cpt, p.amode, false, p.smem_bytes, st));
             OD_CUDA(od::launch_pack(c->d_ch, ci, dp, h.foff[6], st));
             (*kernels) += 2;
             (*calls) += 2;
@@ -357,6 +358,23 @@ void od_config_default(od_config *cfg) {
     cfg->seed = 1;
     cfg->init_mode = OD_INIT_UNIFORM;
     cfg->path = OD_PATH_FUSED;
+    cfg->arith = -1;
+}
+
+od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n) {
+    if (n < 0 || (n > 0 && (!a || !out || (op == 1 && !b)))) return fail(OD_EINVAL, "bad arguments");
+    if (op != 0 && op != 1) return fail(OD_EINVAL, "host op must be 0 (div6) or 1 (add)");
+    for (int64_t i = 0; i < n; ++i) out[i] = op == 0 ? od::div6(a[i]) : od::add(a[i], b[i]);
+    return OD_OK;
+}
+
+od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n) {
+    if (n < 0 || (n > 0 && (!a || !out || ((op == 1 || op == 3) && !b)))) return fail(OD_EINVAL, "bad arguments");
+    if (op < 0 || op > 3) return fail(OD_EINVAL, "op must be 0..3");
+    if (n == 0) return OD_OK;
+    OD_CUDA(od::launch_arith(op, a, b, out, n, 0));
+    OD_CUDA(cudaStreamSynchronize(0));
+    return OD_OK;
 }
 
 od_status od_plan(const od_config *cfg, od_plan_info *out) {
@@ -416,7 +434,7 @@ od_status od_create(od_ctx **out, const od_config *cfg) {
         }                                                 \
     } while (0)
     OD_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-    if (!od::tile_shape_supported(p.threads, p.cpt)) {
+    if (!od::tile_shape_supported(p.threads, p.cpt, p.amode)) {
         release(c);
         return fail(OD_EINVAL, "unsupported threads / cells_per_thread");
     }
@@ -479,7 +497,7 @@ od_status od_create(od_ctx **out, const od_config *cfg) {
                                cudaMemcpyHostToDevice, c->stream));
     OD_TRY(cudaMemcpyAsync(c->d_order, p.order.data(), p.order.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, c->stream));
-    OD_TRY(od::prepare_tile_kernels(p.threads, p.cpt, p.smem_bytes));
+    OD_TRY(od::prepare_tile_kernels(p.threads, p.cpt, p.amode, p.smem_bytes));
     // per-chare path resources
     int P = cfg->stream_pool > 0 ? cfg->stream_pool : 32;
     P = (int)std::min<int64_t>(P, (int64_t)p.ch.size());

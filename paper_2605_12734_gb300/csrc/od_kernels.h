@@ -7,22 +7,22 @@
 
 namespace od {
 
-// Tile kernels are instantiated for threads in {128,256,512} and cells per
-// thread in {1,2,4,8}.
-bool tile_shape_supported(int threads, int cpt);
+// Tile kernels exist for (threads, cells per thread) in {128}x{2,4,8},
+// {256}x{1,2,4,8}, {512}x{1,2} and arithmetic modes 0..6 (od_tile.cuh).
+bool tile_shape_supported(int threads, int cpt, int amode);
 
 // Raise the dynamic shared-memory limit of the tile kernels of one shape.
-cudaError_t prepare_tile_kernels(int threads, int cpt, int smem_bytes);
+cudaError_t prepare_tile_kernels(int threads, int cpt, int amode, int smem_bytes);
 
 // One CTA per tile, tiles [a.tile_begin, a.tile_begin + grid).  push = 1 also
 // stores each new boundary value into the neighbour's ghost layer.
-cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, bool push, int smem_bytes,
+cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, int amode, bool push, int smem_bytes,
                          cudaStream_t s);
 
 // Persistent ticket kernel over a.iters steps.
-cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, int smem_bytes,
+cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, int amode, int smem_bytes,
                               cudaStream_t s);
-cudaError_t persistent_occupancy(int threads, int cpt, int smem_bytes, int *blocks_per_sm);
+cudaError_t persistent_occupancy(int threads, int cpt, int amode, int smem_bytes, int *blocks_per_sm);
 
 cudaError_t launch_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
                         int mode, cudaStream_t s);
@@ -30,6 +30,9 @@ cudaError_t launch_pack(const ChareDev *ch, int c, int parity, int elems, cudaSt
 cudaError_t launch_unpack(const ChareDev *ch, int c, int parity, int slot, int elems, cudaStream_t s);
 cudaError_t launch_gather(const ChareDev *ch, int nch, int parity, int64_t nx, int64_t ny, double *g,
                           cudaStream_t s);
+// Arithmetic self-test over device arrays (op: 0 div6, 1 add on the integer
+// pipes; 2 division by 6, 3 add on the FP64 pipe).
+cudaError_t launch_arith(int op, const double *a, const double *b, double *out, int64_t n, cudaStream_t s);
 cudaError_t launch_scatter(const ChareDev *ch, int nch, int parity, int64_t nx, int64_t ny, int64_t nz,
                            const double *g, cudaStream_t s);
 

@@ -18,6 +18,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int32_t kMaxSmem = 232448;  // 227 KB opt-in per CTA on sm_100/sm_103
 constexpr int32_t kSmemHeader = 128;  // mbarriers + ticket slot
+constexpr int32_t kDefaultArith = 1;   // integer-pipe division, FP64 adds
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int32_t round_up(int32_t v, int32_t a) { return (v + a - 1) / a * a; }
@@ -127,12 +128,19 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
     p.stages = cfg->stages ? cfg->stages : 4;
     p.tile_y = cfg->tile_y;
     p.tile_z = cfg->tile_z;
+    p.amode = cfg->arith < 0 ? kDefaultArith : cfg->arith;
+    if (p.amode > 6) {
+        *err = "arith must be in [0, 6] (or -1 for the default)";
+        return OD_EINVAL;
+    }
     if (p.threads != 128 && p.threads != 256 && p.threads != 512) {
         *err = "threads must be 128, 256 or 512";
         return OD_EINVAL;
     }
-    if (p.cpt != 1 && p.cpt != 2 && p.cpt != 4 && p.cpt != 8) {
-        *err = "cells_per_thread must be 1, 2, 4 or 8";
+    if (!((p.threads == 128 && (p.cpt == 2 || p.cpt == 4 || p.cpt == 8)) ||
+          (p.threads == 256 && (p.cpt == 1 || p.cpt == 2 || p.cpt == 4 || p.cpt == 8)) ||
+          (p.threads == 512 && (p.cpt == 1 || p.cpt == 2)))) {
+        *err = "supported (threads, cells_per_thread): 128 x {2,4,8}, 256 x {1,2,4,8}, 512 x {1,2}";
         return OD_EINVAL;
     }
     if (p.stages < 2 || p.stages > 8) {
@@ -220,6 +228,8 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
                 t.k0 = ks[a]; t.nk = kl[a];
                 p.tiles.push_back(t);
                 max_stage = std::max(max_stage, stage_doubles_for(t.nj, h.pitch));
+                p.max_nj = std::max(p.max_nj, t.nj);
+                p.max_nk = std::max(p.max_nk, t.nk);
                 if (p.tiles.size() > (size_t)0x7fffffff) {
                     *err = "too many tiles";
                     return OD_EINVAL;
@@ -298,8 +308,9 @@ void plan_info(const Plan &p, od_plan_info *o) {
     o->face_cells_dirichlet = p.face_dirichlet;
     o->arena_bytes = p.arena_bytes;
     o->bytes_per_step = p.bytes_per_step;
-    o->tile_y = p.tile_y;
-    o->tile_z = p.tile_z;
+    o->tile_y = p.max_nj;
+    o->tile_z = p.max_nk;
+    o->arith = p.amode;
     o->threads = p.threads;
     o->cells_per_thread = p.cpt;
     o->stages = p.stages;

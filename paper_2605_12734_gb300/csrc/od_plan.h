@@ -33,7 +33,8 @@ struct Plan {
     std::vector<int32_t> dep_ptr, dep_idx;    // CSR: tiles each tile reads
     std::vector<int32_t> order;               // persistent task order
     // execution shape
-    int32_t threads = 256, cpt = 4, stages = 4, tile_y = 0, tile_z = 0;
+    int32_t threads = 256, cpt = 4, stages = 4, tile_y = 0, tile_z = 0, amode = 1;
+    int32_t max_nj = 0, max_nk = 0;                // largest tile actually used
     int32_t stage_doubles = 0;                // per-stage smem slot
     int32_t smem_bytes = 0;                   // dynamic smem per CTA
     // arena layout (byte offsets from the arena base)

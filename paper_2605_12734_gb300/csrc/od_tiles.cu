@@ -1,0 +1,31 @@
+// od_tiles.cu -- instantiates the tile kernels for one arithmetic mode.
+// Built once per mode with -DOD_AMODE=<0..6> (the build compiles the copies
+// in parallel); od_kernels.cu dispatches on the mode at launch time.
+#include "od_tile.cuh"
+
+#ifndef OD_AMODE
+#error "compile with -DOD_AMODE=<mode>"
+#endif
+
+#define OD_CAT2(a, b) a##b
+#define OD_CAT(a, b) OD_CAT2(a, b)
+
+namespace od {
+
+// kind 0: k_tiles without push, 1: k_tiles with push, 2: k_persistent
+void *OD_CAT(tile_kernel_am, OD_AMODE)(int threads, int cpt, int kind) {
+    using namespace tile;
+#define OD_CASE(NT_, C_)                                                          \
+    if (threads == NT_ && cpt == C_) {                                            \
+        if (kind == 0) return (void *)k_tiles<NT_, C_, false, OD_AMODE>;          \
+        if (kind == 1) return (void *)k_tiles<NT_, C_, true, OD_AMODE>;           \
+        return (void *)k_persistent<NT_, C_, OD_AMODE>;                           \
+    }
+    OD_CASE(128, 2) OD_CASE(128, 4) OD_CASE(128, 8)
+    OD_CASE(256, 1) OD_CASE(256, 2) OD_CASE(256, 4) OD_CASE(256, 8)
+    OD_CASE(512, 1) OD_CASE(512, 2)
+#undef OD_CASE
+    return nullptr;
+}
+
+}  // namespace od

@@ -96,6 +96,8 @@ def test_plan_model_bytes(od, odf):
     dict(split=(1, 1, 1), dims=(0, 4, 4)),          # empty grid
     dict(split=(1, 1, 1), dims=(4, 4, 4), threads=96),
     dict(split=(1, 1, 1), dims=(4, 4, 4), cells_per_thread=3),
+    dict(split=(1, 1, 1), dims=(4, 4, 4), threads=512, cells_per_thread=4),
+    dict(split=(1, 1, 1), dims=(4, 4, 4), arith=7),
     dict(split=(1, 1, 1), dims=(4, 4, 4), stages=9),
     dict(split=(1, 1, 1), dims=(8192, 4, 4)),       # row wider than the CTA can hold
     dict(cuts=([0, 3, 2, 8], None, None), dims=(8, 4, 4)),  # not ascending
@@ -118,7 +120,7 @@ def test_invalid_configs_rejected(od, bad):
     dict(dims=(64, 64, 64), split=(2, 2, 2)),
     dict(dims=(37, 29, 23), split=(3, 2, 2), tile_y=5, tile_z=4),
     dict(dims=(512, 512, 512), split=(1, 1, 1)),
-    dict(dims=(120, 7, 9), split=(1, 1, 1), threads=128, cells_per_thread=1),
+    dict(dims=(120, 7, 9), split=(1, 1, 1), threads=128, cells_per_thread=2),
 ])
 def test_tile_counts(od, kw):
     dims = kw.pop("dims")

@@ -1,0 +1,145 @@
+"""The kernels' integer-pipe binary64 routines (division by 6, addition) run on
+the host through od_arith_host and must equal IEEE round-to-nearest results
+(numpy on this CPU) bit for bit, on random, structured and special inputs."""
+import numpy as np
+import pytest
+
+from paper_2605_12734_gb300 import build as od_build
+
+
+@pytest.fixture(scope="module")
+def od():
+    od_build.build()
+    import paper_2605_12734_gb300 as pkg
+    return pkg
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float64).view(np.uint64)
+
+
+def same(got, want):
+    g, w = bits(got), bits(want)
+    nan = np.isnan(want)
+    ok = (g == w) | (nan & np.isnan(got))
+    if not ok.all():
+        i = int(np.flatnonzero(~ok)[0])
+        raise AssertionError(f"{(~ok).sum()} mismatches; first input index {i}: got {got[i]!r} want {want[i]!r}")
+
+
+def from_bits(u):
+    return np.asarray(u, dtype=np.uint64).view(np.float64)
+
+
+def positive_normals(rng, n, emin=1, emax=2046):
+    e = rng.integers(emin, emax + 1, n, dtype=np.uint64)
+    m = rng.integers(0, 1 << 52, n, dtype=np.uint64)
+    return from_bits((e << np.uint64(52)) | m)
+
+
+SPECIALS = np.array([0.0, -0.0, 1.0, -1.0, 6.0, 3.0, 0.5, np.inf, -np.inf, np.nan,
+                     5e-324, 2.2250738585072014e-308, 2.225073858507201e-308, 1.7976931348623157e308,
+                     -2.5, 1e-310, 4.4e-308, 1.3e-307, 0.1, 1 / 3, 2 / 3], dtype=np.float64)
+
+
+def test_div6_random_unit_interval(od):
+    rng = np.random.default_rng(1)
+    a = rng.random(2_000_000) * 6.0
+    same(od.arith_host(0, a), a / 6.0)
+
+
+def test_div6_all_binades(od):
+    rng = np.random.default_rng(2)
+    a = positive_normals(rng, 2_000_000)
+    same(od.arith_host(0, a), a / 6.0)
+    same(od.arith_host(0, -a), -a / 6.0)
+
+
+def test_div6_structured_significands(od):
+    # significands around the 3*2^51 split, multiples of 3 (exact quotients),
+    # remainders 1 and 2, all-ones, for exponents at the fast-path edge
+    M = []
+    for base in (1 << 52, 3 << 51, (1 << 53) - 1):
+        M += [base + d for d in range(-40, 41) if (1 << 52) <= base + d < (1 << 53)]
+    M += [3 * k for k in range((1 << 52) // 3 + 1, (1 << 52) // 3 + 200)]
+    M = np.array(M, dtype=np.uint64) - np.uint64(1 << 52)
+    for e in (1, 2, 3, 4, 5, 1023, 2045, 2046):
+        a = from_bits((np.uint64(e) << np.uint64(52)) | M)
+        same(od.arith_host(0, a), a / 6.0)
+
+
+def test_div6_specials_and_subnormals(od):
+    rng = np.random.default_rng(3)
+    sub = from_bits(rng.integers(1, 1 << 52, 100_000, dtype=np.uint64))
+    a = np.concatenate([SPECIALS, sub, -sub])
+    same(od.arith_host(0, a), a / 6.0)
+
+
+def test_add_random_unit_interval(od):
+    rng = np.random.default_rng(4)
+    a = rng.random(2_000_000)
+    b = rng.random(2_000_000) * rng.choice([1.0, 1e-3, 1e-9, 3.0], 2_000_000)
+    same(od.arith_host(1, a, b), a + b)
+
+
+def test_add_all_exponent_gaps(od):
+    rng = np.random.default_rng(5)
+    n = 20_000
+    for gap in list(range(0, 70)) + [100, 500, 1000]:
+        ea = rng.integers(gap + 1, 2046, n, dtype=np.uint64)
+        eb = ea - np.uint64(gap)
+        ma = rng.integers(0, 1 << 52, n, dtype=np.uint64)
+        mb = rng.integers(0, 1 << 52, n, dtype=np.uint64)
+        a = from_bits((ea << np.uint64(52)) | ma)
+        b = from_bits((eb << np.uint64(52)) | mb)
+        same(od.arith_host(1, a, b), a + b)
+        same(od.arith_host(1, b, a), b + a)
+
+
+def test_add_ties_and_carries(od):
+    # exact halfway cases (round to even both ways), carries into a new binade,
+    # rounding carries into the exponent, largest finite sums
+    one = 1.0
+    ulp = 2.0 ** -52
+    cases = [
+        (one, ulp / 2), (one + ulp, ulp / 2), (one, 3 * ulp / 2), (one + ulp, 3 * ulp / 2),
+        (1.5, 1.5), (2 - ulp, 2 - ulp), (2 - ulp, ulp / 2), (2 - ulp, ulp), (2 - ulp, ulp / 4),
+        (1.0, 1.0), (0.75, 0.25), (2 - ulp, 2 - 2 * ulp), (1.7976931348623157e308 / 2, 1.7976931348623157e308 / 2),
+        (8.98846567431158e307, 8.98846567431158e307), (1.0, 2.0 ** -60), (1.0, 2.0 ** -53 + 2.0 ** -105),
+    ]
+    rng = np.random.default_rng(6)
+    m = rng.integers(0, 1 << 52, 50_000, dtype=np.uint64)
+    a = from_bits((np.uint64(1023) << np.uint64(52)) | m)
+    # b = a's low half-ulp patterns: same exponent minus 53/54 with trailing bits
+    b1 = from_bits((np.uint64(1023 - 53) << np.uint64(52)) | (m & np.uint64(0xFF)))
+    b2 = from_bits((np.uint64(1023 - 52) << np.uint64(52)))
+    A = np.concatenate([np.array([c[0] for c in cases]), a, a, 2.0 - a / 4])
+    B = np.concatenate([np.array([c[1] for c in cases]), b1, np.full_like(a, b2[()] if b2.shape == () else b2),
+                        a])
+    same(od.arith_host(1, A, B), A + B)
+    same(od.arith_host(1, B, A), B + A)
+
+
+def test_add_specials_mixed_signs_subnormals(od):
+    rng = np.random.default_rng(7)
+    n = 200_000
+    pool = np.concatenate([SPECIALS, -SPECIALS, positive_normals(rng, 1000),
+                           from_bits(rng.integers(1, 1 << 52, 1000, dtype=np.uint64))])
+    a = rng.choice(pool, n)
+    b = rng.choice(pool, n)
+    with np.errstate(all="ignore"):
+        same(od.arith_host(1, a, b), a + b)
+
+
+def test_jacobi_sum_chain(od):
+    # the kernels' exact sequence (((((W+E)+S)+N)+D)+U)/6 assembled from the
+    # host routines equals the IEEE chain
+    rng = np.random.default_rng(8)
+    v = rng.random((6, 1_000_000))
+    v[:, ::7] = 0.0
+    s_ieee = ((((v[0] + v[1]) + v[2]) + v[3]) + v[4]) + v[5]
+    s = od.arith_host(1, v[0], v[1])
+    for k in range(2, 6):
+        s = od.arith_host(1, s, v[k])
+    same(s, s_ieee)
+    same(od.arith_host(0, s), s_ieee / 6.0)

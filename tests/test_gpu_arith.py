@@ -1,0 +1,60 @@
+"""On the GPU, the integer-pipe division by 6 and addition must equal both
+CUDA's own IEEE operations (__ddiv_rn, __dadd_rn) and the host's IEEE results,
+bit for bit, on tens of millions of inputs."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_12734_gb300 import build
+    build.build()
+    import paper_2605_12734_gb300 as pkg
+    return pkg, torch
+
+
+def _bits(t):
+    return t.view(dtype=__import__("torch").int64)
+
+
+def test_div6_device(env):
+    pkg, torch = env
+    g = torch.Generator(device="cuda:0").manual_seed(1)
+    for scale in (6.0, 1e-300, 1e300):
+        a = torch.rand(32_000_000, dtype=torch.float64, device="cuda:0", generator=g) * scale
+        fast = pkg.arith_device(0, a)
+        ieee = pkg.arith_device(2, a)
+        assert torch.equal(_bits(fast), _bits(ieee))
+    # random bit patterns over every binade (and sign)
+    u = torch.randint(0, 2**62, (16_000_000,), device="cuda:0", generator=g, dtype=torch.int64)
+    a = u.view(torch.float64)
+    a = torch.where(torch.isfinite(a), a, torch.zeros_like(a))
+    assert torch.equal(_bits(pkg.arith_device(0, a)), _bits(pkg.arith_device(2, a)))
+    assert torch.equal(_bits(pkg.arith_device(0, -a)), _bits(pkg.arith_device(2, -a)))
+    host = a[:2_000_000].cpu().numpy()
+    assert np.array_equal(pkg.arith_device(0, a[:2_000_000]).cpu().numpy().view(np.uint64),
+                          (host / 6.0).view(np.uint64))
+
+
+def test_add_device(env):
+    pkg, torch = env
+    g = torch.Generator(device="cuda:0").manual_seed(2)
+    n = 32_000_000
+    a = torch.rand(n, dtype=torch.float64, device="cuda:0", generator=g)
+    for scale in (1.0, 1e-5, 1e-12, 3.0, 2.0 ** -53):
+        b = torch.rand(n, dtype=torch.float64, device="cuda:0", generator=g) * scale
+        assert torch.equal(_bits(pkg.arith_device(1, a, b)), _bits(pkg.arith_device(3, a, b)))
+    u = torch.randint(0, 2**62, (2, 16_000_000), device="cuda:0", generator=g, dtype=torch.int64)
+    x = u.view(torch.float64)
+    x = torch.where(torch.isfinite(x), x, torch.ones_like(x))
+    assert torch.equal(_bits(pkg.arith_device(1, x[0], x[1])), _bits(pkg.arith_device(3, x[0], x[1])))
+    ha, hb = x[0, :2_000_000].cpu().numpy(), x[1, :2_000_000].cpu().numpy()
+    with np.errstate(all="ignore"):
+        want = (ha + hb).view(np.uint64)
+    assert np.array_equal(pkg.arith_device(1, x[0, :2_000_000].contiguous(),
+                                           x[1, :2_000_000].contiguous()).cpu().numpy().view(np.uint64), want)
