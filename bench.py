@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--tile-z", type=int, default=0)
+    ap.add_argument("--arith", type=int, default=-1,
+                    help="where the update's operations run (od_config.arith; -1 = library default)")
     return ap.parse_args()
 
 
@@ -230,7 +232,7 @@ def run_ours(args):
         raise SystemExit("--odf must be a cube")
     stream = torch.cuda.Stream(device=dev)
     tune_kw = dict(threads=args.threads, cells_per_thread=args.cpt, stages=args.stages,
-                   tile_y=args.tile_y, tile_z=args.tile_z, autotune=args.tune, device=dev)
+                   tile_y=args.tile_y, tile_z=args.tile_z, arith=args.arith, autotune=args.tune, device=dev)
 
     solver = pkg.Jacobi3D(edge, edge, edge, split=(p, p, p), seed=2, init_mode=1, path=args.path,
                           stream=stream.cuda_stream, **tune_kw)
@@ -338,8 +340,8 @@ def run_ours(args):
                            "init": "U[0,1) everywhere, Dirichlet shell fixed",
                            "l2": "no flush: 2 parity buffers of ~2.3 GB each exceed the 129 MB L2",
                            "parallelism": f"replicas x{world}",
-                           "tiling": {k: plan[k] for k in ("threads", "cells_per_thread", "stages",
-                                                           "smem_bytes", "ntiles")}},
+                           "tiling": {k: plan[k] for k in ("threads", "cells_per_thread", "stages", "arith",
+                                                           "tile_y", "tile_z", "smem_bytes", "ntiles")}},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "eff_GBps": 16 * updates_step / (ms_step * 1e-3) / 1e9,
                 "per_chare_baseline": baseline}

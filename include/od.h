@@ -106,14 +106,19 @@ typedef struct od_config {
                                     after tuning, so results do not change) */
     int32_t tile_y;              /* max rows per tile (0 = planner default) */
     int32_t tile_z;              /* planes per tile (0 = planner default) */
-    int32_t threads;             /* threads per CTA: 128, 256 or 512 (0 = 256) */
-    int32_t cells_per_thread;    /* 1, 2, 4 or 8 (0 = planner default) */
-    int32_t stages;              /* TMA plane stages in flight, 2..8 (0 = 4) */
+    int32_t threads;             /* threads per CTA: 128, 256 or 512 */
+    int32_t cells_per_thread;    /* 1, 2, 4 or 8; supported pairs 128 x {2,4,8},
+                                    256 x {1,2,4,8}, 512 x {1,2}.  Both 0: the
+                                    planner takes the smallest of 128x4, 256x4,
+                                    256x8 that holds two rows of the widest
+                                    chare */
+    int32_t stages;              /* TMA ring slots, 3..8 (0 = 4): planes k-1,
+                                    k, k+1 resident, the rest in flight */
     int32_t arith;               /* where the update's operations run (the bits
                                     never change): 0 all on the FP64 pipe;
                                     1 division by 6 on the integer pipes;
                                     1+k (k = 1..5) also the first k adds on the
-                                    integer pipes; -1 = library default (1) */
+                                    integer pipes; -1 = library default (2) */
     int32_t order;               /* persistent path task order: 0 linear every
                                     step, 1 reversed on odd steps */
     int32_t stream_pool;         /* per-chare path: streams (0 = min(nchares,32)) */
@@ -214,7 +219,9 @@ OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
  * correctly rounded division by 6 and a correctly rounded addition, written
  * from the IEEE 754 binary64 definition).  op 0: out[i] = a[i] / 6.0;
  * op 1: out[i] = a[i] + b[i] (b unused for op 0); op 2 / 3: the same on the
- * FP64 pipe (device only).  od_arith_host runs the routines on the host CPU
+ * FP64 pipe (device only); op 10+m (m = 0..6): the whole Jacobi update
+ * (((((a0+a1)+a2)+a3)+a4)+a5)/6 of the six operands a[6i..6i+5] in
+ * arithmetic mode m (see od_config.arith), b unused.  od_arith_host runs the routines on the host CPU
  * over host arrays; od_arith_device runs them in a kernel over device arrays
  * of the current device and synchronises.  n >= 0 elements. */
 OD_API od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n);

@@ -88,11 +88,13 @@ def decompose(nx, ny, nz, **kw):
 
 def arith_host(op: int, a: np.ndarray, b: np.ndarray | None = None) -> np.ndarray:
     """Run the kernels' exact integer-pipe arithmetic on the host: op 0
-    a/6, op 1 a+b (float64 arrays)."""
+    a/6, op 1 a+b, op 10+m the Jacobi update in arithmetic mode m over six
+    operands per element (float64 arrays)."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = a if b is None else np.ascontiguousarray(b, dtype=np.float64)
-    out = np.empty_like(a)
-    check(lib().od_arith_host(int(op), a.ctypes.data, b.ctypes.data, out.ctypes.data, a.size), "od_arith_host")
+    n = a.size // 6 if op >= 10 else a.size
+    out = np.empty(n, dtype=np.float64)
+    check(lib().od_arith_host(int(op), a.ctypes.data, b.ctypes.data, out.ctypes.data, n), "od_arith_host")
     return out
 
 
@@ -101,9 +103,9 @@ def arith_device(op: int, a, b=None):
     pipe's IEEE division / add."""
     import torch
     b = a if b is None else b
-    out = torch.empty_like(a)
-    check(lib().od_arith_device(int(op), a.data_ptr(), b.data_ptr(), out.data_ptr(), a.numel()),
-          "od_arith_device")
+    n = a.numel() // 6 if op >= 10 else a.numel()
+    out = torch.empty(n, dtype=torch.float64, device=a.device)
+    check(lib().od_arith_device(int(op), a.data_ptr(), b.data_ptr(), out.data_ptr(), n), "od_arith_device")
     return out
 
 

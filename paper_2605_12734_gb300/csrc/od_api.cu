@@ -363,14 +363,16 @@ void od_config_default(od_config *cfg) {
 
 od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n) {
     if (n < 0 || (n > 0 && (!a || !out || (op == 1 && !b)))) return fail(OD_EINVAL, "bad arguments");
-    if (op != 0 && op != 1) return fail(OD_EINVAL, "host op must be 0 (div6) or 1 (add)");
-    for (int64_t i = 0; i < n; ++i) out[i] = op == 0 ? od::div6(a[i]) : od::add(a[i], b[i]);
+    if (op != 0 && op != 1 && !(op >= 10 && op <= 16))
+        return fail(OD_EINVAL, "host op must be 0 (div6), 1 (add) or 10..16 (update)");
+    for (int64_t i = 0; i < n; ++i)
+        out[i] = op == 0 ? od::div6(a[i]) : op == 1 ? od::add(a[i], b[i]) : od::jacobi_update_mode(op - 10, a + 6 * i);
     return OD_OK;
 }
 
 od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n) {
     if (n < 0 || (n > 0 && (!a || !out || ((op == 1 || op == 3) && !b)))) return fail(OD_EINVAL, "bad arguments");
-    if (op < 0 || op > 3) return fail(OD_EINVAL, "op must be 0..3");
+    if (!((op >= 0 && op <= 3) || (op >= 10 && op <= 16))) return fail(OD_EINVAL, "op must be 0..3 or 10..16");
     if (n == 0) return OD_OK;
     OD_CUDA(od::launch_arith(op, a, b, out, n, 0));
     OD_CUDA(cudaStreamSynchronize(0));
@@ -474,13 +476,12 @@ od_status od_create(od_ctx **out, const od_config *cfg) {
         const od::HostChare &h = p.ch[i];
         ChareDev &d = c->h_ch[i];
         memset(&d, 0, sizeof d);
-        d.bx = h.bx; d.by = h.by; d.bz = h.bz; d.pitch = h.pitch; d.xgp = h.xgp;
+        d.bx = h.bx; d.by = h.by; d.bz = h.bz; d.pitch = h.pitch;
         for (int f = 0; f < 6; ++f) d.nbr[f] = h.nbr[f];
         for (int f = 0; f < 7; ++f) d.foff[f] = h.foff[f];
         d.x0 = h.x0; d.y0 = h.y0; d.z0 = h.z0;
         for (int s2 = 0; s2 < 2; ++s2) {
             d.A[s2] = (double *)(A + h.offA[s2]);
-            for (int sd = 0; sd < 2; ++sd) d.XG[s2][sd] = (double *)(A + h.offXG[s2][sd]);
             d.recv[s2] = (double *)(A + h.offRecv[s2]);
         }
         d.send = (double *)(A + h.offSend);

@@ -137,4 +137,169 @@ OD_HD double add(double a, double b) {
     return f64_from(((uint64_t)(e - 1u) << 52) + Mt);
 }
 
+// ---------------------------------------------------------------- chains
+//
+// A chain of additions keeps its partial sum unpacked: value = m * 2^(e-1075)
+// with m in [2^52, 2^53) and biased exponent e, i.e. exactly the binary64
+// number the IEEE sum would have produced, minus the packing.  Every step is
+// still rounded to 53 bits, so the chain reproduces the IEEE sequence bit for
+// bit.  The chain accepts only operands in its domain: positive with biased
+// exponent in [4, 2040] (so no partial sum of up to six such operands can
+// overflow, and s/6 of the total stays normal); callers fall back to IEEE
+// operations when any operand is outside it.
+
+struct Unpacked {
+    uint64_t m;  // significand with the hidden bit, [2^52, 2^53)
+    uint32_t e;  // biased exponent
+};
+
+// Unpack x; returns false when x is outside the chain's domain.
+OD_HD bool unpack_chain(double x, Unpacked &u) {
+    const uint64_t b = f64_bits(x);
+    const uint32_t hi = (uint32_t)(b >> 32);
+    u.e = hi >> 20;  // includes the sign bit: negative x gives e >= 2048
+    u.m = (b & kFrac) | kHid;
+    return u.e - 4u <= 2036u;
+}
+
+OD_HD double pack_chain(const Unpacked &u) { return f64_from(((uint64_t)(u.e - 1u) << 52) + u.m); }
+
+// a + b rounded to nearest even, both in the chain's domain.  Both
+// significands are scaled by 2^10 inside a 64-bit word; the bits of the
+// smaller one that fall off the word are folded into bit 0 (a sticky bit),
+// which is enough for the round-to-nearest-even decision because the guard
+// field's half-way pattern has bit 0 clear.  No branches.
+OD_HD Unpacked add_chain(const Unpacked &a, const Unpacked &b) {
+    const bool swap = b.e > a.e;
+    const uint32_t e = swap ? b.e : a.e;
+    const uint32_t d0 = swap ? b.e - a.e : a.e - b.e;
+    const uint32_t d = d0 < 63u ? d0 : 63u;
+    const uint64_t big10 = (swap ? b.m : a.m) << 10;
+    const uint64_t small10 = (swap ? a.m : b.m) << 10;
+    const uint64_t B = small10 >> d;
+    const uint64_t sticky = (B << d) != small10 ? 1u : 0u;
+    const uint64_t S = (big10 + B) | sticky;  // < 2^64
+    const uint32_t c = (uint32_t)(S >> 63);   // carry into a new binade
+    const uint32_t sh = 10u + c;
+    const uint64_t M0 = S >> sh;
+    const uint32_t rem = (uint32_t)S & ((1u << sh) - 1u);
+    const uint32_t half = 1u << (sh - 1u);
+    const uint32_t up = (rem > half || (rem == half && (M0 & 1u))) ? 1u : 0u;
+    const uint64_t M = M0 + up;
+    const bool carry = M == (kHid << 1);      // rounding carried into 2^53
+    Unpacked r;
+    r.m = carry ? kHid : M;
+    r.e = e + c + (carry ? 1u : 0u);
+    return r;
+}
+
+// s / 6 for s in the chain's range (exponent >= 4): see div6.
+OD_HD double div6_chain(const Unpacked &s) {
+    const bool big = s.m >= (3ull << 51);
+    const uint64_t N = big ? (s.m << 1) : (s.m << 2);
+    const uint64_t Q0 = mulhi64(N, 0xAAAAAAAAAAAAAAABull) >> 1;
+    const uint32_t r = (uint32_t)N - 3u * (uint32_t)Q0;
+    const uint64_t Q = Q0 + (r == 2u ? 1u : 0u);
+    const uint64_t er = (uint64_t)(s.e - (big ? 2u : 3u));
+    return f64_from(((er - 1u) << 52) + Q);
+}
+
+// ---------------------------------------------------------------- update
+
+// s / 6 on the integer pipes without a branch; ok = false when s is outside
+// [2^-1019, inf) in magnitude (zero, subnormal results, inf, NaN), where the
+// caller must use the IEEE division instead.
+OD_HD double div6_fast(double s, bool &ok) {
+    const uint64_t b = f64_bits(s);
+    const uint32_t es = (uint32_t)(b >> 52) & 0x7FFu;
+    ok = es - 4u <= 2042u;
+    const uint64_t M = (b & kFrac) | kHid;
+    const bool big = M >= (3ull << 51);
+    const uint64_t N = big ? (M << 1) : (M << 2);
+    const uint64_t Q0 = mulhi64(N, 0xAAAAAAAAAAAAAAABull) >> 1;
+    const uint32_t r = (uint32_t)N - 3u * (uint32_t)Q0;
+    const uint64_t Q = Q0 + (r == 2u ? 1u : 0u);
+    const uint64_t er = (uint64_t)(es - (big ? 2u : 3u));
+    return f64_from((b & kSign) | (((er - 1u) << 52) + Q));
+}
+
+// The Jacobi update (((((W+E)+S)+N)+D)+U)/6 in binary64 round-to-nearest,
+// as IEEE operations (the reference form, and the fallback of the fast one).
+template <bool INT_DIV>
+OD_HD double jacobi_update_ieee(double W, double E, double S, double N, double D, double U) {
+    double s = ieee_add(W, E);
+    s = ieee_add(s, S);
+    s = ieee_add(s, N);
+    s = ieee_add(s, D);
+    s = ieee_add(s, U);
+    if (INT_DIV) return div6(s);
+    return ieee_div(s, 6.0);
+}
+
+// The same update with its operations placed by AM, never changing a bit:
+//   AM = 0  every add and the division as IEEE operations (FP64 pipe)
+//   AM = 1  IEEE adds, division by 6 on the integer pipes
+//   AM = 1+k, k = 1..5: the first k adds as an unpacked integer chain, the
+//           remaining 5-k as IEEE adds, the division on the integer pipes.
+// Branch-free: ok = false when an operand or the sum left the integer
+// routines' domain; the result is then garbage and the caller recomputes the
+// cell with jacobi_update_ieee (a rare path kept out of the hot loop).
+template <int AM>
+OD_HD double jacobi_update_fast(double W, double E, double S, double N, double D, double U, bool &ok) {
+    constexpr int K = AM > 1 ? AM - 1 : 0;
+    if constexpr (AM == 0) {
+        ok = true;
+        return jacobi_update_ieee<false>(W, E, S, N, D, U);
+    } else if constexpr (K == 0) {
+        double s = ieee_add(W, E);
+        s = ieee_add(s, S);
+        s = ieee_add(s, N);
+        s = ieee_add(s, D);
+        s = ieee_add(s, U);
+        return div6_fast(s, ok);
+    } else {
+        const double x[6] = {W, E, S, N, D, U};
+        Unpacked acc, b;
+        bool good = unpack_chain(x[0], acc);
+#pragma unroll
+        for (int t = 1; t <= K; ++t) {
+            good &= unpack_chain(x[t], b);
+            acc = add_chain(acc, b);
+        }
+        if constexpr (K == 5) {
+            ok = good;
+            return div6_chain(acc);
+        } else {
+            double s = pack_chain(acc);
+#pragma unroll
+            for (int t = K + 1; t <= 5; ++t) s = ieee_add(s, x[t]);
+            bool okd;
+            const double v = div6_fast(s, okd);
+            ok = good && okd;
+            return v;
+        }
+    }
+}
+
+// Complete update in mode AM for every input (fast form, IEEE fallback).
+template <int AM>
+OD_HD double jacobi_update(double W, double E, double S, double N, double D, double U) {
+    bool ok;
+    const double v = jacobi_update_fast<AM>(W, E, S, N, D, U, ok);
+    return ok ? v : jacobi_update_ieee<false>(W, E, S, N, D, U);
+}
+
+// Run-time dispatch of jacobi_update (tests).
+OD_HD double jacobi_update_mode(int am, const double *x) {
+    switch (am) {
+        case 0: return jacobi_update<0>(x[0], x[1], x[2], x[3], x[4], x[5]);
+        case 1: return jacobi_update<1>(x[0], x[1], x[2], x[3], x[4], x[5]);
+        case 2: return jacobi_update<2>(x[0], x[1], x[2], x[3], x[4], x[5]);
+        case 3: return jacobi_update<3>(x[0], x[1], x[2], x[3], x[4], x[5]);
+        case 4: return jacobi_update<4>(x[0], x[1], x[2], x[3], x[4], x[5]);
+        case 5: return jacobi_update<5>(x[0], x[1], x[2], x[3], x[4], x[5]);
+        default: return jacobi_update<6>(x[0], x[1], x[2], x[3], x[4], x[5]);
+    }
+}
+
 }  // namespace od

@@ -2,18 +2,17 @@
 // of libod (overdecomposed 3D 7-point FP64 Jacobi on one GPU).
 //
 // Memory layout of one chare (block) in HBM, per parity p in {0,1}:
-//   A[p]   : (bz+2) planes x (by+2) rows x pitch doubles, pitch = bx rounded
-//            up to 4 (rows start 32-byte aligned).  Plane 0 / bz+1 are the
-//            z-ghost planes, row 0 / by+1 of every plane the y-ghost rows,
-//            columns [0,bx) the cells; columns [bx,pitch) are padding.
-//            Interior cell (i,j,k) is A[p][((k+1)*(by+2) + (j+1))*pitch + i].
-//   XG[p][s]: x-ghost columns kept apart (s=0: left of i=0, s=1: right of
-//            i=bx-1) as bz rows of xgp doubles, xgp = by rounded up to 2;
-//            ghost of row j, plane k at XG[p][s][k*xgp + j].
-// Keeping x-ghosts out of the rows lets a whole tile of rows (with its y-halo
-// rows) be one contiguous run, fetched by a single 1D bulk copy (TMA), and
-// keeps interior rows aligned.  Edge and corner ghost cells of the padded box
-// exist in A but are never read by a 7-point stencil.
+//   A[p] : (bz+2) planes x (by+2) rows x pitch doubles, pitch = bx+2 rounded
+//          up to 2 (every row starts 16-byte aligned).  Plane 0 / bz+1 are the
+//          z-ghost planes, row 0 / by+1 of every plane the y-ghost rows,
+//          column 0 / bx+1 of every row the x-ghost cells, columns [1,bx] the
+//          cells; a last column may be padding.
+//          Interior cell (i,j,k) is A[p][((k+1)*(by+2) + (j+1))*pitch + i+1].
+// A tile of full rows plus its two y-halo rows is then one contiguous run
+// that already holds the x-ghosts, fetched by a single 1D bulk copy (TMA),
+// and in shared memory x-1 / x+1 are the neighbouring words for every cell.
+// Edge and corner ghost cells of the padded box exist but are never read by
+// a 7-point stencil.
 //
 // A neighbour "delivers" a face by storing straight into these ghost cells
 // (the chare's mailbox).  Faces on the domain boundary hold the Dirichlet
@@ -36,12 +35,10 @@
 struct ChareDev {
     int32_t bx, by, bz;     // interior extents
     int32_t pitch;          // row stride of A, doubles
-    int32_t xgp;            // row stride of XG, doubles
     int32_t nbr[6];         // neighbour per face or -1 (Dirichlet)
     int32_t foff[7];        // face offsets inside send/recv buffers (doubles)
     int64_t x0, y0, z0;     // global interior offset of cell (0,0,0)
     double *A[2];
-    double *XG[2][2];       // [parity][side]
     double *send;           // per-chare path: packed new faces
     double *recv[2];        // per-chare path: faces from neighbours, 2 slots
 };

@@ -53,89 +53,83 @@ __device__ __forceinline__ double field_init(int64_t gx, int64_t gy, int64_t gz,
     return field_uniform(seed, (uint64_t)(gx + (nx + 2) * (gy + (ny + 2) * gz)));
 }
 
+// Classify element e of a chare's padded array: returns false for padding
+// and for edge/corner ghosts (never read), else the padded global
+// coordinates of the cell it holds.
+__device__ __forceinline__ bool padded_cell(const ChareDev &C, int64_t e, int64_t *gx, int64_t *gy,
+                                            int64_t *gz) {
+    const int col = (int)(e % C.pitch);
+    const int64_t row = e / C.pitch;
+    const int jp = (int)(row % (C.by + 2)), kp = (int)(row / (C.by + 2));
+    if (col > C.bx + 1) return false;
+    const int ghosts = (col == 0 || col == C.bx + 1) + (jp == 0 || jp == C.by + 1) + (kp == 0 || kp == C.bz + 1);
+    if (ghosts > 1) return false;
+    *gx = C.x0 + col;
+    *gy = C.y0 + jp;
+    *gz = C.z0 + kp;
+    return true;
+}
+
+// A2: the initial field in both parities, interior and every ghost cell.
 __global__ void k_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
                        int mode) {
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
         const int64_t na = (int64_t)(C.bz + 2) * (C.by + 2) * C.pitch;
-        const int64_t nxg = (int64_t)C.bz * C.xgp;
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na + 2 * nxg;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na;
              e += (int64_t)gridDim.x * blockDim.x) {
+            int64_t gx, gy, gz;
             double v = 0.0;
-            if (e < na) {
-                const int i = (int)(e % C.pitch);
-                const int64_t row = e / C.pitch;
-                const int jp = (int)(row % (C.by + 2)), kp = (int)(row / (C.by + 2));
-                const bool yg = jp == 0 || jp == C.by + 1, zg = kp == 0 || kp == C.bz + 1;
-                if (i < C.bx && !(yg && zg))
-                    v = field_init(C.x0 + i + 1, C.y0 + jp, C.z0 + kp, nx, ny, nz, seed, mode);
-                C.A[0][e] = v;
-                C.A[1][e] = v;
-            } else {
-                int64_t e2 = e - na;
-                const int side = e2 >= nxg ? 1 : 0;
-                e2 -= side * nxg;
-                const int j = (int)(e2 % C.xgp), k = (int)(e2 / C.xgp);
-                if (j < C.by)
-                    v = field_init(side ? C.x0 + C.bx + 1 : C.x0, C.y0 + j + 1, C.z0 + k + 1, nx, ny, nz, seed,
-                                   mode);
-                C.XG[0][side][e2] = v;
-                C.XG[1][side][e2] = v;
-            }
+            if (padded_cell(C, e, &gx, &gy, &gz)) v = field_init(gx, gy, gz, nx, ny, nz, seed, mode);
+            C.A[0][e] = v;
+            C.A[1][e] = v;
         }
     }
+}
+
+// Offset in A of face element q of face f: `ghost` = false gives the
+// chare's own boundary cell (pack), true the ghost cell facing it (unpack).
+__device__ __forceinline__ int64_t face_offset(const ChareDev &C, int f, int q, bool ghost) {
+    const int bx = C.bx, by = C.by, bz = C.bz, pitch = C.pitch;
+    const int64_t plane = (int64_t)(by + 2) * pitch;
+    if (f < 2) {
+        const int k = q / by, j = q - k * by;
+        const int col = f == OD_FACE_XLO ? (ghost ? 0 : 1) : (ghost ? bx + 1 : bx);
+        return (k + 1) * plane + (int64_t)(j + 1) * pitch + col;
+    }
+    if (f < 4) {
+        const int k = q / bx, i = q - k * bx;
+        const int row = f == OD_FACE_YLO ? (ghost ? 0 : 1) : (ghost ? by + 1 : by);
+        return (k + 1) * plane + (int64_t)row * pitch + i + 1;
+    }
+    const int j = q / bx, i = q - j * bx;
+    const int pl = f == OD_FACE_ZLO ? (ghost ? 0 : 1) : (ghost ? bz + 1 : bz);
+    return (int64_t)pl * plane + (int64_t)(j + 1) * pitch + i + 1;
 }
 
 // Per-chare path, A4: new boundary planes of parity p -> contiguous send
 // buffer (faces with a neighbour only).
 __global__ void k_pack(const ChareDev *ch, int c, int p) {
     const ChareDev &C = ch[c];
-    const int bx = C.bx, by = C.by, bz = C.bz, pitch = C.pitch;
-    const int64_t plane = (int64_t)(by + 2) * pitch;
     const double *A = C.A[p];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.foff[6]; e += gridDim.x * blockDim.x) {
         int f = 0;
         while (e >= C.foff[f + 1]) ++f;
         if (C.nbr[f] < 0) continue;
-        const int q = e - C.foff[f];
-        int64_t o;
-        if (f < 2) {
-            const int k = q / by, j = q - k * by;
-            o = (k + 1) * plane + (int64_t)(j + 1) * pitch + (f == OD_FACE_XLO ? 0 : bx - 1);
-        } else if (f < 4) {
-            const int k = q / bx, i = q - k * bx;
-            o = (k + 1) * plane + (int64_t)(f == OD_FACE_YLO ? 1 : by) * pitch + i;
-        } else {
-            const int j = q / bx, i = q - j * bx;
-            o = (int64_t)(f == OD_FACE_ZLO ? 1 : bz) * plane + (int64_t)(j + 1) * pitch + i;
-        }
-        C.send[e] = A[o];
+        C.send[e] = A[face_offset(C, f, e - C.foff[f], false)];
     }
 }
 
 // Per-chare path, A6: receive slot -> ghost layers of parity p.
 __global__ void k_unpack(const ChareDev *ch, int c, int p, int slot) {
     const ChareDev &C = ch[c];
-    const int bx = C.bx, by = C.by, bz = C.bz, pitch = C.pitch, xgp = C.xgp;
-    const int64_t plane = (int64_t)(by + 2) * pitch;
     double *A = C.A[p];
     const double *R = C.recv[slot];
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.foff[6]; e += gridDim.x * blockDim.x) {
         int f = 0;
         while (e >= C.foff[f + 1]) ++f;
         if (C.nbr[f] < 0) continue;
-        const int q = e - C.foff[f];
-        const double v = R[e];
-        if (f < 2) {
-            const int k = q / by, j = q - k * by;
-            C.XG[p][f][(int64_t)k * xgp + j] = v;
-        } else if (f < 4) {
-            const int k = q / bx, i = q - k * bx;
-            A[(k + 1) * plane + (int64_t)(f == OD_FACE_YLO ? 0 : by + 1) * pitch + i] = v;
-        } else {
-            const int j = q / bx, i = q - j * bx;
-            A[(int64_t)(f == OD_FACE_ZLO ? 0 : bz + 1) * plane + (int64_t)(j + 1) * pitch + i] = v;
-        }
+        A[face_offset(C, f, e - C.foff[f], true)] = R[e];
     }
 }
 
@@ -151,52 +145,31 @@ __global__ void k_gather(const ChareDev *ch, int nch, int p, int64_t nx, int64_t
             const int64_t r = e / C.bx;
             const int j = (int)(r % C.by), k = (int)(r / C.by);
             g[(C.z0 + k) * ny * nx + (C.y0 + j) * nx + C.x0 + i] =
-                C.A[p][(k + 1) * plane + (int64_t)(j + 1) * C.pitch + i];
+                C.A[p][(k + 1) * plane + (int64_t)(j + 1) * C.pitch + i + 1];
         }
     }
 }
 
-// Import: global x-fastest interior -> interiors and internal ghost layers of
+// Import: global x-fastest interior -> interiors and internal ghost cells of
 // parity p (Dirichlet ghosts keep the shell).
 __global__ void k_scatter(const ChareDev *ch, int nch, int p, int64_t nx, int64_t ny, int64_t nz,
                           const double *g) {
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
         const int64_t na = (int64_t)(C.bz + 2) * (C.by + 2) * C.pitch;
-        const int64_t nxg = (int64_t)C.bz * C.xgp;
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na + 2 * nxg;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na;
              e += (int64_t)gridDim.x * blockDim.x) {
             int64_t gx, gy, gz;
-            if (e < na) {
-                const int i = (int)(e % C.pitch);
-                const int64_t row = e / C.pitch;
-                const int jp = (int)(row % (C.by + 2)), kp = (int)(row / (C.by + 2));
-                const bool yg = jp == 0 || jp == C.by + 1, zg = kp == 0 || kp == C.bz + 1;
-                if (i >= C.bx || (yg && zg)) continue;
-                gx = C.x0 + i + 1; gy = C.y0 + jp; gz = C.z0 + kp;
-            } else {
-                int64_t e2 = e - na;
-                const int side = e2 >= nxg ? 1 : 0;
-                e2 -= side * nxg;
-                const int j = (int)(e2 % C.xgp), k = (int)(e2 / C.xgp);
-                if (j >= C.by) continue;
-                gx = side ? C.x0 + C.bx + 1 : C.x0; gy = C.y0 + j + 1; gz = C.z0 + k + 1;
-            }
+            if (!padded_cell(C, e, &gx, &gy, &gz)) continue;
             if (gx == 0 || gy == 0 || gz == 0 || gx == nx + 1 || gy == ny + 1 || gz == nz + 1) continue;
-            const double v = g[(gz - 1) * ny * nx + (gy - 1) * nx + (gx - 1)];
-            if (e < na) {
-                C.A[p][e] = v;
-            } else {
-                int64_t e2 = e - na;
-                const int side = e2 >= nxg ? 1 : 0;
-                C.XG[p][side][e2 - side * nxg] = v;
-            }
+            C.A[p][e] = g[(gz - 1) * ny * nx + (gy - 1) * nx + (gx - 1)];
         }
     }
 }
 
 // Arithmetic self-test: op 0 div6, 1 add (integer pipes); 2 division by 6,
-// 3 add (FP64 pipe).
+// 3 add (FP64 pipe); 10+m the whole Jacobi update in arithmetic mode m over
+// six operands per element (a[6i .. 6i+5]).
 __global__ void k_arith(int op, const double *a, const double *b, double *out, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double r;
@@ -204,7 +177,8 @@ __global__ void k_arith(int op, const double *a, const double *b, double *out, i
             case 0: r = div6(a[i]); break;
             case 1: r = add(a[i], b[i]); break;
             case 2: r = __ddiv_rn(a[i], 6.0); break;
-            default: r = __dadd_rn(a[i], b[i]); break;
+            case 3: r = __dadd_rn(a[i], b[i]); break;
+            default: r = jacobi_update_mode(op - 10, a + 6 * i); break;
         }
         out[i] = r;
     }

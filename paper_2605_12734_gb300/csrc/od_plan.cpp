@@ -17,8 +17,8 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int32_t kMaxSmem = 232448;  // 227 KB opt-in per CTA on sm_100/sm_103
-constexpr int32_t kSmemHeader = 128;  // mbarriers + ticket slot
-constexpr int32_t kDefaultArith = 1;   // integer-pipe division, FP64 adds
+constexpr int32_t kSmemHeader = 256;  // mbarriers + neighbour push table
+constexpr int32_t kDefaultArith = 2;   // first add and the division on the integer pipes
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int32_t round_up(int32_t v, int32_t a) { return (v + a - 1) / a * a; }
@@ -101,9 +101,7 @@ void balanced_parts(int32_t n, int32_t cap, std::vector<int32_t> *starts, std::v
 }  // namespace
 
 int32_t stage_doubles_for(int32_t nj, int32_t pitch) {
-    int32_t rows = (nj + 2) * pitch;           // tile rows + the two y-halo rows
-    int32_t xg = round_up(nj + 2, 2);          // one x-ghost slot (16-byte aligned span)
-    return round_up(rows + 2 * xg, 16);        // keep stages 128-byte aligned
+    return round_up((nj + 2) * pitch, 16);     // keep slots 128-byte aligned
 }
 
 od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
@@ -123,8 +121,9 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         *err = "unknown path";
         return OD_EINVAL;
     }
-    p.threads = cfg->threads ? cfg->threads : 256;
+    p.threads = cfg->threads ? cfg->threads : 128;
     p.cpt = cfg->cells_per_thread ? cfg->cells_per_thread : 4;
+    const bool auto_shape = cfg->threads == 0 && cfg->cells_per_thread == 0;
     p.stages = cfg->stages ? cfg->stages : 4;
     p.tile_y = cfg->tile_y;
     p.tile_z = cfg->tile_z;
@@ -143,8 +142,8 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         *err = "supported (threads, cells_per_thread): 128 x {2,4,8}, 256 x {1,2,4,8}, 512 x {1,2}";
         return OD_EINVAL;
     }
-    if (p.stages < 2 || p.stages > 8) {
-        *err = "stages must be in [2, 8]";
+    if (p.stages < 3 || p.stages > 8) {
+        *err = "stages must be in [3, 8]";
         return OD_EINVAL;
     }
     if (p.tile_y < 0 || p.tile_z < 0) {
@@ -163,6 +162,21 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
     if (nch > (1ll << 24)) {
         *err = "more than 2^24 chares";
         return OD_EINVAL;
+    }
+    if (auto_shape) {
+        // smallest CTA shape that holds two rows of the widest chare (one if
+        // none does): 128 x 4, 256 x 4, 256 x 8 cells
+        int64_t wmax = 0;
+        for (int64_t e = 1; e < (int64_t)p.ex.size(); ++e) wmax = std::max(wmax, p.ex[e] - p.ex[e - 1]);
+        const int32_t shapes[3][2] = {{128, 4}, {256, 4}, {256, 8}};
+        int pick = 2;
+        for (int i = 2; i >= 0; --i)
+            if ((int64_t)shapes[i][0] * shapes[i][1] >= 2 * wmax) pick = i;
+        if ((int64_t)shapes[pick][0] * shapes[pick][1] < 2 * wmax)
+            for (int i = 2; i >= 0; --i)
+                if ((int64_t)shapes[i][0] * shapes[i][1] >= wmax) pick = i;
+        p.threads = shapes[pick][0];
+        p.cpt = shapes[pick][1];
     }
     for (int64_t e = 1; e < (int64_t)p.ex.size(); ++e)
         if (p.ex[e] - p.ex[e - 1] > (int64_t)p.threads * p.cpt) {
@@ -186,8 +200,7 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
                 h.x0 = p.ex[cx]; h.bx = (int32_t)(p.ex[cx + 1] - p.ex[cx]);
                 h.y0 = p.ey[cy]; h.by = (int32_t)(p.ey[cy + 1] - p.ey[cy]);
                 h.z0 = p.ez[cz]; h.bz = (int32_t)(p.ez[cz + 1] - p.ez[cz]);
-                h.pitch = round_up(h.bx, 4);
-                h.xgp = round_up(h.by, 2);
+                h.pitch = round_up(h.bx + 2, 2);
                 h.nbr[OD_FACE_XLO] = cx > 0 ? (int32_t)(c - 1) : -1;
                 h.nbr[OD_FACE_XHI] = cx < p.px - 1 ? (int32_t)(c + 1) : -1;
                 h.nbr[OD_FACE_YLO] = cy > 0 ? (int32_t)(c - p.px) : -1;
@@ -238,6 +251,12 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         h.tile_end = (int32_t)p.tiles.size();
     }
     p.stage_doubles = max_stage;
+    // the tile kernels pack a cell's ring offset into 16 bits and its tile row
+    // into 11 bits
+    if (p.stage_doubles >= 65536 || p.max_nj > 2048) {
+        *err = "tile too large for the kernels' cell encoding; lower tile_y";
+        return OD_EINVAL;
+    }
     int64_t smem = kSmemHeader + (int64_t)p.stages * p.stage_doubles * 8;
     if (smem > kMaxSmem) {
         char buf[200];
@@ -286,11 +305,8 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
     p.off_order = take(p.order.size() * sizeof(int32_t));
     for (auto &h : p.ch) {
         size_t a_bytes = (size_t)(h.bz + 2) * (size_t)(h.by + 2) * (size_t)h.pitch * 8;
-        size_t xg_bytes = (size_t)h.bz * (size_t)h.xgp * 8;
         size_t f_bytes = (size_t)h.foff[6] * 8;
         for (int s = 0; s < 2; ++s) h.offA[s] = take(a_bytes);
-        for (int s = 0; s < 2; ++s)
-            for (int d = 0; d < 2; ++d) h.offXG[s][d] = take(xg_bytes);
         h.offSend = take(f_bytes);
         h.offRecv[0] = take(f_bytes);
         h.offRecv[1] = take(f_bytes);

@@ -15,11 +15,10 @@ namespace od {
 struct HostChare {
     int32_t cx, cy, cz;
     int64_t x0, y0, z0;
-    int32_t bx, by, bz, pitch, xgp;
+    int32_t bx, by, bz, pitch;
     int32_t nbr[6];
     int32_t foff[7];
     size_t offA[2];
-    size_t offXG[2][2];
     size_t offSend, offRecv[2];
     int32_t tile_begin, tile_end;   // tiles [begin,end) belong to this chare
 };
@@ -49,8 +48,8 @@ struct Plan {
 // Build the full plan; returns OD_OK or OD_EINVAL with *err set.
 od_status build_plan(const od_config *cfg, Plan *plan, std::string *err);
 
-// Stage bytes of the TMA ring for a tile of `nj` rows in a chare of pitch
-// `pitch` (rows incl. 2 halo rows + two x-ghost slots), in doubles.
+// Ring-slot size for a tile of `nj` rows in a chare of row pitch `pitch`
+// (the rows plus the two y-halo rows), in doubles.
 int32_t stage_doubles_for(int32_t nj, int32_t pitch);
 
 // Fill plan->info.

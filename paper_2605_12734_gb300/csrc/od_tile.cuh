@@ -114,24 +114,14 @@ __device__ __forceinline__ void record_err(ErrDev *e, int code, int tile, int st
 
 // ---------------------------------------------------------------- update
 
-// The Jacobi update (((((W+E)+S)+N)+D)+U)/6 in binary64 round-to-nearest.
-// AM selects where the operations run, never what they compute:
-//   AM = 0  every add and the division on the FP64 pipe (__dadd_rn, __ddiv_rn)
-//   AM = 1  adds on the FP64 pipe, division by 6 on the integer pipes
-//   AM = 1+k, k = 1..5: additionally the first k adds on the integer pipes
-// (od_arith.cuh; identical bits for every input).
-template <int AM>
-__device__ __forceinline__ double jacobi_update(double W, double E, double S, double N, double D, double U) {
-    constexpr int NE = AM > 1 ? AM - 1 : 0;
-    double s = NE >= 1 ? add(W, E) : __dadd_rn(W, E);
-    s = NE >= 2 ? add(s, S) : __dadd_rn(s, S);
-    s = NE >= 3 ? add(s, N) : __dadd_rn(s, N);
-    s = NE >= 4 ? add(s, D) : __dadd_rn(s, D);
-    s = NE >= 5 ? add(s, U) : __dadd_rn(s, U);
-    return AM >= 1 ? div6(s) : __ddiv_rn(s, 6.0);
-}
-
 // ---------------------------------------------------------------- tile sweep
+
+// IEEE form of the update for the rare cells whose operands leave the
+// integer routines' domain.  Kept out of line so the compiler cannot merge it
+// with (or speculate it beside) the fast form in the hot loop.
+static __device__ __noinline__ double update_slow(double W, double E, double S, double N, double D, double U) {
+    return jacobi_update_ieee<false>(W, E, S, N, D, U);
+}
 
 struct Ring {
     double *base;      // first slot
@@ -139,26 +129,45 @@ struct Ring {
     uint32_t seq;      // planes issued by this CTA before the current tile
 };
 
+// Where a tile's boundary values go (the neighbours' ghost cells of the
+// destination parity), prepared once per tile by thread 0 in shared memory.
+// For a cell with ring-slot offset r in tile row j and plane k:
+//   x-: xlo + (k+1)*xlo_plane + (j+1)*xlo_pitch    x+: same with xhi
+//   y-: ylo + (k+1)*ylo_plane + r                  y+: same with yhi
+//   z-: zlo + r (plane k == 0)                      z+: zhi + r (k == bz-1)
+struct PushInfo {
+    double *xlo, *xhi, *ylo, *yhi, *zlo, *zhi;
+    int32_t xlo_pitch, xlo_plane, xhi_pitch, xhi_plane, ylo_plane, yhi_plane;
+};
+
+constexpr int kSmemBars = 0;     // up to 8 mbarriers
+constexpr int kSmemPush = 64;    // PushInfo
+constexpr int kSmemRing = 256;   // first ring slot (matches the planner's header)
+static_assert(sizeof(PushInfo) <= kSmemRing - kSmemPush, "push info overflows the header");
+
+// Per-cell word: bits 0-15 ring-slot offset r of the cell, 16-26 tile row j,
+// 27 the slot holds a real cell (its result is stored), 28/29/30/31 the cell
+// lies on a face with an x-/x+/y-/y+ neighbour.
+constexpr uint32_t kValid = 1u << 27;
+constexpr uint32_t kXlo = 1u << 28, kXhi = 1u << 29, kYlo = 1u << 30, kYhi = 1u << 31;
+
 // Sweep one tile from parity sp into parity sp^1.  Returns false (all
 // threads agree) if a wait ran out; the error is recorded and thread 0 has
 // waited, bounded, for the copies this tile still had in flight.
 template <int NT, int CPT, bool PUSH, int AM>
-__device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ring &ring, int step) {
+__device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ring &ring, PushInfo *pi,
+                                         int step) {
     const TileDev T = a.tiles[tile_id];
     const ChareDev &C = a.ch[T.c];
-    const int bx = C.bx, by = C.by, bz = C.bz, pitch = C.pitch, xgp = C.xgp;
+    const int bx = C.bx, by = C.by, bz = C.bz, pitch = C.pitch;
     const int plane = (by + 2) * pitch;
     const int dp = sp ^ 1;
-    const double *__restrict__ src = C.A[sp];
-    double *__restrict__ dst = C.A[dp];
-    const double *xlo_src = C.XG[sp][0];
-    const double *xhi_src = C.XG[sp][1];
-    const int rows_d = (T.nj + 2) * pitch;            // doubles of one plane's rows
-    const int xj0 = T.j0 & ~1;                        // 16-byte aligned start
-    const int xcnt = ((T.j0 + T.nj + 1) & ~1) - xj0;  // even count covering [j0, j0+nj)
-    const int xoff = T.j0 - xj0;
+    // row j0 (the tile's lower y-halo row) of plane 0; plane p+1 holds interior plane p
+    const double *__restrict__ src = C.A[sp] + (size_t)T.j0 * pitch;
+    double *__restrict__ dst = C.A[dp] + (size_t)T.j0 * pitch;
+    const uint32_t run_bytes = (uint32_t)((T.nj + 2) * pitch) * 8u;  // one plane's rows
     const int S = a.stages, SD = a.stage_doubles;
-    const int kb = T.k0 - 1, ke = T.k0 + T.nk;        // planes kb..ke are loaded
+    const int kb = T.k0 - 1, ke = T.k0 + T.nk;  // planes kb..ke are loaded
     const int tid = threadIdx.x;
     const uint32_t seq0 = ring.seq;
 
@@ -168,118 +177,128 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     auto phase = [&](int p) -> uint32_t { return ((seq0 + (uint32_t)(p - kb)) / (uint32_t)S) & 1u; };
     auto issue = [&](int p) {
         const uint32_t s = slot(p);
-        double *sb = ring.base + (size_t)s * SD;
         uint64_t *bar = ring.bars + s;
-        const bool xg = (p >= 0 && p < bz);
-        const uint32_t rb = (uint32_t)rows_d * 8u, xb = (uint32_t)xcnt * 8u;
-        mbar_expect_tx(bar, rb + (xg ? 2u * xb : 0u));
-        bulk_g2s(sb, src + (size_t)(p + 1) * plane + (size_t)T.j0 * pitch, rb, bar);
-        if (xg) {
-            bulk_g2s(sb + rows_d, xlo_src + (size_t)p * xgp + xj0, xb, bar);
-            bulk_g2s(sb + rows_d + xcnt, xhi_src + (size_t)p * xgp + xj0, xb, bar);
-        }
+        mbar_expect_tx(bar, run_bytes);
+        bulk_g2s(ring.base + (size_t)s * SD, src + (size_t)(p + 1) * plane, run_bytes, bar);
     };
     int issued_hi = kb - 1;  // highest plane issued so far (same value in every thread)
+    // (a ring of S slots holds planes k-1, k, k+1 and S-3 planes in flight)
     auto drain = [&](int from) {
         if (tid == 0)
             for (int p = from; p <= issued_hi; ++p) mbar_wait_bounded(ring.bars + slot(p), phase(p), a.spin_ns);
         ring.seq = seq0 + (uint32_t)(issued_hi - kb + 1);
     };
 
-    // cells of this thread: plane-local (j, i) for q = tid + m*NT
-    const int ncell = T.nj * bx;
-    int cj[CPT], ci[CPT];
-#pragma unroll
-    for (int m = 0; m < CPT; ++m) {
-        const int q = tid + m * NT;
-        cj[m] = q / bx;
-        ci[m] = q - cj[m] * bx;
-    }
-
-    // neighbour mailboxes (ghost layers of parity dp) for the fused paths
-    double *nb_xlo = nullptr, *nb_xhi = nullptr, *nb_ylo = nullptr, *nb_yhi = nullptr;
-    double *nb_zlo = nullptr, *nb_zhi = nullptr;
-    int plane_ylo = 0, plane_yhi = 0;
-    if (PUSH) {
-        if (C.nbr[OD_FACE_XLO] >= 0) nb_xlo = a.ch[C.nbr[OD_FACE_XLO]].XG[dp][1] + T.j0;
-        if (C.nbr[OD_FACE_XHI] >= 0) nb_xhi = a.ch[C.nbr[OD_FACE_XHI]].XG[dp][0] + T.j0;
-        if (C.nbr[OD_FACE_YLO] >= 0) {
-            const ChareDev &N = a.ch[C.nbr[OD_FACE_YLO]];
-            plane_ylo = (N.by + 2) * pitch;
-            nb_ylo = N.A[dp] + (size_t)(N.by + 1) * pitch;
-        }
-        if (C.nbr[OD_FACE_YHI] >= 0) {
-            const ChareDev &N = a.ch[C.nbr[OD_FACE_YHI]];
-            plane_yhi = (N.by + 2) * pitch;
-            nb_yhi = N.A[dp];
-        }
-        if (C.nbr[OD_FACE_ZLO] >= 0) {
-            const ChareDev &N = a.ch[C.nbr[OD_FACE_ZLO]];
-            nb_zlo = N.A[dp] + (size_t)(N.bz + 1) * plane;
-        }
-        if (C.nbr[OD_FACE_ZHI] >= 0) nb_zhi = a.ch[C.nbr[OD_FACE_ZHI]].A[dp];
-    }
-
     if (tid == 0) {
         const int last = min(ke, kb + S - 1);
         for (int p = kb; p <= last; ++p) issue(p);
+        if (PUSH) {
+            PushInfo q;
+            q.xlo = q.xhi = q.ylo = q.yhi = q.zlo = q.zhi = nullptr;
+            q.xlo_pitch = q.xlo_plane = q.xhi_pitch = q.xhi_plane = q.ylo_plane = q.yhi_plane = 0;
+            if (C.nbr[OD_FACE_XLO] >= 0) {
+                const ChareDev &N = a.ch[C.nbr[OD_FACE_XLO]];
+                q.xlo_pitch = N.pitch;
+                q.xlo_plane = (N.by + 2) * N.pitch;
+                q.xlo = N.A[dp] + (size_t)T.j0 * N.pitch + (N.bx + 1);
+            }
+            if (C.nbr[OD_FACE_XHI] >= 0) {
+                const ChareDev &N = a.ch[C.nbr[OD_FACE_XHI]];
+                q.xhi_pitch = N.pitch;
+                q.xhi_plane = (N.by + 2) * N.pitch;
+                q.xhi = N.A[dp] + (size_t)T.j0 * N.pitch;
+            }
+            if (C.nbr[OD_FACE_YLO] >= 0) {  // cell row 0 -> its ghost row by_n+1
+                const ChareDev &N = a.ch[C.nbr[OD_FACE_YLO]];
+                q.ylo_plane = (N.by + 2) * pitch;
+                q.ylo = N.A[dp] + (size_t)N.by * pitch;
+            }
+            if (C.nbr[OD_FACE_YHI] >= 0) {  // cell row by-1 -> its ghost row 0
+                const ChareDev &N = a.ch[C.nbr[OD_FACE_YHI]];
+                q.yhi_plane = (N.by + 2) * pitch;
+                q.yhi = N.A[dp] - (ptrdiff_t)(by - T.j0) * pitch;
+            }
+            if (C.nbr[OD_FACE_ZLO] >= 0) {  // plane 0 -> its ghost plane bz_n+1
+                const ChareDev &N = a.ch[C.nbr[OD_FACE_ZLO]];
+                q.zlo = N.A[dp] + (size_t)(N.bz + 1) * plane + (size_t)T.j0 * pitch;
+            }
+            if (C.nbr[OD_FACE_ZHI] >= 0) q.zhi = a.ch[C.nbr[OD_FACE_ZHI]].A[dp] + (size_t)T.j0 * pitch;
+            *pi = q;
+        }
     }
     issued_hi = min(ke, kb + S - 1);
 
-    double down[CPT], cur[CPT];
+    // this thread's cells: q = tid + m*NT in the tile plane, row-major.  A slot
+    // past the end of the tile repeats the tile's first cell and stores
+    // nothing, so the cell loop needs no validity branch.
+    const int ncell = T.nj * bx;
+    uint32_t rf[CPT];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+        const int q0 = tid + m * NT;
+        const bool valid = q0 < ncell;
+        const int q = valid ? q0 : 0;
+        const int j = q / bx, i = q - j * bx, gj = T.j0 + j;
+        uint32_t w = (uint32_t)((j + 1) * pitch + i + 1) | ((uint32_t)j << 16);
+        if (valid) {
+            w |= kValid;
+            if (PUSH) {
+                if (i == 0 && C.nbr[OD_FACE_XLO] >= 0) w |= kXlo;
+                if (i == bx - 1 && C.nbr[OD_FACE_XHI] >= 0) w |= kXhi;
+                if (gj == 0 && C.nbr[OD_FACE_YLO] >= 0) w |= kYlo;
+                if (gj == by - 1 && C.nbr[OD_FACE_YHI] >= 0) w |= kYhi;
+            }
+        }
+        rf[m] = w;
+    }
+
+    // Planes k-1, k and k+1 must be resident while plane k is computed (the
+    // z-1 value is read from the ring, not kept in registers), so a slot is
+    // refilled once the plane after next has been computed.
     bool fail = !mbar_wait_bounded(ring.bars + slot(kb), phase(kb), a.spin_ns);
-    if (!fail) {
-        const double *sb = ring.base + (size_t)slot(kb) * SD;
-#pragma unroll
-        for (int m = 0; m < CPT; ++m)
-            if (tid + m * NT < ncell) down[m] = sb[(cj[m] + 1) * pitch + ci[m]];
-        fail = !mbar_wait_bounded(ring.bars + slot(kb + 1), phase(kb + 1), a.spin_ns);
-    }
-    if (!fail) {
-        const double *sb = ring.base + (size_t)slot(kb + 1) * SD;
-#pragma unroll
-        for (int m = 0; m < CPT; ++m)
-            if (tid + m * NT < ncell) cur[m] = sb[(cj[m] + 1) * pitch + ci[m]];
-    }
+    if (!fail) fail = !mbar_wait_bounded(ring.bars + slot(kb + 1), phase(kb + 1), a.spin_ns);
     if (__syncthreads_or(fail)) {
         if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
         drain(kb);
         return false;
     }
-    if (kb + S <= ke) {
-        if (tid == 0) issue(kb + S);
-        issued_hi = kb + S;
-    }
 
     for (int k = T.k0; k < ke; ++k) {
         fail = !mbar_wait_bounded(ring.bars + slot(k + 1), phase(k + 1), a.spin_ns);
         if (!fail) {
+            const double *sd = ring.base + (size_t)slot(k - 1) * SD;
             const double *sc = ring.base + (size_t)slot(k) * SD;
             const double *su = ring.base + (size_t)slot(k + 1) * SD;
-            const double *xl = sc + rows_d + xoff;
-            const double *xh = sc + rows_d + xcnt + xoff;
-            double *dplane = dst + (size_t)(k + 1) * plane + (size_t)(T.j0 + 1) * pitch;
+            double *dpl = dst + (size_t)(k + 1) * plane;
+            double *zp0 = nullptr, *zp1 = nullptr;
+            if (PUSH) {
+                if (k == 0) zp0 = pi->zlo;
+                if (k == bz - 1) zp1 = pi->zhi;
+            }
 #pragma unroll
             for (int m = 0; m < CPT; ++m) {
-                if (tid + m * NT < ncell) {
-                    const int j = cj[m], i = ci[m];
-                    const int r = (j + 1) * pitch + i;
-                    const double up = su[r];
-                    const double W = (i > 0) ? sc[r - 1] : xl[j];
-                    const double E = (i < bx - 1) ? sc[r + 1] : xh[j];
-                    const double v = jacobi_update<AM>(W, E, sc[r - pitch], sc[r + pitch], down[m], up);
-                    dplane[(size_t)j * pitch + i] = v;
+                const uint32_t w = rf[m];
+                const int r = (int)(w & 0xFFFFu);
+                bool ok;
+                double v = jacobi_update_fast<AM>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r],
+                                                  ok);
+                if (!ok)  // rare: an operand left the integer routines' domain
+                    v = update_slow(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r]);
+                if (w & kValid) {
+                    dpl[r] = v;
                     if (PUSH) {
-                        const int gj = T.j0 + j;
-                        if (i == 0 && nb_xlo) nb_xlo[(size_t)k * xgp + j] = v;
-                        if (i == bx - 1 && nb_xhi) nb_xhi[(size_t)k * xgp + j] = v;
-                        if (gj == 0 && nb_ylo) nb_ylo[(size_t)(k + 1) * plane_ylo + i] = v;
-                        if (gj == by - 1 && nb_yhi) nb_yhi[(size_t)(k + 1) * plane_yhi + i] = v;
-                        if (k == 0 && nb_zlo) nb_zlo[(size_t)(gj + 1) * pitch + i] = v;
-                        if (k == bz - 1 && nb_zhi) nb_zhi[(size_t)(gj + 1) * pitch + i] = v;
+                        if (w >> 28) {
+                            const int j1 = (int)((w >> 16) & 0x7FFu) + 1;
+                            if (w & kXlo)
+                                pi->xlo[(size_t)(k + 1) * pi->xlo_plane + (size_t)j1 * pi->xlo_pitch] = v;
+                            if (w & kXhi)
+                                pi->xhi[(size_t)(k + 1) * pi->xhi_plane + (size_t)j1 * pi->xhi_pitch] = v;
+                            if (w & kYlo) pi->ylo[(size_t)(k + 1) * pi->ylo_plane + r] = v;
+                            if (w & kYhi) pi->yhi[(size_t)(k + 1) * pi->yhi_plane + r] = v;
+                        }
+                        if (zp0) zp0[r] = v;
+                        if (zp1) zp1[r] = v;
                     }
-                    down[m] = cur[m];
-                    cur[m] = up;
                 }
             }
         }
@@ -288,9 +307,10 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
             drain(k + 1);
             return false;
         }
-        if (k + S <= ke) {
-            if (tid == 0) issue(k + S);
-            issued_hi = k + S;
+        // plane k-1 is no longer needed: refill its slot
+        if (k - 1 + S <= ke) {
+            if (tid == 0) issue(k - 1 + S);
+            issued_hi = k - 1 + S;
         }
     }
     ring.seq = seq0 + (uint32_t)(ke - kb + 1);
@@ -300,8 +320,8 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
 template <int NT>
 __device__ __forceinline__ Ring ring_setup(const KArgs &a, unsigned char *smem) {
     Ring r;
-    r.bars = reinterpret_cast<uint64_t *>(smem);
-    r.base = reinterpret_cast<double *>(smem + 128);
+    r.bars = reinterpret_cast<uint64_t *>(smem + kSmemBars);
+    r.base = reinterpret_cast<double *>(smem + kSmemRing);
     r.seq = 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) mbar_init(r.bars + s, 1);
@@ -320,7 +340,8 @@ __global__ void __launch_bounds__(NT) k_tiles(const KArgs a) {
         return;
     }
     Ring ring = ring_setup<NT>(a, smem);
-    run_tile<NT, CPT, PUSH, AM>(a, a.tile_begin + (int)blockIdx.x, a.parity, ring, -1);
+    run_tile<NT, CPT, PUSH, AM>(a, a.tile_begin + (int)blockIdx.x, a.parity, ring,
+                                reinterpret_cast<PushInfo *>(smem + kSmemPush), -1);
 }
 
 // Persistent kernel: CTAs take tickets in step-major order; ticket
@@ -373,7 +394,9 @@ __global__ void __launch_bounds__(NT) k_persistent(const KArgs a) {
             fence_proxy_async();
         }
         if (!__syncthreads_and(ok)) break;
-        if (!run_tile<NT, CPT, true, AM>(a, tile, step & 1, ring, step)) break;
+        if (!run_tile<NT, CPT, true, AM>(a, tile, step & 1, ring, reinterpret_cast<PushInfo *>(smem + kSmemPush),
+                                         step))
+            break;
         if (threadIdx.x == 0 && (int64_t)tile != a.stall_tile) {
             __threadfence();
             st_release(a.epoch + tile, r + 1);

@@ -76,6 +76,16 @@ def test_decompose_uneven_cuts_and_neighbours(od):
     assert int(np.sum(box[:, 1] * box[:, 3] * box[:, 5])) == w.cells
 
 
+def test_auto_cta_shape(od):
+    def shape(*dims, **kw):
+        i = od.plan(*dims, **kw)
+        return i["threads"], i["cells_per_thread"]
+    assert shape(512, 512, 512, split=(16, 16, 16)) == (128, 4)
+    assert shape(512, 512, 512, split=(1, 1, 1)) == (256, 4)
+    assert shape(1024, 8, 8, split=(1, 1, 1)) == (256, 8)
+    assert shape(2048, 8, 8, split=(1, 1, 1)) == (256, 8)
+
+
 @pytest.mark.parametrize("odf", [1, 8, 64, 512, 4096])
 def test_plan_model_bytes(od, odf):
     p = round(odf ** (1 / 3))
@@ -99,7 +109,9 @@ def test_plan_model_bytes(od, odf):
     dict(split=(1, 1, 1), dims=(4, 4, 4), threads=512, cells_per_thread=4),
     dict(split=(1, 1, 1), dims=(4, 4, 4), arith=7),
     dict(split=(1, 1, 1), dims=(4, 4, 4), stages=9),
-    dict(split=(1, 1, 1), dims=(8192, 4, 4)),       # row wider than the CTA can hold
+    dict(split=(1, 1, 1), dims=(4, 4, 4), stages=2),
+    dict(split=(1, 1, 1), dims=(8192, 4, 4)),       # row wider than any CTA can hold
+    dict(split=(1, 1, 1), dims=(600, 4, 4), threads=128, cells_per_thread=4),  # 600 > 512
     dict(cuts=([0, 3, 2, 8], None, None), dims=(8, 4, 4)),  # not ascending
     dict(cuts=([1, 8], None, None), dims=(8, 4, 4)),        # does not start at 0
 ])
@@ -126,8 +138,7 @@ def test_tile_counts(od, kw):
     dims = kw.pop("dims")
     info = od.plan(*dims, **kw)
     box, _ = od.decompose(*dims, **kw)
-    thr = kw.get("threads", 256) or 256
-    cpt = kw.get("cells_per_thread", 4) or 4
+    thr, cpt = info["threads"], info["cells_per_thread"]
     ty = kw.get("tile_y", 0)
     tz = kw.get("tile_z", 0) or 32
     total = 0

@@ -143,3 +143,43 @@ def test_jacobi_sum_chain(od):
         s = od.arith_host(1, s, v[k])
     same(s, s_ieee)
     same(od.arith_host(0, s), s_ieee / 6.0)
+
+
+def _update_inputs(rng, n):
+    """Six operands per cell: mostly the solver's regime (values in [0,1)),
+    plus zeros, negatives, subnormals, huge/tiny exponents and exact ties."""
+    x = rng.random((n, 6))
+    k = n // 8
+    x[:k] = positive_normals(rng, 6 * k).reshape(k, 6) * rng.choice([1.0, 1e-300, 1e300], (k, 6))
+    x[k:2 * k, rng.integers(0, 6)] = 0.0
+    x[2 * k:3 * k] *= rng.choice([-1.0, 1.0], (k, 6))
+    x[3 * k:3 * k + 100] = from_bits(rng.integers(1, 1 << 52, (100, 6), dtype=np.uint64))
+    # chain partial sums landing on exact halves: 1 + 2^-53 patterns
+    x[4 * k:4 * k + 1000, 0] = 1.0
+    x[4 * k:4 * k + 1000, 1] = 2.0 ** -53
+    x[4 * k:4 * k + 1000, 2] = 2.0 ** -53 * rng.integers(1, 4, 1000)
+    # a partial sum of exactly 1.0 met by an operand just above half an ulp
+    # whose excess lies far below the 64-bit alignment window (the sticky
+    # bit alone decides the rounding), at every position of the chain
+    base = 6 * k
+    for t in range(1, 6):
+        parts = [0.5 ** (i + 1) for i in range(t - 1)]
+        parts.append(1.0 - sum(parts))
+        rows = slice(base + (t - 1) * 200, base + t * 200)
+        x[rows, :t] = parts
+        x[rows, t] = 2.0 ** -53 * (1 + 2.0 ** -int(rng.integers(20, 52)))
+    # exponents at the chain domain's edges (biased 3, 4, 2040, 2041)
+    for j, e in enumerate((3, 4, 2040, 2041)):
+        sl = slice(5 * k + j * 100, 5 * k + (j + 1) * 100)
+        x[sl] = from_bits((np.uint64(e) << np.uint64(52)) | rng.integers(0, 1 << 52, (100, 6), dtype=np.uint64))
+    return x
+
+
+@pytest.mark.parametrize("mode", range(7))
+def test_update_every_mode_matches_ieee(od, mode):
+    rng = np.random.default_rng(100 + mode)
+    x = _update_inputs(rng, 400_000)
+    with np.errstate(all="ignore"):
+        want = (((((x[:, 0] + x[:, 1]) + x[:, 2]) + x[:, 3]) + x[:, 4]) + x[:, 5]) / 6.0
+    got = od.arith_host(10 + mode, np.ascontiguousarray(x).ravel())[: len(x)]
+    same(got, want)

@@ -58,3 +58,18 @@ def test_add_device(env):
         want = (ha + hb).view(np.uint64)
     assert np.array_equal(pkg.arith_device(1, x[0, :2_000_000].contiguous(),
                                            x[1, :2_000_000].contiguous()).cpu().numpy().view(np.uint64), want)
+
+
+@pytest.mark.parametrize("mode", range(7))
+def test_update_every_mode_device(env, mode):
+    # the full update on the GPU in every arithmetic mode equals the host IEEE
+    # chain, on the same mix of inputs as the host test
+    pkg, torch = env
+    import test_arith_cpu as host
+    rng = np.random.default_rng(200 + mode)
+    x = host._update_inputs(rng, 2_000_000)
+    with np.errstate(all="ignore"):
+        want = (((((x[:, 0] + x[:, 1]) + x[:, 2]) + x[:, 3]) + x[:, 4]) + x[:, 5]) / 6.0
+    xd = torch.from_numpy(np.ascontiguousarray(x).ravel()).to("cuda:0")
+    got = pkg.arith_device(10 + mode, xd).cpu().numpy()
+    host.same(got, want)

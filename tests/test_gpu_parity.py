@@ -116,7 +116,7 @@ def test_device_read_and_write(od):
 @pytest.mark.parametrize("shape", [
     dict(threads=128, cells_per_thread=2), dict(threads=128, cells_per_thread=8),
     dict(threads=256, cells_per_thread=1), dict(threads=256, cells_per_thread=8),
-    dict(threads=512, cells_per_thread=1), dict(threads=512, cells_per_thread=2, stages=2),
+    dict(threads=512, cells_per_thread=1), dict(threads=512, cells_per_thread=2, stages=3),
     dict(threads=256, cells_per_thread=4, stages=8),
     dict(threads=256, cells_per_thread=4, tile_y=3, tile_z=1),
 ] + [dict(arith=m) for m in range(7)])
