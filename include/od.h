@@ -227,6 +227,39 @@ OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
 OD_API od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n);
 OD_API od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n);
 
+/* Jacobi iterations on a caller's field without allocating device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory where they call -- a framework that owns all
+ * device memory through its own pool and forbids allocations it does not
+ * track, or a latency-critical loop where cudaMalloc/cudaFree would
+ * synchronise the device.  It calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * u_in, u_out: caller-owned device arrays of the current device, each the
+ * padded field (nx+2)*(ny+2)*(nz+2) doubles, x fastest (cell (gx,gy,gz) at
+ * gx + (nx+2)*(gy + (ny+2)*gz)); the one-cell shell is the fixed Dirichlet
+ * boundary.  u_in is read only; on completion u_out holds the field after
+ * `iters` >= 0 iterations (shell copied from u_in), bit-identical to the
+ * undecomposed sweep and to od_step.  u_in and u_out must not overlap.
+ * Work is enqueued on `stream` (a cudaStream_t, NULL = the legacy default
+ * stream); the call returns without waiting.
+ *
+ * Scratch: the second buffer of the double buffer is a static device array of
+ * OD_NOALLOC_MAX_PADDED_CELLS doubles (64 MiB) that every GPU which loads
+ * this library holds until the process exits.  Larger grids are rejected with
+ * OD_EINVAL.  Every call shares that array and it keeps the last call's
+ * contents (each call first overwrites the part it uses), so calls whose work
+ * overlaps on the GPU -- on different streams or from different host threads
+ * -- race and must be serialised by the caller.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.
+ * Errors: OD_EINVAL (null, aliasing or out-of-range arguments, grid too
+ * large), OD_ECUDA (a CUDA call failed); message in od_last_error(). */
+#define OD_NOALLOC_MAX_PADDED_CELLS (8ll * 1024 * 1024)
+OD_API od_status od_jacobi_noalloc(const double *u_in, double *u_out, int64_t nx, int64_t ny, int64_t nz,
+                                   int32_t iters, void *stream);
+
 /* Free everything the context owns (synchronises first).  NULL is allowed. */
 OD_API od_status od_destroy(od_ctx *ctx);
 

@@ -22,7 +22,7 @@ from . import _native
 from ._native import ODError, PATHS, check, lib, od_config, od_plan_info, od_stats
 
 __all__ = ["Jacobi3D", "ODError", "PATHS", "make_config", "plan", "decompose", "lib", "arith_host",
-           "arith_device"]
+           "arith_device", "jacobi_noalloc"]
 
 
 def _cuts_array(cuts):
@@ -107,6 +107,13 @@ def arith_device(op: int, a, b=None):
     out = torch.empty(n, dtype=torch.float64, device=a.device)
     check(lib().od_arith_device(int(op), a.data_ptr(), b.data_ptr(), out.data_ptr(), n), "od_arith_device")
     return out
+
+
+def jacobi_noalloc(u_in, u_out, nx: int, ny: int, nz: int, iters: int, stream: int | None = None) -> None:
+    """Iterate a caller-owned padded field (device tensors of (nx+2)(ny+2)(nz+2)
+    float64) without any device allocation; see od_jacobi_noalloc in od.h."""
+    check(lib().od_jacobi_noalloc(u_in.data_ptr(), u_out.data_ptr(), int(nx), int(ny), int(nz), int(iters),
+                                  stream), "od_jacobi_noalloc")
 
 
 class Jacobi3D:

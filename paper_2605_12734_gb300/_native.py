@@ -76,6 +76,7 @@ SIGNATURES = {
     "od_debug_stall_tile": (_i32, [_vp, _i64]),
     "od_arith_host": (_i32, [_i32, _vp, _vp, _vp, _i64]),
     "od_arith_device": (_i32, [_i32, _vp, _vp, _vp, _i64]),
+    "od_jacobi_noalloc": (_i32, [_vp, _vp, _i64, _i64, _i64, _i32, _vp]),
     "od_destroy": (_i32, [_vp]),
     "od_last_error": (ctypes.c_char_p, []),
     "od_version": (ctypes.c_char_p, []),

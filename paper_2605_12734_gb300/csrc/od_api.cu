@@ -55,6 +55,11 @@ constexpr uint64_t kDefaultSpinNs = 2000000000ull;
 
 }  // namespace
 
+namespace od {
+// Record an error for od_last_error() from another translation unit.
+od_status set_last_error(od_status s, const std::string &msg) { return fail(s, msg); }
+}  // namespace od
+
 struct od_ctx {
     od_config cfg{};
     od::Plan plan;
