@@ -124,6 +124,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# GB300 unit counts and clock (profiling recipe): 152 SMs, 2.07 GHz maximum
+# SM clock, FP64 1.25 TFLOP/s nominal = 2 FMA lanes per SM per clock.
+SMS = 152
+SM_MAX_GHZ = 2.07
+FP64_LANES_PER_SM = 2
+
+
+def profiled_traffic(args, plan):
+    """DRAM bytes per step of the tile kernel from the committed ncu summary
+    (profiles/traffic_*.json) when it was taken on this exact kernel build and
+    workload; None otherwise."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{args.path}_{args.edge}cubed_odf{args.odf}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("arith") != plan["arith"] or d.get("threads") != plan["threads"] or \
+            d.get("cells_per_thread") != plan["cells_per_thread"] or d.get("kernel_rev") != KERNEL_REV:
+        return None
+    return d["dram_bytes_per_step"]
+
+
+# bumped whenever the tile kernel changes, so stale profiler counters are not reused
+KERNEL_REV = 6
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -266,14 +292,33 @@ def run_ours(args):
     value = updates_step * world / (ms_step * 1e-3)
     launches = st1["kernel_launches"] - st0["kernel_launches"]
 
-    # roofline: the tile kernel does all of the step's HBM traffic
-    peak, peak_kind = measured_peaks()
+    # roofline of the tile kernel (it does all of a step's arithmetic and HBM
+    # traffic).  On GB300 the update is bound by the FP64 pipe, not by HBM:
+    # 5 adds + 1 division per cell, of which arithmetic mode m runs
+    # fp64_adds(m) adds on the FP64 pipe and the rest on the integer pipes.
+    fp64_adds = {0: 5, 1: 5, 2: 4, 3: 3, 4: 2, 5: 1, 6: 0}[plan["arith"]]
+    fp64_peak = FP64_LANES_PER_SM * SMS * SM_MAX_GHZ  # G FP64 instructions/s
+    hbm_peak, peak_kind = measured_peaks()
     bytes_step = plan["bytes_per_step"]
-    achieved = bytes_step / (ms_step * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "note": f"algorithmic bytes/step {bytes_step:.4g} (16 B/cell + 16 B per internal ghost "
-                        f"cell + 8 B per Dirichlet ghost cell); peak {peak_kind}"}
+    ups = updates_step / (ms_step * 1e-3)
+    hbm = {"achieved": bytes_step / (ms_step * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+           "frac": bytes_step / (ms_step * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
+           "bytes_per_step": bytes_step,
+           "note": "algorithmic bytes: 16 B/cell + 16 B per internal ghost cell + 8 B per Dirichlet ghost cell"}
+    if fp64_adds > 0:
+        roofline = {"bound": "alu", "achieved": fp64_adds * ups / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
+                    "frac": fp64_adds * ups / 1e9 / fp64_peak, "traffic": None,
+                    "note": (f"binding unit: FP64 pipe; {fp64_adds} of the update's 5 adds run there (the rest "
+                             f"and the division by 6 run exactly on the integer pipes); peak = "
+                             f"{FP64_LANES_PER_SM} FP64 lanes/clk/SM x {SMS} SMs x {SM_MAX_GHZ} GHz, derived "
+                             f"from the 1.25 TFLOP/s FP64 nominal (an FMA counted as 2 flops)"),
+                    "hbm": hbm}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm["frac"], "traffic": None, "note": hbm["note"] + "; peak " + peak_kind}
+    traffic = profiled_traffic(args, plan)
+    if traffic is not None:
+        roofline["traffic"] = traffic
 
     # end to end through the public API with pinned host buffers: each e2e
     # step is a whole solve of the config's 100 iterations: write the initial

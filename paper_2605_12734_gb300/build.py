@@ -55,6 +55,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
+    # tuning overrides for experiments, e.g. OD_NVCC_EXTRA="-DOD_MIN_THREADS_PER_SM=1280"
+    EXTRA = os.environ.get("OD_NVCC_EXTRA", "").split()
     procs, objs = [], []
     units = [(os.path.join(CSRC, s), [], os.path.basename(s)) for s in SOURCES]
     units += [(os.path.join(CSRC, TILE_SOURCE), [f"-DOD_AMODE={m}"], f"od_tiles_am{m}")
@@ -63,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         obj = os.path.join(BUILD, stem + ".o")
         objs.append(obj)
         if src.endswith(".cu"):
-            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *defs, "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *defs, *EXTRA, "-c", src, "-o", obj]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")
         else:

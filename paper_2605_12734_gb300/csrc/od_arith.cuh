@@ -184,23 +184,24 @@ OD_HD Unpacked add_chain(const Unpacked &a, const Unpacked &b) {
     const uint64_t M0 = S >> sh;
     const uint32_t rem = (uint32_t)S & ((1u << sh) - 1u);
     const uint32_t half = 1u << (sh - 1u);
-    const uint32_t up = (rem > half || (rem == half && (M0 & 1u))) ? 1u : 0u;
+    // round to nearest even (bitwise, no short-circuit branches)
+    const uint32_t up = (uint32_t)(rem > half) | ((uint32_t)(rem == half) & (uint32_t)M0 & 1u);
     const uint64_t M = M0 + up;
-    const bool carry = M == (kHid << 1);      // rounding carried into 2^53
+    const uint32_t carry = (uint32_t)(M >> 53);  // rounding carried into 2^53
     Unpacked r;
-    r.m = carry ? kHid : M;
-    r.e = e + c + (carry ? 1u : 0u);
+    r.m = M >> carry;                             // 2^53 -> 2^52
+    r.e = e + c + carry;
     return r;
 }
 
 // s / 6 for s in the chain's range (exponent >= 4): see div6.
 OD_HD double div6_chain(const Unpacked &s) {
-    const bool big = s.m >= (3ull << 51);
-    const uint64_t N = big ? (s.m << 1) : (s.m << 2);
+    const uint32_t big = (uint32_t)(s.m >= (3ull << 51));
+    const uint64_t N = s.m << (2u - big);
     const uint64_t Q0 = mulhi64(N, 0xAAAAAAAAAAAAAAABull) >> 1;
     const uint32_t r = (uint32_t)N - 3u * (uint32_t)Q0;
-    const uint64_t Q = Q0 + (r == 2u ? 1u : 0u);
-    const uint64_t er = (uint64_t)(s.e - (big ? 2u : 3u));
+    const uint64_t Q = Q0 + (r >> 1);
+    const uint64_t er = (uint64_t)(s.e - 3u + big);
     return f64_from(((er - 1u) << 52) + Q);
 }
 
@@ -214,12 +215,12 @@ OD_HD double div6_fast(double s, bool &ok) {
     const uint32_t es = (uint32_t)(b >> 52) & 0x7FFu;
     ok = es - 4u <= 2042u;
     const uint64_t M = (b & kFrac) | kHid;
-    const bool big = M >= (3ull << 51);
-    const uint64_t N = big ? (M << 1) : (M << 2);
+    const uint32_t big = (uint32_t)(M >= (3ull << 51));
+    const uint64_t N = M << (2u - big);
     const uint64_t Q0 = mulhi64(N, 0xAAAAAAAAAAAAAAABull) >> 1;
-    const uint32_t r = (uint32_t)N - 3u * (uint32_t)Q0;
-    const uint64_t Q = Q0 + (r == 2u ? 1u : 0u);
-    const uint64_t er = (uint64_t)(es - (big ? 2u : 3u));
+    const uint32_t r = (uint32_t)N - 3u * (uint32_t)Q0;  // 0, 1 or 2
+    const uint64_t Q = Q0 + (r >> 1);                      // round up iff r == 2
+    const uint64_t er = (uint64_t)(es - 3u + big);
     return f64_from((b & kSign) | (((er - 1u) << 52) + Q));
 }
 

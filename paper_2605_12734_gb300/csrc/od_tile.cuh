@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "od_arith.cuh"
 #include "od_internal.h"
 
@@ -263,44 +265,46 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
         return false;
     }
 
+    // One plane: ZP = the plane is a chare z-face with a neighbour there, so
+    // every cell is also stored into that neighbour's ghost plane (zp).
+    auto compute_plane = [&](auto zp_tag, int k, double *zp) {
+        constexpr bool ZP = decltype(zp_tag)::value;
+        const double *sd = ring.base + (size_t)slot(k - 1) * SD;
+        const double *sc = ring.base + (size_t)slot(k) * SD;
+        const double *su = ring.base + (size_t)slot(k + 1) * SD;
+        double *dpl = dst + (size_t)(k + 1) * plane;
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+            const uint32_t w = rf[m];
+            const int r = (int)(w & 0xFFFFu);
+            bool ok;
+            double v = jacobi_update_fast<AM>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
+            if (!ok)  // rare: an operand left the integer routines' domain
+                v = update_slow(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r]);
+            if (w & kValid) {
+                dpl[r] = v;
+                if (PUSH) {
+                    if (w >> 28) {
+                        const int j1 = (int)((w >> 16) & 0x7FFu) + 1;
+                        if (w & kXlo) pi->xlo[(size_t)(k + 1) * pi->xlo_plane + (size_t)j1 * pi->xlo_pitch] = v;
+                        if (w & kXhi) pi->xhi[(size_t)(k + 1) * pi->xhi_plane + (size_t)j1 * pi->xhi_pitch] = v;
+                        if (w & kYlo) pi->ylo[(size_t)(k + 1) * pi->ylo_plane + r] = v;
+                        if (w & kYhi) pi->yhi[(size_t)(k + 1) * pi->yhi_plane + r] = v;
+                    }
+                    if (ZP) zp[r] = v;
+                }
+            }
+        }
+    };
+
     for (int k = T.k0; k < ke; ++k) {
         fail = !mbar_wait_bounded(ring.bars + slot(k + 1), phase(k + 1), a.spin_ns);
         if (!fail) {
-            const double *sd = ring.base + (size_t)slot(k - 1) * SD;
-            const double *sc = ring.base + (size_t)slot(k) * SD;
-            const double *su = ring.base + (size_t)slot(k + 1) * SD;
-            double *dpl = dst + (size_t)(k + 1) * plane;
-            double *zp0 = nullptr, *zp1 = nullptr;
-            if (PUSH) {
-                if (k == 0) zp0 = pi->zlo;
-                if (k == bz - 1) zp1 = pi->zhi;
-            }
-#pragma unroll
-            for (int m = 0; m < CPT; ++m) {
-                const uint32_t w = rf[m];
-                const int r = (int)(w & 0xFFFFu);
-                bool ok;
-                double v = jacobi_update_fast<AM>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r],
-                                                  ok);
-                if (!ok)  // rare: an operand left the integer routines' domain
-                    v = update_slow(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r]);
-                if (w & kValid) {
-                    dpl[r] = v;
-                    if (PUSH) {
-                        if (w >> 28) {
-                            const int j1 = (int)((w >> 16) & 0x7FFu) + 1;
-                            if (w & kXlo)
-                                pi->xlo[(size_t)(k + 1) * pi->xlo_plane + (size_t)j1 * pi->xlo_pitch] = v;
-                            if (w & kXhi)
-                                pi->xhi[(size_t)(k + 1) * pi->xhi_plane + (size_t)j1 * pi->xhi_pitch] = v;
-                            if (w & kYlo) pi->ylo[(size_t)(k + 1) * pi->ylo_plane + r] = v;
-                            if (w & kYhi) pi->yhi[(size_t)(k + 1) * pi->yhi_plane + r] = v;
-                        }
-                        if (zp0) zp0[r] = v;
-                        if (zp1) zp1[r] = v;
-                    }
-                }
-            }
+            double *z0 = (PUSH && k == 0) ? pi->zlo : nullptr;
+            double *z1 = (PUSH && k == bz - 1) ? pi->zhi : nullptr;
+            if (z0) compute_plane(std::true_type(), k, z0);
+            if (z1) compute_plane(std::true_type(), k, z1);  // bz == 1 with both: the plane twice
+            if (!z0 && !z1) compute_plane(std::false_type(), k, nullptr);
         }
         if (__syncthreads_or(fail)) {
             if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
@@ -332,8 +336,16 @@ __device__ __forceinline__ Ring ring_setup(const KArgs &a, unsigned char *smem) 
 }
 
 // One CTA per tile (per-chare compute when !PUSH, fused step when PUSH).
+// Resident threads per SM the register budget must allow (1280 = 51
+// registers a thread): the FP64 pipe needs many warps to hide shared-memory
+// and pipe latency.  A build may override it (-DOD_MIN_THREADS_PER_SM=...).
+#ifndef OD_MIN_THREADS_PER_SM
+#define OD_MIN_THREADS_PER_SM 1280
+#endif
+constexpr int min_blocks(int nt) { return OD_MIN_THREADS_PER_SM / nt; }
+
 template <int NT, int CPT, bool PUSH, int AM>
-__global__ void __launch_bounds__(NT) k_tiles(const KArgs a) {
+__global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (blockDim.x != NT) {
         if (threadIdx.x == 0) record_err(a.err, OD_ERR_BAD_LAUNCH, -1, -1);
@@ -351,7 +363,7 @@ __global__ void __launch_bounds__(NT) k_tiles(const KArgs a) {
 // smaller than the waiter's, and tickets are taken in order by running CTAs,
 // so the wait graph has no cycle and needs no co-residency guarantee.
 template <int NT, int CPT, int AM>
-__global__ void __launch_bounds__(NT) k_persistent(const KArgs a) {
+__global__ void __launch_bounds__(NT, min_blocks(NT)) k_persistent(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int32_t s_ticket;
     if (blockDim.x != NT) {
