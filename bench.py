@@ -36,6 +36,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="odf", choices=["odf", "uneven", "ceiling", "serve"],
+                    help="odf: 512^3 at --odf (default); uneven: 768x512x512 in ~300 uneven chares; "
+                         "ceiling: 1024^3 in 4096 chares; serve: Poisson stream of jobs into the server")
+    ap.add_argument("--jobs", type=int, default=300, help="serve: number of jobs")
+    ap.add_argument("--rate", type=float, default=60.0, help="serve: Poisson arrival rate (jobs/s)")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
     ap.add_argument("--odf", type=int, default=4096)
     ap.add_argument("--edge", type=int, default=512)
     ap.add_argument("--path", default="persistent",
@@ -252,6 +258,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     od_build.build()
     dev = local
+    if args.workload == "serve":
+        return run_serve(args, pkg, torch, rank, world, dev)
     edge, odf = args.edge, args.odf
     p = round(odf ** (1 / 3))
     if p ** 3 != odf:
@@ -259,9 +267,20 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     tune_kw = dict(threads=args.threads, cells_per_thread=args.cpt, stages=args.stages,
                    tile_y=args.tile_y, tile_z=args.tile_z, arith=args.arith, autotune=args.tune, device=dev)
+    from paper_2605_12734_gb300 import inputs
+    if args.workload == "uneven":
+        w = inputs.uneven_768()
+        dims, dec, name = (w.nx, w.ny, w.nz), dict(cuts=w.cuts), w.name
+        tune_kw["autotune"] = True
+    elif args.workload == "ceiling":
+        w = inputs.ceiling_1024()
+        dims, dec, name = (w.nx, w.ny, w.nz), dict(split=w.split), w.name
+    else:
+        dims, dec, name = (edge, edge, edge), dict(split=(p, p, p)), f"jacobi3d-{edge}^3-odf{odf}"
+    seed = 2 if args.workload == "odf" else w.seed
 
-    solver = pkg.Jacobi3D(edge, edge, edge, split=(p, p, p), seed=2, init_mode=1, path=args.path,
-                          stream=stream.cuda_stream, **tune_kw)
+    solver = pkg.Jacobi3D(*dims, seed=seed, init_mode=1, path=args.path, stream=stream.cuda_stream,
+                          **dec, **tune_kw)
     plan = solver.stats()["plan"]
     solver.step(args.warmup)
     solver.sync()
@@ -349,7 +368,7 @@ def run_ours(args):
     solver.close()
 
     baseline = None
-    if args.baseline_steps > 0 and rank == 0:
+    if args.baseline_steps > 0 and rank == 0 and args.workload == "odf":
         ms_b, b0, b1 = time_path(pkg, edge, odf, "per_chare", args.baseline_steps, 1, stream,
                                  dict(device=dev))
         baseline = {"path": "per_chare", "ms_per_step": ms_b, "value": updates_step / (ms_b * 1e-3),
@@ -374,16 +393,18 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_cpu_baseline(edge)
+        cpu = oracle_cpu_baseline(edge if args.workload == "odf" else 512)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"jacobi3d-{edge}^3-odf{odf}", "nx": edge, "ny": edge, "nz": edge,
-                           "odf": odf, "chare_edge": edge // p, "path": args.path, "seed": 2,
+                "config": {"workload": name, "nx": dims[0], "ny": dims[1], "nz": dims[2],
+                           "odf": plan["nchares"], "chare_edge": (edge // p) if args.workload == "odf" else None,
+                           "path": args.path, "seed": seed, "tuned": bool(st1.get("tuned")),
                            "init": "U[0,1) everywhere, Dirichlet shell fixed",
-                           "l2": "no flush: 2 parity buffers of ~2.3 GB each exceed the 129 MB L2",
+                           "l2": f"no flush: the two parity buffers ({plan['arena_bytes'] / 2**30:.1f} GiB "
+                                 f"with ghosts) far exceed the 129 MB L2",
                            "parallelism": f"replicas x{world}",
                            "tiling": {k: plan[k] for k in ("threads", "cells_per_thread", "stages", "arith",
                                                            "tile_y", "tile_z", "smem_bytes", "ntiles")}},
@@ -395,6 +416,65 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_serve(args, pkg, torch, rank, world, dev):
+    """Serving stream: independent jobs arrive as a Poisson process (seeded),
+    each a cubic grid with edge log-uniform in [64, 384], ODF in {8, 27, 64,
+    216} and 10..200 iterations; the server admits them under the HBM budget
+    and batches every running job into one launch per iteration.  Reports
+    aggregate updates/s and p50/p99 job latency (completion - arrival)."""
+    from paper_2605_12734_gb300 import inputs
+    jobs = inputs.serving_stream(args.jobs, args.rate, seed=6)
+    budget = int(args.budget_gb * (1 << 30))
+    srv = pkg.Server(budget, device=dev, threads=args.threads, cells_per_thread=args.cpt,
+                     stages=args.stages, arith=args.arith)
+    # warm-up: one small job through the whole path
+    w = srv.submit(64, 64, 64, 3, split=(2, 2, 2), seed=1)
+    srv.wait(w, 60.0)
+    srv.release(w)
+    ids = {}
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t0 = time.perf_counter()
+    base = srv.stats()["seconds"]
+    for j in jobs:
+        delay = t0 + j.arrival_s - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        jid = srv.submit(j.edge, j.edge, j.edge, j.iters, split=(j.p, j.p, j.p), seed=j.seed)
+        ids[jid] = j
+    lat, upd, first_submit, last_done = [], 0.0, None, 0.0
+    for jid, j in ids.items():
+        st = srv.wait(jid, 600.0)
+        if st != 2:
+            raise SystemExit(f"job {jid} ended in state {st}")
+        info = srv.info(jid)
+        lat.append(info["t_done"] - info["t_submit"])
+        first_submit = info["t_submit"] if first_submit is None else min(first_submit, info["t_submit"])
+        last_done = max(last_done, info["t_done"])
+        upd += j.updates
+        srv.release(jid)
+    clk = clocks.stop()
+    st = srv.stats()
+    srv.close()
+    wall = last_done - first_submit
+    lat_sorted = sorted(lat)
+    def pct(q):
+        return lat_sorted[min(len(lat_sorted) - 1, int(round(q * (len(lat_sorted) - 1))))]
+    line = {"metric": METRIC, "value": upd / wall, "unit": UNIT, "n_gpus": world, "steps": args.jobs,
+            "warmup": 1, "ms_per_step": wall * 1e3 / args.jobs, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "jacobi3d-serving-poisson", "jobs": args.jobs, "rate_per_s": args.rate,
+                       "edge": "log-uniform [64,384]", "odf": "{8,27,64,216}", "iters": "U[10,200]",
+                       "budget_gb": args.budget_gb, "seed": 6, "note": "a step here is one job"},
+            "latency_p50_s": pct(0.50), "latency_p99_s": pct(0.99), "latency_mean_s": sum(lat) / len(lat),
+            "latency_max_s": lat_sorted[-1], "wall_s": wall, "launches": st["launches"],
+            "pool_peak_gb": st["pool_peak"] / (1 << 30), "offered_updates_per_s": upd / jobs[-1].arrival_s,
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 

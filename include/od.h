@@ -101,9 +101,17 @@ typedef struct od_config {
     uint64_t seed;               /* initial-field seed */
     int32_t init_mode;           /* OD_INIT_ZERO_INTERIOR or OD_INIT_UNIFORM */
     int32_t path;                /* od_path */
-    int32_t autotune;            /* 1: time candidate tilings at od_create and
-                                    keep the fastest (the field is initialised
-                                    after tuning, so results do not change) */
+    int32_t autotune;            /* 1: od_create times candidate execution
+                                    shapes (CTA shape x arithmetic mode, then
+                                    ring depth x planes per tile) on this
+                                    decomposition and keeps the fastest; the
+                                    field is initialised after tuning, so
+                                    results do not change.  The choice is
+                                    cached in OD_TUNE_CACHE (default
+                                    $HOME/.cache/libod/tune.txt, "off" = no
+                                    cache).  Needs a second arena's worth of
+                                    device memory while tuning (skipped if
+                                    that is not available). */
     int32_t tile_y;              /* max rows per tile (0 = planner default) */
     int32_t tile_z;              /* planes per tile (0 = planner default) */
     int32_t threads;             /* threads per CTA: 128, 256 or 512 */
@@ -157,6 +165,8 @@ typedef struct od_stats {
     int64_t graph_launches;
     int32_t path;
     int32_t persistent_grid;       /* CTAs of the last persistent launch */
+    int32_t tuned;                 /* 1: the execution shape came from the autotuner */
+    double tune_ms_per_step;       /* the autotuner's time per step for it */
     od_plan_info plan;
 } od_stats;
 
@@ -226,6 +236,72 @@ OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
  * of the current device and synchronises.  n >= 0 elements. */
 OD_API od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n);
 OD_API od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n);
+
+/* ------------------------------------------------------------------ serving
+ *
+ * A server admits independent solves as they arrive, keeps their state
+ * resident in one device pool of hbm_budget_bytes and advances every running
+ * job by one iteration per launch of a batched fused kernel (continuous
+ * batching: jobs that arrive while others run join the next launch, finished
+ * jobs drop out).  Admission is first come, first served, while a slot is free
+ * (max_active, 0 = no limit) and the pool has room for the job's arena.  A
+ * worker thread inside the server drives the device; every call below is
+ * thread-safe.  Each job's result is bit-identical to the same job solved
+ * alone with od_create/od_step.  The paper's runtime schedules many chares of
+ * one application per GPU (Sec. III); serving many applications on one GPU
+ * has no counterpart in the paper. */
+#define OD_JOB_QUEUED 0
+#define OD_JOB_RUNNING 1
+#define OD_JOB_DONE 2
+#define OD_JOB_FAILED 3
+
+typedef struct od_server od_server;
+
+typedef struct od_server_config {
+    uint64_t hbm_budget_bytes;   /* device memory for all resident jobs */
+    int32_t max_active;          /* jobs resident at once (0 = no limit) */
+    int32_t max_jobs_per_launch; /* batch table size (0 = 256) */
+    int32_t device;
+    int32_t threads, cells_per_thread, stages; /* tile shape for every job (0 = 128, 4, 4) */
+    int32_t arith;               /* as od_config.arith (-1 = 2) */
+    void *pool;                  /* caller device memory of hbm_budget_bytes, 256-byte
+                                    aligned, or NULL: the server allocates it once */
+} od_server_config;
+
+typedef struct od_job_info {
+    int32_t state;               /* OD_JOB_* */
+    int32_t iters;
+    int64_t cells;
+    uint64_t arena_bytes;        /* the job's share of the budget */
+    double t_submit, t_admit, t_done;  /* seconds since the server was created */
+} od_job_info;
+
+typedef struct od_server_stats_t {
+    int64_t queued, running, done, failed;
+    int64_t launches;            /* batched kernel launches */
+    double updates_done;         /* cell updates of completed jobs */
+    uint64_t pool_used, pool_peak;
+    double seconds;              /* since the server was created */
+} od_server_stats_t;
+
+OD_API void od_server_config_default(od_server_config *cfg);
+/* Allocate the pool (unless given), streams and launch tables; start the worker. */
+OD_API od_status od_server_create(od_server **out, const od_server_config *cfg);
+/* Queue a job: the decomposition and seed of *job (cut lists are copied;
+ * path, tile shape, stream and arena fields are ignored) and its iteration
+ * count.  OD_EBUDGET if the job alone exceeds the whole budget. */
+OD_API od_status od_server_submit(od_server *s, const od_config *job, int32_t iters, uint64_t *job_id);
+/* Wait up to timeout_s seconds for the job to be done or failed; *state is
+ * its state on return (OD_OK also on timeout). */
+OD_API od_status od_server_wait(od_server *s, uint64_t job_id, double timeout_s, int32_t *state);
+OD_API od_status od_server_job_info(od_server *s, uint64_t job_id, od_job_info *out);
+/* Copy a done job's field (nx*ny*nz doubles, x fastest) to dst (device or host). */
+OD_API od_status od_server_fetch(od_server *s, uint64_t job_id, double *dst, int32_t dst_is_device);
+/* Forget a job that is done, failed or still queued, returning its memory to the pool. */
+OD_API od_status od_server_release(od_server *s, uint64_t job_id);
+OD_API od_status od_server_stats(od_server *s, od_server_stats_t *out);
+/* Stop the worker (after the launches in flight) and free everything. */
+OD_API od_status od_server_destroy(od_server *s);
 
 /* Jacobi iterations on a caller's field without allocating device memory.
  *

@@ -21,7 +21,7 @@ import numpy as np
 from . import _native
 from ._native import ODError, PATHS, check, lib, od_config, od_plan_info, od_stats
 
-__all__ = ["Jacobi3D", "ODError", "PATHS", "make_config", "plan", "decompose", "lib", "arith_host",
+__all__ = ["Jacobi3D", "Server", "ODError", "PATHS", "make_config", "plan", "decompose", "lib", "arith_host",
            "arith_device", "jacobi_noalloc"]
 
 
@@ -127,6 +127,8 @@ class Jacobi3D:
                 import torch
                 if torch.cuda.is_available():
                     need = plan(nx, ny, nz, **kw)["arena_bytes"]
+                    if kw.get("autotune"):  # other tilings need larger tables
+                        need = need + need // 16 + (64 << 20)
                     dev = kw.get("device", 0)
                     self._arena_tensor = torch.empty(need + 256, dtype=torch.uint8, device=f"cuda:{dev}")
                     base = self._arena_tensor.data_ptr()
@@ -193,6 +195,78 @@ class Jacobi3D:
             lib().od_destroy(self._h)
             self._h = ctypes.c_void_p()
         self._arena_tensor = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop (od_server): admits independent solves under an HBM budget,
+    keeps them resident and advances all running jobs together."""
+
+    def __init__(self, hbm_budget_bytes: int, *, max_active: int = 0, device: int = 0, threads: int = 0,
+                 cells_per_thread: int = 0, stages: int = 0, arith: int = -1, max_jobs_per_launch: int = 0):
+        cfg = _native.od_server_config()
+        lib().od_server_config_default(ctypes.byref(cfg))
+        cfg.hbm_budget_bytes = int(hbm_budget_bytes)
+        cfg.max_active, cfg.device = int(max_active), int(device)
+        cfg.threads, cfg.cells_per_thread, cfg.stages, cfg.arith = int(threads), int(cells_per_thread), \
+            int(stages), int(arith)
+        if max_jobs_per_launch:
+            cfg.max_jobs_per_launch = int(max_jobs_per_launch)
+        h = ctypes.c_void_p()
+        check(lib().od_server_create(ctypes.byref(h), ctypes.byref(cfg)), "od_server_create")
+        self._h = h
+        self._sizes = {}
+
+    def submit(self, nx, ny, nz, iters, **kw) -> int:
+        cfg, keep = make_config(nx, ny, nz, **kw)
+        jid = ctypes.c_uint64()
+        check(lib().od_server_submit(self._h, ctypes.byref(cfg), int(iters), ctypes.byref(jid)), "od_server_submit")
+        self._sizes[jid.value] = int(nx) * int(ny) * int(nz)
+        return jid.value
+
+    def wait(self, job: int, timeout_s: float = 60.0) -> int:
+        st = ctypes.c_int32()
+        check(lib().od_server_wait(self._h, job, float(timeout_s), ctypes.byref(st)), "od_server_wait")
+        return st.value
+
+    def info(self, job: int) -> dict:
+        i = _native.od_job_info()
+        check(lib().od_server_job_info(self._h, job, ctypes.byref(i)), "od_server_job_info")
+        return {f: getattr(i, f) for f, _ in _native.od_job_info._fields_}
+
+    def fetch(self, job: int, out=None):
+        if out is None:
+            out = np.empty(self._sizes[job], dtype=np.float64)
+        if isinstance(out, np.ndarray):
+            check(lib().od_server_fetch(self._h, job, out.ctypes.data, 0), "od_server_fetch")
+        else:
+            check(lib().od_server_fetch(self._h, job, out.data_ptr(), 1), "od_server_fetch")
+        return out
+
+    def release(self, job: int) -> None:
+        check(lib().od_server_release(self._h, job), "od_server_release")
+        self._sizes.pop(job, None)
+
+    def stats(self) -> dict:
+        st = _native.od_server_stats_t()
+        check(lib().od_server_stats(self._h, ctypes.byref(st)), "od_server_stats")
+        return {f: getattr(st, f) for f, _ in _native.od_server_stats_t._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().od_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
 
     def __enter__(self):
         return self

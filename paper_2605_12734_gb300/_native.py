@@ -49,8 +49,33 @@ class od_plan_info(ctypes.Structure):
 class od_stats(ctypes.Structure):
     _fields_ = [
         ("steps_done", _i64), ("kernel_launches", _i64), ("api_calls", _i64), ("graph_launches", _i64),
-        ("path", _i32), ("persistent_grid", _i32), ("plan", od_plan_info),
+        ("path", _i32), ("persistent_grid", _i32), ("tuned", _i32), ("tune_ms_per_step", ctypes.c_double),
+        ("plan", od_plan_info),
     ]
+
+
+class od_server_config(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", _u64), ("max_active", _i32), ("max_jobs_per_launch", _i32), ("device", _i32),
+        ("threads", _i32), ("cells_per_thread", _i32), ("stages", _i32), ("arith", _i32), ("pool", _vp),
+    ]
+
+
+class od_job_info(ctypes.Structure):
+    _fields_ = [
+        ("state", _i32), ("iters", _i32), ("cells", _i64), ("arena_bytes", _u64),
+        ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+    ]
+
+
+class od_server_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("queued", _i64), ("running", _i64), ("done", _i64), ("failed", _i64), ("launches", _i64),
+        ("updates_done", ctypes.c_double), ("pool_used", _u64), ("pool_peak", _u64), ("seconds", ctypes.c_double),
+    ]
+
+
+OD_JOB_QUEUED, OD_JOB_RUNNING, OD_JOB_DONE, OD_JOB_FAILED = range(4)
 
 
 class ODError(RuntimeError):
@@ -76,6 +101,15 @@ SIGNATURES = {
     "od_debug_stall_tile": (_i32, [_vp, _i64]),
     "od_arith_host": (_i32, [_i32, _vp, _vp, _vp, _i64]),
     "od_arith_device": (_i32, [_i32, _vp, _vp, _vp, _i64]),
+    "od_server_config_default": (None, [ctypes.POINTER(od_server_config)]),
+    "od_server_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(od_server_config)]),
+    "od_server_submit": (_i32, [_vp, ctypes.POINTER(od_config), _i32, ctypes.POINTER(_u64)]),
+    "od_server_wait": (_i32, [_vp, _u64, ctypes.c_double, ctypes.POINTER(_i32)]),
+    "od_server_job_info": (_i32, [_vp, _u64, ctypes.POINTER(od_job_info)]),
+    "od_server_fetch": (_i32, [_vp, _u64, _vp, _i32]),
+    "od_server_release": (_i32, [_vp, _u64]),
+    "od_server_stats": (_i32, [_vp, ctypes.POINTER(od_server_stats_t)]),
+    "od_server_destroy": (_i32, [_vp]),
     "od_jacobi_noalloc": (_i32, [_vp, _vp, _i64, _i64, _i64, _i32, _vp]),
     "od_destroy": (_i32, [_vp]),
     "od_last_error": (ctypes.c_char_p, []),

@@ -7,8 +7,11 @@
 // execution spaces created once), and every path only enqueues work.
 #include <cuda_runtime.h>
 
+#include <sys/stat.h>
+
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -18,6 +21,7 @@
 #include "od_internal.h"
 #include "od_kernels.h"
 #include "od_plan.h"
+#include "od_ctx.h"
 
 namespace {
 
@@ -51,52 +55,14 @@ struct DeviceGuard {
     }
 };
 
-constexpr uint64_t kDefaultSpinNs = 2000000000ull;
-
 }  // namespace
 
-namespace od {
-// Record an error for od_last_error() from another translation unit.
-od_status set_last_error(od_status s, const std::string &msg) { return fail(s, msg); }
-}  // namespace od
 
-struct od_ctx {
-    od_config cfg{};
-    od::Plan plan;
-    int device = 0;
-    int num_sms = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    char *arena = nullptr;
-    bool own_arena = false;
-    ChareDev *d_ch = nullptr;
-    TileDev *d_tiles = nullptr;
-    ErrDev *d_err = nullptr;
-    int32_t *d_queue = nullptr, *d_epoch = nullptr, *d_dep_ptr = nullptr, *d_dep_idx = nullptr,
-            *d_order = nullptr;
-    std::vector<ChareDev> h_ch;       // host copy (device pointers)
-    double *d_stage = nullptr;        // lazily allocated host-transfer staging
-    int path = OD_PATH_FUSED;
-    int64_t steps = 0;
-    int64_t launches = 0, api_calls = 0, graph_launches = 0;
-    int persistent_grid = 0;
-    int64_t stall_tile = -1;
-    uint64_t spin_ns = kDefaultSpinNs;
-    bool failed = false;
-    // per-chare path
-    std::vector<cudaStream_t> pool;
-    std::vector<cudaEvent_t> ev;      // ev[2*c + slot]: chare c delivered its faces
-    cudaEvent_t fork = nullptr;
-    std::vector<cudaEvent_t> join;
-    // graph path
-    cudaGraphExec_t g2 = nullptr, g1[2] = {nullptr, nullptr};
-    int64_t g2_kernels = 0, g1_kernels[2] = {0, 0};
-    int64_t g2_calls = 0, g1_calls[2] = {0, 0};
-};
+
 
 namespace {
 
-KArgs base_args(const od_ctx *c) {
+KArgs base_args_impl(const od_ctx *c) {
     KArgs a;
     memset(&a, 0, sizeof a);
     a.ch = c->d_ch;
@@ -120,7 +86,7 @@ KArgs base_args(const od_ctx *c) {
 od_status enqueue_fused(od_ctx *c, int32_t iters) {
     const od::Plan &p = c->plan;
     for (int32_t s = 0; s < iters; ++s) {
-        KArgs a = base_args(c);
+        KArgs a = base_args_impl(c);
         a.tile_begin = 0;
         a.parity = (int32_t)(c->steps & 1);
         OD_CUDA(od::launch_tiles(a, (int)p.tiles.size(), p.threads, p.cpt, p.amode, true, p.smem_bytes, c->stream));
@@ -147,7 +113,7 @@ od_status enqueue_persistent(od_ctx *c, int32_t iters) {
         int32_t n = std::min(iters - done, chunk_max);
         OD_CUDA(cudaMemsetAsync(c->d_queue, 0, sizeof(int32_t), c->stream));
         OD_CUDA(cudaMemsetAsync(c->d_epoch, 0, (size_t)nt * sizeof(int32_t), c->stream));
-        KArgs a = base_args(c);
+        KArgs a = base_args_impl(c);
         a.iters = n;
         a.t0 = (int32_t)(c->steps & 0x7fffffff);
         OD_CUDA(od::launch_persistent(a, grid, p.threads, p.cpt, p.amode, p.smem_bytes, c->stream));
@@ -185,7 +151,7 @@ od_status enqueue_per_chare_steps(od_ctx *c, int64_t t_first, int32_t iters, int
         for (int ci = 0; ci < nch; ++ci) {
             const od::HostChare &h = p.ch[(size_t)ci];
             cudaStream_t st = c->pool[ci % P];
-            KArgs a = base_args(c);
+            KArgs a = base_args_impl(c);
             a.tile_begin = h.tile_begin;
             a.parity = sp;
             OD_CUDA(od::launch_tiles(a, h.tile_end - h.tile_begin, p.threads, p.cpt, p.amode, false, p.smem_bytes, st));
@@ -294,7 +260,7 @@ od_status enqueue_graph(od_ctx *c, int32_t iters) {
     return OD_OK;
 }
 
-od_status check_device_error(od_ctx *c) {
+od_status check_device_error_impl(od_ctx *c) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         c->failed = true;
@@ -348,6 +314,231 @@ void release(od_ctx *c) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- autotuner
+//
+// od_create with autotune = 1 times candidate execution shapes on the real
+// decomposition before the context is built: each candidate is a temporary
+// context (autotune off) laid out in one shared tuning buffer, initialised,
+// stepped twice untimed and then timed with events.  Candidates (in two
+// rounds, coordinate descent): CTA shape x arithmetic mode with the default
+// ring, then ring depth x planes per tile for the best of those.  Every
+// candidate computes the same bits, so the choice only changes speed.  The
+// winner is cached in a text file (OD_TUNE_CACHE, default
+// $HOME/.cache/libod/tune.txt; "off" disables the cache) keyed by device,
+// path, grid and block edges.
+namespace {
+
+struct TuneChoice {
+    int threads = 0, cpt = 0, stages = 0, arith = -1, tile_z = 0;
+    double ms = 0;
+};
+
+std::string tune_cache_path() {
+    const char *e = getenv("OD_TUNE_CACHE");
+    if (e && *e) return std::string(e);
+    const char *h = getenv("HOME");
+    return std::string(h && *h ? h : "/tmp") + "/.cache/libod/tune.txt";
+}
+
+std::string tune_key(const od_config *cfg, const od::Plan &p, int device) {
+    cudaDeviceProp prop;
+    std::string name = "unknown";
+    int sms = 0;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) {
+        name = prop.name;
+        sms = prop.multiProcessorCount;
+    }
+    for (auto &ch : name)
+        if (ch == ' ') ch = '_';
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the block edges
+    auto mix = [&](int64_t v) {
+        for (int b = 0; b < 8; ++b) {
+            h ^= (uint64_t)((v >> (8 * b)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    };
+    for (auto v : p.ex) mix(v);
+    mix(-1);
+    for (auto v : p.ey) mix(v);
+    mix(-1);
+    for (auto v : p.ez) mix(v);
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s/%d/path%d/%lldx%lldx%lld/%016llx", name.c_str(), sms, cfg->path,
+             (long long)p.nx, (long long)p.ny, (long long)p.nz, (unsigned long long)h);
+    return buf;
+}
+
+bool tune_cache_lookup(const std::string &key, TuneChoice *c) {
+    std::string path = tune_cache_path();
+    if (path == "off") return false;
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return false;
+    char k[256];
+    TuneChoice t;
+    bool found = false;
+    while (fscanf(f, "%255s %d %d %d %d %d %lf", k, &t.threads, &t.cpt, &t.stages, &t.arith, &t.tile_z, &t.ms) == 7)
+        if (key == k) {
+            *c = t;
+            found = true;
+        }
+    fclose(f);
+    return found;
+}
+
+void tune_cache_store(const std::string &key, const TuneChoice &c) {
+    std::string path = tune_cache_path();
+    if (path == "off") return;
+    std::string dir = path.substr(0, path.find_last_of('/'));
+    if (!dir.empty()) {  // create the directory chain
+        for (size_t i = 1; i <= dir.size(); ++i)
+            if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+    }
+    FILE *f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d %d %d %d %.17g\n", key.c_str(), c.threads, c.cpt, c.stages, c.arith, c.tile_z, c.ms);
+    fclose(f);
+}
+
+od_status run_tuning(const od_config *cfg, TuneChoice *best) {
+    od::Plan base;
+    std::string err;
+    od_status s = od::build_plan(cfg, &base, &err);
+    if (s != OD_OK) return fail(s, err);
+    const std::string key = tune_key(cfg, base, cfg->device);
+    if (tune_cache_lookup(key, best)) return OD_OK;
+
+    const int shapes[6][2] = {{128, 4}, {128, 8}, {256, 4}, {256, 8}, {128, 2}, {256, 2}};
+    const int ariths[3] = {1, 2, 3};
+    std::vector<TuneChoice> round1;
+    for (auto &sh : shapes)
+        for (int am : ariths) {
+            TuneChoice c;
+            c.threads = sh[0];
+            c.cpt = sh[1];
+            c.stages = 4;
+            c.arith = am;
+            c.tile_z = cfg->tile_z;
+            round1.push_back(c);
+        }
+    auto make_cfg = [&](const TuneChoice &c, void *arena, uint64_t bytes, cudaStream_t st) {
+        od_config t = *cfg;
+        t.autotune = 0;
+        t.threads = c.threads;
+        t.cells_per_thread = c.cpt;
+        t.stages = c.stages;
+        t.arith = c.arith;
+        t.tile_z = c.tile_z;
+        t.arena = arena;
+        t.arena_bytes = bytes;
+        t.stream = st;
+        if (t.path == OD_PATH_PER_CHARE || t.path == OD_PATH_GRAPH) t.path = OD_PATH_FUSED;
+        t.stream_pool = 1;
+        return t;
+    };
+    // the tuning buffer: the largest arena any candidate needs
+    uint64_t need = 0;
+    std::vector<TuneChoice> cands;
+    auto consider = [&](std::vector<TuneChoice> &list) {
+        std::vector<TuneChoice> ok;
+        for (auto &c : list) {
+            od_config t = make_cfg(c, nullptr, 0, nullptr);
+            od::Plan p;
+            std::string e2;
+            if (od::build_plan(&t, &p, &e2) != OD_OK) continue;
+            // with a caller arena the final context must fit in it
+            if (cfg->arena && p.arena_bytes > cfg->arena_bytes) continue;
+            need = std::max<uint64_t>(need, p.arena_bytes);
+            ok.push_back(c);
+        }
+        list.swap(ok);
+    };
+    consider(round1);
+    if (round1.empty()) return fail(OD_EINVAL, "autotune: no candidate fits this decomposition");
+    // round-2 candidates may need more table space; size generously
+    need = need + need / 8 + (1u << 20);
+    void *buf = nullptr;
+    bool own_buf = false;
+    if (cfg->arena && cfg->arena_bytes >= need) {
+        buf = cfg->arena;  // the caller's arena is free until the context is built
+    } else {
+        if (cudaMalloc(&buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return OD_OK;  // no room to tune: keep the defaults
+        }
+        own_buf = true;
+    }
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_one = [&](TuneChoice &c) -> bool {
+        od_config t = make_cfg(c, buf, need, st);
+        od_ctx *tmp = nullptr;
+        if (od_create(&tmp, &t) != OD_OK) return false;
+        bool good = od_step(tmp, 2) == OD_OK;
+        if (good) {
+            const int n = 5;
+            cudaEventRecord(e0, st);
+            good = od_step(tmp, n) == OD_OK;
+            cudaEventRecord(e1, st);
+            good = good && od_sync(tmp) == OD_OK;
+            float ms = 0;
+            if (good && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) c.ms = ms / n;
+            else good = false;
+        }
+        od_destroy(tmp);
+        return good;
+    };
+    TuneChoice win;
+    win.ms = 1e30;
+    for (auto &c : round1)
+        if (time_one(c) && c.ms < win.ms) win = c;
+    if (win.ms < 1e30) {
+        std::vector<TuneChoice> round2;
+        const int stages_c[3] = {3, 5, 6};
+        const int tz_c[3] = {16, 32, 64};
+        for (int sg : stages_c) {
+            TuneChoice c = win;
+            c.stages = sg;
+            round2.push_back(c);
+        }
+        for (int tz : tz_c) {
+            TuneChoice c = win;
+            c.tile_z = tz;
+            round2.push_back(c);
+        }
+        std::vector<TuneChoice> fits;
+        for (auto &c : round2) {
+            od_config t = make_cfg(c, nullptr, 0, nullptr);
+            od::Plan p;
+            std::string e2;
+            if (od::build_plan(&t, &p, &e2) == OD_OK && p.arena_bytes <= need &&
+                (!cfg->arena || p.arena_bytes <= cfg->arena_bytes))
+                fits.push_back(c);
+        }
+        for (auto &c : fits)
+            if (time_one(c) && c.ms < win.ms) win = c;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (own_buf) cudaFree(buf);
+    g_last_error.clear();
+    if (win.ms >= 1e30) return OD_OK;  // nothing ran: keep the defaults
+    *best = win;
+    tune_cache_store(key, win);
+    return OD_OK;
+}
+
+}  // namespace
+
+namespace od {
+od_status set_last_error(od_status s, const std::string &msg) { return fail(s, msg); }
+KArgs base_args(const od_ctx *c) { return base_args_impl(c); }
+od_status check_device_error(od_ctx *c) { return check_device_error_impl(c); }
+}  // namespace od
 
 extern "C" {
 
@@ -410,11 +601,31 @@ od_status od_decompose(const od_config *cfg, int64_t *box, int32_t *nbr, int64_t
     return OD_OK;
 }
 
-od_status od_create(od_ctx **out, const od_config *cfg) {
-    if (!out || !cfg) return fail(OD_EINVAL, "null argument");
+od_status od_create(od_ctx **out, const od_config *cfg_in) {
+    if (!out || !cfg_in) return fail(OD_EINVAL, "null argument");
     *out = nullptr;
+    od_config tuned = *cfg_in;
+    const od_config *cfg = &tuned;
+    double tune_ms = 0;
+    if (cfg_in->autotune) {
+        DeviceGuard dg0(cfg_in->device);
+        TuneChoice best;
+        od_status ts = run_tuning(cfg_in, &best);
+        if (ts != OD_OK) return ts;
+        if (best.threads) {
+            tuned.threads = best.threads;
+            tuned.cells_per_thread = best.cpt;
+            tuned.stages = best.stages;
+            tuned.arith = best.arith;
+            tuned.tile_z = best.tile_z;
+            tune_ms = best.ms;
+        }
+        tuned.autotune = 0;
+    }
     od_ctx *c = new od_ctx();
     c->cfg = *cfg;
+    c->tuned = cfg_in->autotune != 0;
+    c->tune_ms = tune_ms;
     c->cfg.cuts_x = c->cfg.cuts_y = c->cfg.cuts_z = nullptr;  // not kept past the call
     std::string err;
     od_status s = od::build_plan(cfg, &c->plan, &err);
@@ -548,13 +759,13 @@ od_status od_set_path(od_ctx *c, int32_t path) {
 od_status od_sync(od_ctx *c) {
     if (!c) return fail(OD_EINVAL, "null context");
     DeviceGuard dg(c->device);
-    return check_device_error(c);
+    return check_device_error_impl(c);
 }
 
 od_status od_read(od_ctx *c, double *dst, int32_t dst_is_device) {
     if (!c || !dst) return fail(OD_EINVAL, "null argument");
     DeviceGuard dg(c->device);
-    od_status s = check_device_error(c);
+    od_status s = check_device_error_impl(c);
     if (s != OD_OK) return s;
     const od::Plan &p = c->plan;
     const int par = (int)(c->steps & 1);
@@ -594,13 +805,15 @@ od_status od_stats_get(od_ctx *c, od_stats *out) {
     if (!c || !out) return fail(OD_EINVAL, "null argument");
     DeviceGuard dg(c->device);
     memset(out, 0, sizeof *out);
-    od_status s = check_device_error(c);
+    od_status s = check_device_error_impl(c);
     out->steps_done = c->steps;
     out->kernel_launches = c->launches;
     out->api_calls = c->api_calls;
     out->graph_launches = c->graph_launches;
     out->path = c->path;
     out->persistent_grid = c->persistent_grid;
+    out->tuned = c->tuned ? 1 : 0;
+    out->tune_ms_per_step = c->tune_ms;
     od::plan_info(c->plan, &out->plan);
     return s;
 }

@@ -198,13 +198,24 @@ bool tile_shape_supported(int threads, int cpt, int amode) {
     return tile_kernel(amode, threads, cpt, 0) != nullptr;
 }
 
+// The dynamic shared-memory cap is per kernel function and shared by every
+// context in the process, so it is raised once to what the hardware allows
+// (227 KB per CTA less the kernel's static shared memory) and never lowered:
+// the launch's own size decides occupancy, the cap only permits it.
 cudaError_t prepare_tile_kernels(int threads, int cpt, int amode, int smem_bytes) {
-    void *fns[3] = {tile_kernel(amode, threads, cpt, 0), tile_kernel(amode, threads, cpt, 1),
-                    tile_kernel(amode, threads, cpt, 2)};
+    void *fns[4] = {tile_kernel(amode, threads, cpt, 0), tile_kernel(amode, threads, cpt, 1),
+                    tile_kernel(amode, threads, cpt, 2), tile_kernel(amode, threads, cpt, 3)};
     for (void *f : fns) {
         if (!f) return cudaErrorInvalidValue;
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, f);
         if (e != cudaSuccess) return e;
+        const int cap = 232448 - (int)fa.sharedSizeBytes;
+        if (smem_bytes > cap) return cudaErrorInvalidValue;
+        if (fa.maxDynamicSharedSizeBytes < cap) {
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaSuccess;
 }
@@ -224,6 +235,15 @@ cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, in
     if (!f) return cudaErrorInvalidValue;
     if (grid <= 0) return cudaSuccess;
     void *args[] = {(void *)&a};
+    return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, (size_t)smem_bytes, s);
+}
+
+cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int grid, int threads,
+                               int cpt, int amode, int smem_bytes, cudaStream_t s) {
+    void *f = tile_kernel(amode, threads, cpt, 3);
+    if (!f) return cudaErrorInvalidValue;
+    if (grid <= 0 || njobs <= 0) return cudaSuccess;
+    void *args[] = {(void *)&jobs, (void *)&first, (void *)&njobs};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, (size_t)smem_bytes, s);
 }
 

@@ -19,6 +19,12 @@ cudaError_t prepare_tile_kernels(int threads, int cpt, int amode, int smem_bytes
 cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, int amode, bool push, int smem_bytes,
                          cudaStream_t s);
 
+// One fused step of several jobs (continuous batching): jobs[j] (device
+// array) is job j's KArgs with its source parity, first[j] its first block
+// (device array of njobs+1 prefix sums, first[njobs] = grid).
+cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int grid, int threads,
+                               int cpt, int amode, int smem_bytes, cudaStream_t s);
+
 // Persistent ticket kernel over a.iters steps.
 cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, int amode, int smem_bytes,
                               cudaStream_t s);

@@ -23,7 +23,7 @@
 
 namespace od {
 od_status set_last_error(od_status s, const std::string &msg);  // od_api.cu
-}
+}  // namespace od
 
 namespace {
 

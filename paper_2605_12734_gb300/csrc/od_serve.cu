@@ -1,0 +1,505 @@
+// od_serve.cu -- serving loop: independent overdecomposed solves submitted as
+// they arrive, admitted under an HBM budget, kept resident on the device and
+// advanced together (continuous batching).
+//
+// One worker thread owns the device side.  Each pass it
+//   1. admits queued jobs in arrival order while a slot is free and the
+//      budget pool (one device allocation, first-fit) has room for the job's
+//      arena -- a job larger than the whole budget is refused at submit;
+//   2. launches ONE fused step for every running job (k_tiles_multi: each
+//      block runs one tile of one job, each job at its own step and parity),
+//      so jobs that arrive while others run join the very next launch and a
+//      finished job simply drops out of the next one;
+//   3. watches the events of launches in flight (at most two ahead) and marks
+//      a job done when the launch holding its last step has completed.
+// A job's result stays on the device until the client fetches and releases
+// it.  Jobs never share memory, so each result is bit-identical to the same
+// job solved alone.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "od.h"
+#include "od_ctx.h"
+#include "od_internal.h"
+#include "od_kernels.h"
+#include "od_plan.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+od_status fail(od_status s, const std::string &m) { return od::set_last_error(s, m); }
+
+// First-fit allocator over one device allocation (offsets, 256-byte units).
+class Pool {
+public:
+    void reset(size_t size) {
+        size_ = size;
+        free_.clear();
+        if (size) free_[0] = size;
+        used_ = peak_ = 0;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                used_ += bytes;
+                peak_ = std::max(peak_, used_);
+                return true;
+            }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t size() const { return size_; }
+    size_t used() const { return used_; }
+    size_t peak() const { return peak_; }
+
+private:
+    size_t size_ = 0, used_ = 0, peak_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+struct Job {
+    uint64_t id = 0;
+    od_config cfg{};
+    std::vector<int32_t> cuts[3];
+    int32_t iters = 0;
+    int64_t steps_enq = 0;      // steps enqueued on the device
+    int state = OD_JOB_QUEUED;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    size_t off = 0, bytes = 0;
+    od_ctx *ctx = nullptr;
+    int64_t done_batch = -1;    // launch index holding the job's last step
+    int64_t cells = 0;
+    std::string err;
+};
+
+struct Batch {
+    int64_t index;
+    cudaEvent_t ev;
+};
+
+}  // namespace
+
+struct od_server {
+    od_server_config cfg{};
+    int device = 0;
+    char *pool_base = nullptr;
+    bool own_pool = false;
+    Pool pool;
+    cudaStream_t compute = nullptr, admit = nullptr;
+    KArgs *d_jobs[2] = {nullptr, nullptr};
+    int32_t *d_first[2] = {nullptr, nullptr};
+    int32_t max_jobs = 0;
+    int threads = 128, cpt = 4, stages = 4, arith = 2, smem_cap = 0;
+    std::vector<cudaEvent_t> free_events;
+    std::deque<Batch> inflight;
+    int64_t next_batch = 0;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Job *> queue;
+    std::vector<Job *> running;
+    std::unordered_map<uint64_t, Job *> jobs;
+    uint64_t next_id = 1;
+    bool stop = false;
+    Clock::time_point t0;
+    // statistics
+    int64_t launches = 0, done = 0, failed = 0;
+    double updates_done = 0;
+    std::string worker_error;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+od_config job_config(od_server *s, Job *j) {
+    od_config c = j->cfg;
+    for (int a = 0; a < 3; ++a) {
+        const int32_t *p = j->cuts[a].empty() ? nullptr : j->cuts[a].data();
+        if (a == 0) c.cuts_x = p;
+        if (a == 1) c.cuts_y = p;
+        if (a == 2) c.cuts_z = p;
+    }
+    c.path = OD_PATH_FUSED;
+    c.autotune = 0;
+    c.threads = s->threads;
+    c.cells_per_thread = s->cpt;
+    c.stages = s->stages;
+    c.arith = s->arith;
+    c.stream_pool = 1;
+    c.device = s->device;
+    c.stream = s->admit;
+    return c;
+}
+
+// Admit queued jobs (called with the lock held; drops it around od_create).
+void admit(od_server *s, std::unique_lock<std::mutex> &lk) {
+    while (!s->queue.empty() && (s->cfg.max_active <= 0 || (int)s->running.size() < s->cfg.max_active) &&
+           (int)s->running.size() < s->max_jobs) {
+        Job *j = s->queue.front();
+        size_t off = 0;
+        if (!s->pool.alloc(j->bytes, &off)) return;  // wait for memory
+        s->queue.pop_front();
+        j->off = off;
+        od_config c = job_config(s, j);
+        c.arena = s->pool_base + off;
+        c.arena_bytes = j->bytes;
+        lk.unlock();
+        od_ctx *ctx = nullptr;
+        od_status st = od_create(&ctx, &c);
+        std::string msg = st == OD_OK ? "" : od_last_error();
+        lk.lock();
+        if (st != OD_OK || ctx->plan.stage_doubles * s->stages * 8 + 256 > s->smem_cap) {
+            if (ctx) od_destroy(ctx);
+            s->pool.release(j->off, j->bytes);
+            j->state = OD_JOB_FAILED;
+            j->err = st == OD_OK ? "tile needs more shared memory than the server's launch shape" : msg;
+            s->failed++;
+            s->cv_done.notify_all();
+            continue;
+        }
+        j->ctx = ctx;
+        j->t_admit = s->now();
+        if (j->iters == 0) {  // nothing to run: done at admission
+            j->state = OD_JOB_DONE;
+            j->t_done = j->t_admit;
+            s->done++;
+            s->cv_done.notify_all();
+            continue;
+        }
+        j->state = OD_JOB_RUNNING;
+        s->running.push_back(j);
+    }
+}
+
+// Retire launches that completed (lock held).
+void retire(od_server *s) {
+    while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().ev) == cudaSuccess) {
+        const Batch b = s->inflight.front();
+        s->inflight.pop_front();
+        s->free_events.push_back(b.ev);
+        const double t = s->now();
+        for (auto &kv : s->jobs) {
+            Job *j = kv.second;
+            if (j->state == OD_JOB_RUNNING && j->done_batch == b.index) {
+                j->state = OD_JOB_DONE;
+                j->t_done = t;
+                j->ctx->steps = j->iters;
+                s->done++;
+                s->updates_done += (double)j->cells * j->iters;
+            }
+        }
+        s->cv_done.notify_all();
+    }
+    cudaGetLastError();  // cudaErrorNotReady is not an error here
+}
+
+// One fused step of every running job that still has steps (lock held).
+bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf) {
+    hk.clear();
+    hf.clear();
+    int32_t grid = 0, max_sd = 0;
+    std::vector<Job *> in;
+    for (Job *j : s->running) {
+        if (j->done_batch >= 0 || j->steps_enq >= j->iters) continue;
+        KArgs a = od::base_args(j->ctx);
+        a.tile_begin = 0;
+        a.parity = (int32_t)(j->steps_enq & 1);
+        a.stages = s->stages;
+        hk.push_back(a);
+        hf.push_back(grid);
+        grid += (int32_t)j->ctx->plan.tiles.size();
+        max_sd = std::max(max_sd, j->ctx->plan.stage_doubles);
+        in.push_back(j);
+    }
+    if (in.empty()) return false;
+    hf.push_back(grid);
+    const int slot = (int)(s->next_batch & 1);
+    cudaMemcpyAsync(s->d_jobs[slot], hk.data(), hk.size() * sizeof(KArgs), cudaMemcpyHostToDevice, s->compute);
+    cudaMemcpyAsync(s->d_first[slot], hf.data(), hf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s->compute);
+    const int smem = 256 + s->stages * max_sd * 8;
+    cudaError_t e = od::launch_tiles_multi(s->d_jobs[slot], s->d_first[slot], (int32_t)in.size(), grid, s->threads,
+                                           s->cpt, s->arith, smem, s->compute);
+    if (e != cudaSuccess) {
+        s->worker_error = std::string("k_tiles_multi: ") + cudaGetErrorString(e);
+        return false;
+    }
+    s->launches++;
+    const int64_t idx = s->next_batch++;
+    for (Job *j : in) {
+        j->steps_enq++;
+        if (j->steps_enq == j->iters) j->done_batch = idx;
+    }
+    cudaEvent_t ev;
+    if (s->free_events.empty()) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    else {
+        ev = s->free_events.back();
+        s->free_events.pop_back();
+    }
+    cudaEventRecord(ev, s->compute);
+    s->inflight.push_back({idx, ev});
+    return true;
+}
+
+void worker_main(od_server *s) {
+    cudaSetDevice(s->device);
+    std::vector<KArgs> hk;
+    std::vector<int32_t> hf;
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        admit(s, lk);
+        retire(s);
+        // drop finished jobs from the running set (their memory stays until release)
+        s->running.erase(std::remove_if(s->running.begin(), s->running.end(),
+                                        [](Job *j) { return j->state != OD_JOB_RUNNING; }),
+                         s->running.end());
+        bool launched = false;
+        if (s->inflight.size() < 2 && s->worker_error.empty()) launched = launch_batch(s, hk, hf);
+        if (launched) continue;
+        if (!s->inflight.empty()) {
+            // wait for the oldest launch outside the lock
+            cudaEvent_t ev = s->inflight.front().ev;
+            lk.unlock();
+            cudaEventSynchronize(ev);
+            lk.lock();
+            continue;
+        }
+        s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+    }
+}
+
+Job *find(od_server *s, uint64_t id) {
+    auto it = s->jobs.find(id);
+    return it == s->jobs.end() ? nullptr : it->second;
+}
+
+}  // namespace
+
+extern "C" {
+
+void od_server_config_default(od_server_config *c) {
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->hbm_budget_bytes = 1ull << 30;
+    c->max_active = 0;
+    c->max_jobs_per_launch = 256;
+    c->arith = -1;
+}
+
+od_status od_server_create(od_server **out, const od_server_config *cfg) {
+    if (!out || !cfg) return fail(OD_EINVAL, "null argument");
+    *out = nullptr;
+    if (cfg->hbm_budget_bytes < (1u << 20)) return fail(OD_EINVAL, "budget below 1 MiB");
+    od_server *s = new od_server();
+    s->cfg = *cfg;
+    s->device = cfg->device;
+    s->threads = cfg->threads ? cfg->threads : 128;
+    s->cpt = cfg->cells_per_thread ? cfg->cells_per_thread : 4;
+    s->stages = cfg->stages ? cfg->stages : 4;
+    s->arith = cfg->arith >= 0 ? cfg->arith : 2;
+    s->max_jobs = cfg->max_jobs_per_launch > 0 ? cfg->max_jobs_per_launch : 256;
+    s->t0 = Clock::now();
+    auto bail = [&](od_status st, const std::string &m) {
+        od_server_destroy(s);
+        return fail(st, m);
+    };
+    if (cudaSetDevice(s->device) != cudaSuccess) return bail(OD_ECUDA, "cannot select the CUDA device");
+    if (!od::tile_shape_supported(s->threads, s->cpt, s->arith)) return bail(OD_EINVAL, "unsupported tile shape");
+    if (cfg->pool) {
+        if ((uintptr_t)cfg->pool & 255u) return bail(OD_EINVAL, "pool must be 256-byte aligned");
+        s->pool_base = (char *)cfg->pool;
+    } else {
+        if (cudaMalloc(&s->pool_base, cfg->hbm_budget_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            s->pool_base = nullptr;
+            return bail(OD_ENOMEM, "cannot allocate the HBM budget pool");
+        }
+        s->own_pool = true;
+    }
+    s->pool.reset(cfg->hbm_budget_bytes);
+    if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(OD_ECUDA, "cannot create streams");
+    for (int k = 0; k < 2; ++k)
+        if (cudaMalloc(&s->d_jobs[k], (size_t)s->max_jobs * sizeof(KArgs)) != cudaSuccess ||
+            cudaMalloc(&s->d_first[k], (size_t)(s->max_jobs + 1) * sizeof(int32_t)) != cudaSuccess)
+            return bail(OD_ENOMEM, "cannot allocate launch tables");
+    s->smem_cap = 200 * 1024;
+    if (od::prepare_tile_kernels(s->threads, s->cpt, s->arith, s->smem_cap) != cudaSuccess)
+        return bail(OD_ECUDA, "cannot configure the tile kernels");
+    s->worker = std::thread(worker_main, s);
+    *out = s;
+    return OD_OK;
+}
+
+od_status od_server_submit(od_server *s, const od_config *job, int32_t iters, uint64_t *job_id) {
+    if (!s || !job || !job_id || iters < 0) return fail(OD_EINVAL, "bad arguments");
+    Job *j = new Job();
+    j->cfg = *job;
+    const int32_t *cp[3] = {job->cuts_x, job->cuts_y, job->cuts_z};
+    const int32_t nc[3] = {job->ncuts_x, job->ncuts_y, job->ncuts_z};
+    for (int a = 0; a < 3; ++a)
+        if (cp[a] && nc[a] > 0) j->cuts[a].assign(cp[a], cp[a] + nc[a] + 1);
+    j->iters = iters;
+    od::Plan plan;
+    std::string err;
+    od_config c = job_config(s, j);
+    od_status st = od::build_plan(&c, &plan, &err);
+    if (st != OD_OK) {
+        delete j;
+        return fail(st, err);
+    }
+    j->bytes = plan.arena_bytes;
+    j->cells = plan.cells;
+    if (j->bytes > s->pool.size()) {
+        delete j;
+        return fail(OD_EBUDGET, "job needs more device memory than the whole budget");
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    j->id = s->next_id++;
+    j->t_submit = s->now();
+    s->jobs[j->id] = j;
+    s->queue.push_back(j);
+    *job_id = j->id;
+    s->cv_work.notify_all();
+    return OD_OK;
+}
+
+od_status od_server_wait(od_server *s, uint64_t id, double timeout_s, int32_t *state) {
+    if (!s) return fail(OD_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    Job *j = find(s, id);
+    if (!j) return fail(OD_ENOTFOUND, "unknown job");
+    const auto until = Clock::now() + std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s);
+    while (j->state == OD_JOB_QUEUED || j->state == OD_JOB_RUNNING)
+        if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout) break;
+    if (state) *state = j->state;
+    return OD_OK;
+}
+
+od_status od_server_job_info(od_server *s, uint64_t id, od_job_info *out) {
+    if (!s || !out) return fail(OD_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    Job *j = find(s, id);
+    if (!j) return fail(OD_ENOTFOUND, "unknown job");
+    memset(out, 0, sizeof *out);
+    out->state = j->state;
+    out->iters = j->iters;
+    out->cells = j->cells;
+    out->arena_bytes = j->bytes;
+    out->t_submit = j->t_submit;
+    out->t_admit = j->t_admit;
+    out->t_done = j->t_done;
+    return OD_OK;
+}
+
+od_status od_server_fetch(od_server *s, uint64_t id, double *dst, int32_t dst_is_device) {
+    if (!s || !dst) return fail(OD_EINVAL, "null argument");
+    od_ctx *ctx = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        Job *j = find(s, id);
+        if (!j) return fail(OD_ENOTFOUND, "unknown job");
+        if (j->state != OD_JOB_DONE) return fail(OD_ESTATE, "job not done");
+        ctx = j->ctx;
+    }
+    return ctx ? od_read(ctx, dst, dst_is_device) : fail(OD_ESTATE, "job has no state");
+}
+
+od_status od_server_release(od_server *s, uint64_t id) {
+    if (!s) return fail(OD_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    Job *j = find(s, id);
+    if (!j) return fail(OD_ENOTFOUND, "unknown job");
+    if (j->state == OD_JOB_RUNNING) return fail(OD_ESTATE, "job still running");
+    if (j->state == OD_JOB_QUEUED) s->queue.erase(std::find(s->queue.begin(), s->queue.end(), j));
+    od_ctx *ctx = j->ctx;
+    const bool had_memory = ctx != nullptr;
+    s->jobs.erase(id);
+    lk.unlock();
+    if (ctx) od_destroy(ctx);
+    lk.lock();
+    if (had_memory) s->pool.release(j->off, j->bytes);
+    delete j;
+    s->cv_work.notify_all();
+    return OD_OK;
+}
+
+od_status od_server_stats(od_server *s, od_server_stats_t *out) {
+    if (!s || !out) return fail(OD_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(out, 0, sizeof *out);
+    out->queued = (int64_t)s->queue.size();
+    out->running = (int64_t)s->running.size();
+    out->done = s->done;
+    out->failed = s->failed;
+    out->launches = s->launches;
+    out->updates_done = s->updates_done;
+    out->pool_used = s->pool.used();
+    out->pool_peak = s->pool.peak();
+    out->seconds = s->now();
+    if (!s->worker_error.empty()) return fail(OD_ECUDA, s->worker_error);
+    return OD_OK;
+}
+
+od_status od_server_destroy(od_server *s) {
+    if (!s) return OD_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv_work.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->device);
+    if (s->compute) cudaStreamSynchronize(s->compute);
+    for (auto &kv : s->jobs) {
+        if (kv.second->ctx) od_destroy(kv.second->ctx);
+        delete kv.second;
+    }
+    for (auto &b : s->inflight) cudaEventDestroy(b.ev);
+    for (auto e : s->free_events) cudaEventDestroy(e);
+    for (int k = 0; k < 2; ++k) {
+        if (s->d_jobs[k]) cudaFree(s->d_jobs[k]);
+        if (s->d_first[k]) cudaFree(s->d_first[k]);
+    }
+    if (s->compute) cudaStreamDestroy(s->compute);
+    if (s->admit) cudaStreamDestroy(s->admit);
+    if (s->own_pool && s->pool_base) cudaFree(s->pool_base);
+    delete s;
+    return OD_OK;
+}
+
+}  // extern "C"

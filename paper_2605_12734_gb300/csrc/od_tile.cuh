@@ -356,6 +356,35 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles(const KArgs a) {
                                 reinterpret_cast<PushInfo *>(smem + kSmemPush), -1);
 }
 
+// Continuous batching: one fused step of several independent jobs in one
+// launch.  jobs[j] holds job j's tables and source parity; job j owns blocks
+// [first[j], first[j+1]); every block runs one tile of its job.  All jobs
+// share the launch's CTA shape, ring depth and slot size.
+template <int NT, int CPT, int AM>
+__global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles_multi(const KArgs *jobs, const int32_t *first,
+                                                                   int32_t njobs) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int32_t s_job;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = njobs - 1;  // last job whose first block <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first[mid] <= (int32_t)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const KArgs &a = jobs[s_job];
+    if (blockDim.x != NT) {
+        if (threadIdx.x == 0) record_err(a.err, OD_ERR_BAD_LAUNCH, -1, -1);
+        return;
+    }
+    Ring ring = ring_setup<NT>(a, smem);
+    run_tile<NT, CPT, true, AM>(a, (int)blockIdx.x - first[s_job], a.parity, ring,
+                                reinterpret_cast<PushInfo *>(smem + kSmemPush), -1);
+}
+
 // Persistent kernel: CTAs take tickets in step-major order; ticket
 // r*ntiles + pos is step r of tile order[pos] (reversed on odd r when
 // order_mode == 1).  Before running it, thread 0 waits until every tile it

@@ -12,13 +12,15 @@
 
 namespace od {
 
-// kind 0: k_tiles without push, 1: k_tiles with push, 2: k_persistent
+// kind 0: k_tiles without push, 1: k_tiles with push, 2: k_persistent,
+// 3: k_tiles_multi
 void *OD_CAT(tile_kernel_am, OD_AMODE)(int threads, int cpt, int kind) {
     using namespace tile;
 #define OD_CASE(NT_, C_)                                                          \
     if (threads == NT_ && cpt == C_) {                                            \
         if (kind == 0) return (void *)k_tiles<NT_, C_, false, OD_AMODE>;          \
         if (kind == 1) return (void *)k_tiles<NT_, C_, true, OD_AMODE>;           \
+        if (kind == 3) return (void *)k_tiles_multi<NT_, C_, OD_AMODE>;           \
         return (void *)k_persistent<NT_, C_, OD_AMODE>;                           \
     }
     OD_CASE(128, 2) OD_CASE(128, 4) OD_CASE(128, 8)

@@ -1,0 +1,114 @@
+"""Serving loop and autotuner on the GPU.
+
+Serving: jobs of different sizes, decompositions and iteration counts are
+submitted while others run; each result must equal the oracle and the same
+job solved alone, bit for bit (the jobs overlap on the device, their state
+never does).  Admission respects the HBM budget and the slot limit.
+
+Autotuner: the tuned context computes the same bits, reports that it was
+tuned, and a second context with the same decomposition takes the choice
+from the cache."""
+import os
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def od():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_12734_gb300 import build
+    build.build()
+    import paper_2605_12734_gb300 as pkg
+    return pkg
+
+
+def same(a, b):
+    return np.array_equal(np.ascontiguousarray(a).view(np.uint64), np.ascontiguousarray(b).view(np.uint64))
+
+
+JOBS = [  # (edge, split, iters, seed, init_mode)
+    (40, (2, 2, 2), 12, 11, 1), (33, (3, 3, 3), 7, 12, 0), (64, (4, 4, 4), 20, 13, 1),
+    (27, (3, 3, 3), 1, 14, 1), (48, (2, 2, 2), 0, 15, 1), (56, (4, 4, 4), 9, 16, 1),
+    (64, (2, 2, 2), 15, 17, 1), (35, (2, 2, 2), 25, 18, 0),
+]
+
+
+def test_jobs_in_the_mix_match_alone_and_oracle(od):
+    results = {}
+    with od.Server(256 << 20, max_active=4) as srv:
+        ids = []
+        for k, (e, sp, it, seed, mode) in enumerate(JOBS):
+            ids.append(srv.submit(e, e, e, it, split=sp, seed=seed, init_mode=mode))
+            if k % 3 == 2:
+                time.sleep(0.002)  # arrivals spread while earlier jobs run
+        for jid, (e, sp, it, seed, mode) in zip(ids, JOBS):
+            assert srv.wait(jid, 60.0) == od._native.OD_JOB_DONE, srv.info(jid)
+            results[jid] = srv.fetch(jid)
+            info = srv.info(jid)
+            assert info["t_submit"] <= info["t_admit"] <= info["t_done"]
+            srv.release(jid)
+        st = srv.stats()
+        assert st["done"] == len(JOBS) and st["failed"] == 0
+        assert st["pool_used"] == 0 and st["launches"] >= max(j[2] for j in JOBS)
+    for jid, (e, sp, it, seed, mode) in zip(ids, JOBS):
+        want = oracle.solve(e, e, e, seed, mode, it)
+        assert same(results[jid], want), (e, sp, it)
+        with od.Jacobi3D(e, e, e, split=sp, seed=seed, init_mode=mode, path="fused") as alone:
+            alone.step(it)
+            assert same(results[jid], alone.read())
+
+
+def test_budget_admission_and_release(od):
+    e, sp = 48, (2, 2, 2)
+    need = od.plan(e, e, e, split=sp, threads=128, cells_per_thread=4, stages=4, arith=2)["arena_bytes"]
+    budget = int(need * 2.5)  # room for two jobs at a time
+    with od.Server(budget) as srv:
+        with pytest.raises(od.ODError) as ei:
+            srv.submit(200, 200, 200, 1, split=(1, 1, 1))
+        assert ei.value.status == od._native.OD_EBUDGET
+        ids = [srv.submit(e, e, e, 30, split=sp, seed=s) for s in range(5)]
+        peak = 0
+        for jid in ids:
+            assert srv.wait(jid, 60.0) == od._native.OD_JOB_DONE
+            peak = max(peak, srv.stats()["pool_peak"])
+            srv.release(jid)
+        assert peak <= budget
+        # a queued job can be released (cancelled) before it runs
+        with od.Server(budget, max_active=1) as srv2:
+            a = srv2.submit(e, e, e, 200, split=sp, seed=1)
+            b = srv2.submit(e, e, e, 200, split=sp, seed=2)
+            c = srv2.submit(e, e, e, 5, split=sp, seed=3)
+            srv2.release(c)
+            assert srv2.wait(a, 60.0) == od._native.OD_JOB_DONE
+            assert srv2.wait(b, 60.0) == od._native.OD_JOB_DONE
+    want = oracle.solve(e, e, e, 4, 1, 30)
+    with od.Server(budget) as srv:
+        j = srv.submit(e, e, e, 30, split=sp, seed=4)
+        assert srv.wait(j, 60.0) == od._native.OD_JOB_DONE
+        assert same(srv.fetch(j), want)
+
+
+def test_autotune_same_bits_and_cache(od, tmp_path, monkeypatch):
+    monkeypatch.setenv("OD_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    nx, ny, nz = 96, 64, 48
+    want = oracle.solve(nx, ny, nz, 8, 1, 6)
+    with od.Jacobi3D(nx, ny, nz, split=(3, 2, 2), seed=8, path="persistent", autotune=True) as s:
+        st = s.stats()
+        assert st["tuned"] == 1 and st["tune_ms_per_step"] > 0
+        s.step(6)
+        assert same(s.read(), want)
+    lines = (tmp_path / "tune.txt").read_text().splitlines()
+    assert len(lines) == 1
+    t0 = time.perf_counter()
+    with od.Jacobi3D(nx, ny, nz, split=(3, 2, 2), seed=8, path="persistent", autotune=True) as s2:
+        assert abs(s2.stats()["tune_ms_per_step"] - st["tune_ms_per_step"]) < 1e-9  # from the cache
+        assert s2.stats()["plan"]["threads"] == st["plan"]["threads"]
+    assert len((tmp_path / "tune.txt").read_text().splitlines()) == 1
