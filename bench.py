@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="also time every path at ODF 1, 8, 64, 512, 4096 (adds a 'sweep' key)")
-    ap.add_argument("--tune", action="store_true", help="autotune the tiling at create")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (default: od_create times candidate execution shapes first)")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--cpt", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
@@ -153,7 +154,7 @@ def profiled_traffic(args, plan):
 
 
 # bumped whenever the tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 6
+KERNEL_REV = 7
 
 
 def measured_peaks():
@@ -266,12 +267,13 @@ def run_ours(args):
         raise SystemExit("--odf must be a cube")
     stream = torch.cuda.Stream(device=dev)
     tune_kw = dict(threads=args.threads, cells_per_thread=args.cpt, stages=args.stages,
-                   tile_y=args.tile_y, tile_z=args.tile_z, arith=args.arith, autotune=args.tune, device=dev)
+                   tile_y=args.tile_y, tile_z=args.tile_z, arith=args.arith,
+                   autotune=not args.no_tune and not (args.threads or args.cpt or args.stages or args.arith >= 0),
+                   device=dev)
     from paper_2605_12734_gb300 import inputs
     if args.workload == "uneven":
         w = inputs.uneven_768()
         dims, dec, name = (w.nx, w.ny, w.nz), dict(cuts=w.cuts), w.name
-        tune_kw["autotune"] = True
     elif args.workload == "ceiling":
         w = inputs.ceiling_1024()
         dims, dec, name = (w.nx, w.ny, w.nz), dict(split=w.split), w.name

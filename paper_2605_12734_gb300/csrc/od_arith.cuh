@@ -205,6 +205,83 @@ OD_HD double div6_chain(const Unpacked &s) {
     return f64_from(((er - 1u) << 52) + Q);
 }
 
+// ---------------------------------------------------------------- window chain
+//
+// A cheaper chain when its operands are close in magnitude.  All K+1
+// operands are aligned once to a common 64-bit fixed-point window: with
+// emax the largest biased exponent, operand t becomes m_t << (8 - (emax -
+// e_t)), so the largest operands put their hidden bit at bit 60 and -- when
+// every exponent lies within 8 of emax -- no operand loses a bit.  Each add is
+// then a plain 64-bit add followed by rounding the partial sum to 53
+// significant bits at its own binade (position p = msb - 52, 0..11), exactly
+// as the IEEE add would; nothing below the window is ever dropped, so no
+// sticky bit is needed.  The value of a window word W is W * 2^(emax - 1083).
+
+OD_HD uint32_t clz32(uint32_t x) {
+#if defined(__CUDA_ARCH__)
+    return (uint32_t)__clz((int)x);
+#else
+    return x ? (uint32_t)__builtin_clz(x) : 32u;
+#endif
+}
+
+// Round W (whose top set bit is at 52 + p, p in [0, 11]) to 53 significant
+// bits, nearest even; returns p.
+OD_HD uint32_t round_window(uint64_t &W) {
+    const uint32_t hi = (uint32_t)(W >> 32), lo = (uint32_t)W;
+    const uint32_t p = 11u - clz32(hi);           // hi >= 2^20
+    const uint32_t unit = 1u << p;
+    const uint32_t rem = lo & (unit - 1u);
+    const uint32_t half = unit >> 1;
+    const uint32_t up = (uint32_t)(rem > half) | ((uint32_t)(rem == half) & (uint32_t)(p != 0u) & (lo >> p));
+    W = (W - rem) + ((uint64_t)(up & 1u) << p);
+    return p;
+}
+
+// First K adds of x[0..K] in the window; ok = false when an operand is not
+// positive, has a biased exponent outside [4, 2040], or lies more than 8
+// binades below the largest.  Returns the rounded window word and sets
+// emax and p (the last rounding position).
+template <int K>
+OD_HD uint64_t window_chain(const double *x, bool &ok, uint32_t &emax, uint32_t &p) {
+    uint32_t e[K + 1];
+    uint64_t m[K + 1];
+    uint32_t lo_e = 0xFFFFFFFFu, hi_e = 0;
+#pragma unroll
+    for (int t = 0; t <= K; ++t) {
+        const uint64_t b = f64_bits(x[t]);
+        e[t] = (uint32_t)(b >> 52);  // includes the sign bit: negative -> >= 2048
+        m[t] = (b & kFrac) | kHid;
+        lo_e = e[t] < lo_e ? e[t] : lo_e;
+        hi_e = e[t] > hi_e ? e[t] : hi_e;
+    }
+    ok = (lo_e - 4u <= 2036u) & (hi_e - 4u <= 2036u) & (hi_e - lo_e <= 8u);
+    emax = hi_e;
+    uint64_t W = m[0] << ((8u - (hi_e - e[0])) & 63u);
+    p = 0;
+#pragma unroll
+    for (int t = 1; t <= K; ++t) {
+        W += m[t] << ((8u - (hi_e - e[t])) & 63u);
+        p = round_window(W);
+    }
+    return W;
+}
+
+// The window word as a binary64 (53 significant bits at position p).
+OD_HD double pack_window(uint64_t W, uint32_t emax, uint32_t p) {
+    const uint64_t M = W >> p;                            // [2^52, 2^53)
+    const uint64_t E = (uint64_t)(emax - 8u + p);         // biased exponent
+    return f64_from(((E - 1u) << 52) + M);
+}
+
+// s / 6 of the window value (see div6), s's exponent emax - 8 + p >= 4.
+OD_HD double div6_window(uint64_t W, uint32_t emax, uint32_t p) {
+    Unpacked u;
+    u.m = W >> p;
+    u.e = emax - 8u + p;
+    return div6_chain(u);
+}
+
 // ---------------------------------------------------------------- update
 
 // s / 6 on the integer pipes without a branch; ok = false when s is outside
@@ -240,11 +317,13 @@ OD_HD double jacobi_update_ieee(double W, double E, double S, double N, double D
 // The same update with its operations placed by AM, never changing a bit:
 //   AM = 0  every add and the division as IEEE operations (FP64 pipe)
 //   AM = 1  IEEE adds, division by 6 on the integer pipes
-//   AM = 1+k, k = 1..5: the first k adds as an unpacked integer chain, the
+//   AM = 1+k, k = 1..5: the first k adds in the integer window chain, the
 //           remaining 5-k as IEEE adds, the division on the integer pipes.
 // Branch-free: ok = false when an operand or the sum left the integer
-// routines' domain; the result is then garbage and the caller recomputes the
-// cell with jacobi_update_ieee (a rare path kept out of the hot loop).
+// routines' domain (for the window: operands more than 8 binades apart,
+// zero, negative, tiny or huge); the result is then garbage and the caller
+// recomputes the cell with jacobi_update_ieee (a rare path kept out of the
+// hot loop).
 template <int AM>
 OD_HD double jacobi_update_fast(double W, double E, double S, double N, double D, double U, bool &ok) {
     constexpr int K = AM > 1 ? AM - 1 : 0;
@@ -260,23 +339,19 @@ OD_HD double jacobi_update_fast(double W, double E, double S, double N, double D
         return div6_fast(s, ok);
     } else {
         const double x[6] = {W, E, S, N, D, U};
-        Unpacked acc, b;
-        bool good = unpack_chain(x[0], acc);
-#pragma unroll
-        for (int t = 1; t <= K; ++t) {
-            good &= unpack_chain(x[t], b);
-            acc = add_chain(acc, b);
-        }
+        bool good;
+        uint32_t emax, p;
+        const uint64_t Wd = window_chain<K>(x, good, emax, p);
         if constexpr (K == 5) {
             ok = good;
-            return div6_chain(acc);
+            return div6_window(Wd, emax, p);
         } else {
-            double s = pack_chain(acc);
+            double s = pack_window(Wd, emax, p);
 #pragma unroll
             for (int t = K + 1; t <= 5; ++t) s = ieee_add(s, x[t]);
             bool okd;
             const double v = div6_fast(s, okd);
-            ok = good && okd;
+            ok = good & okd;
             return v;
         }
     }
