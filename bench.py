@@ -175,10 +175,14 @@ def oracle_cpu_baseline(edge: int, target_s: float = 12.0):
     oracle.build()
     threads = oracle.max_threads()
     P = oracle.init_padded(edge, edge, edge, 2, inputs.INIT_UNIFORM)
+    # per-iteration cost without the sweep's one-off copy: t(3) - t(1) over 2
     t0 = time.perf_counter()
     oracle.sweep(P, 1, threads)
-    one = time.perf_counter() - t0
-    iters = max(1, min(1000, int(target_s / max(one, 1e-3))))
+    t1 = time.perf_counter()
+    oracle.sweep(P, 3, threads)
+    t3 = time.perf_counter()
+    per_iter = max((t3 - t1) - (t1 - t0), 1e-3) / 2
+    iters = max(1, min(1000, int(target_s / per_iter)))
     t0 = time.perf_counter()
     oracle.sweep(P, iters, threads)
     dt = time.perf_counter() - t0
