@@ -136,6 +136,8 @@ class ClockSampler:
 SMS = 152
 SM_MAX_GHZ = 2.07
 FP64_LANES_PER_SM = 2
+FP64_NOMINAL_GFLOPS = 1250.0
+FLOPS_PER_UPDATE = 6  # 5 additions + 1 division
 
 
 def profiled_traffic(args, plan):
@@ -318,11 +320,13 @@ def run_ours(args):
     launches = st1["kernel_launches"] - st0["kernel_launches"]
 
     # roofline of the tile kernel (it does all of a step's arithmetic and HBM
-    # traffic).  On GB300 the update is bound by the FP64 pipe, not by HBM:
-    # 5 adds + 1 division per cell, of which arithmetic mode m runs
-    # fp64_adds(m) adds on the FP64 pipe and the rest on the integer pipes.
+    # traffic).  On GB300 the update is bound by arithmetic, not by HBM: the
+    # method needs 5 FP64 adds + 1 FP64 division per cell (6 flops), and the
+    # GPU's FP64 rate is 1.25 TFLOP/s nominal.  The kernel runs fp64_adds(m) of
+    # the adds on the FP64 pipe and the rest, with the division, exactly on
+    # the integer pipes.
     fp64_adds = {0: 5, 1: 5, 2: 4, 3: 3, 4: 2, 5: 1, 6: 0}[plan["arith"]]
-    fp64_peak = FP64_LANES_PER_SM * SMS * SM_MAX_GHZ  # G FP64 instructions/s
+    fp64_pipe = FP64_LANES_PER_SM * SMS * SM_MAX_GHZ  # G FP64 instructions/s
     hbm_peak, peak_kind = measured_peaks()
     bytes_step = plan["bytes_per_step"]
     ups = updates_step / (ms_step * 1e-3)
@@ -330,20 +334,19 @@ def run_ours(args):
            "frac": bytes_step / (ms_step * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
            "bytes_per_step": bytes_step,
            "note": "algorithmic bytes: 16 B/cell + 16 B per internal ghost cell + 8 B per Dirichlet ghost cell"}
-    if fp64_adds > 0:
-        roofline = {"bound": "alu", "achieved": fp64_adds * ups / 1e9, "peak": fp64_peak, "unit": "GFLOP/s",
-                    "frac": fp64_adds * ups / 1e9 / fp64_peak, "traffic": None,
-                    "note": (f"binding unit: FP64 pipe; {fp64_adds} of the update's 5 adds run there (the rest "
-                             f"and the division by 6 run exactly on the integer pipes); peak = "
-                             f"{FP64_LANES_PER_SM} FP64 lanes/clk/SM x {SMS} SMs x {SM_MAX_GHZ} GHz, derived "
-                             f"from the 1.25 TFLOP/s FP64 nominal (an FMA counted as 2 flops)"),
-                    "hbm": hbm}
-    else:
-        roofline = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm["frac"], "traffic": None, "note": hbm["note"] + "; peak " + peak_kind}
+    roofline = {"bound": "alu", "achieved": FLOPS_PER_UPDATE * ups / 1e9, "peak": FP64_NOMINAL_GFLOPS,
+                "unit": "GFLOP/s", "frac": FLOPS_PER_UPDATE * ups / 1e9 / FP64_NOMINAL_GFLOPS, "traffic": None,
+                "note": ("algorithmic FP64 work: 5 adds + 1 division per update; peak: GB300 FP64 1.25 TFLOP/s "
+                         "nominal (recipe), = 2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz x 2 flops per FMA; "
+                         f"this kernel runs {fp64_adds} adds per update on the FP64 pipe and the rest with the "
+                         "division, bit-exactly, on the integer pipes"),
+                "fp64_pipe": {"adds_per_update": fp64_adds, "peak_ginst_per_s": fp64_pipe,
+                              "busy_frac_est": fp64_adds * ups / 1e9 / fp64_pipe},
+                "hbm": hbm}
     traffic = profiled_traffic(args, plan)
     if traffic is not None:
         roofline["traffic"] = traffic
+        roofline["traffic_note"] = "DRAM bytes per iteration (ncu, one persistent launch of this kernel build)"
 
     # end to end through the public API with pinned host buffers: each e2e
     # step is a whole solve of the config's 100 iterations: write the initial
