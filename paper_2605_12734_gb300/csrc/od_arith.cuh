@@ -1,7 +1,7 @@
 // od_arith.cuh -- exact IEEE binary64 arithmetic on the integer pipes.
 //
 // GB300 runs FP64 at a small fraction of its FP32/INT32 rate (measured on
-// the pool: DADD ~0.5 Tops/s, DDIV ~0.07 Tops/s for the whole GPU, against
+// GB300: DADD ~0.5 Tops/s, DDIV ~0.07 Tops/s for the whole GPU, against
 // ~19 Tops/s IMAD and ~36 Tops/s FADD), so the Jacobi update
 // (((((W+E)+S)+N)+D)+U)/6 is bound by the FP64 pipe, not by HBM.  These
 // routines compute the SAME correctly rounded binary64 results with integer
