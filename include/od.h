@@ -126,7 +126,9 @@ typedef struct od_config {
                                     never change): 0 all on the FP64 pipe;
                                     1 division by 6 on the integer pipes;
                                     1+k (k = 1..5) also the first k adds on the
-                                    integer pipes; -1 = library default (2) */
+                                    integer pipes; 7 / 8: modes 2 and 3 mixed
+                                    cell by cell (half / a quarter of the cells
+                                    in mode 3); -1 = library default (7) */
     int32_t order;               /* persistent path task order: 0 linear every
                                     step, 1 reversed on odd steps */
     int32_t stream_pool;         /* per-chare path: streams (0 = min(nchares,32)) */
@@ -263,7 +265,7 @@ typedef struct od_server_config {
     int32_t max_jobs_per_launch; /* batch table size (0 = 256) */
     int32_t device;
     int32_t threads, cells_per_thread, stages; /* tile shape for every job (0 = 128, 4, 4) */
-    int32_t arith;               /* as od_config.arith (-1 = 2) */
+    int32_t arith;               /* as od_config.arith (-1 = 7) */
     void *pool;                  /* caller device memory of hbm_budget_bytes, 256-byte
                                     aligned, or NULL: the server allocates it once */
 } od_server_config;

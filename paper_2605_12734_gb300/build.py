@@ -28,7 +28,7 @@ CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-I", INCLUDE,
 SOURCES = ["od_kernels.cu", "od_api.cu", "od_plan.cpp", "od_noalloc.cu", "od_serve.cu"]
 # the tile kernels, compiled once per arithmetic mode (-DOD_AMODE=m)
 TILE_SOURCE = "od_tiles.cu"
-AMODES = range(7)
+AMODES = range(9)
 HEADERS = ["od_internal.h", "od_kernels.h", "od_plan.h", "od_tile.cuh", "od_arith.cuh", "od_ctx.h"]
 
 

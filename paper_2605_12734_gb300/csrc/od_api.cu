@@ -321,8 +321,9 @@ void release(od_ctx *c) {
 // decomposition before the context is built: each candidate is a temporary
 // context (autotune off) laid out in one shared tuning buffer, initialised,
 // stepped twice untimed and then timed with events.  Candidates (in two
-// rounds, coordinate descent): CTA shape x arithmetic mode with the default
-// ring, then ring depth x planes per tile for the best of those.  Every
+// rounds, coordinate descent): CTA shape x arithmetic mode (2, 3 and the
+// mixed 7, 8) with the default ring, then ring depth x planes per tile for
+// the best of those.  Every
 // candidate computes the same bits, so the choice only changes speed.  The
 // winner is cached in a text file (OD_TUNE_CACHE, default
 // $HOME/.cache/libod/tune.txt; "off" disables the cache) keyed by device,
@@ -409,7 +410,7 @@ od_status run_tuning(const od_config *cfg, TuneChoice *best) {
     if (tune_cache_lookup(key, best)) return OD_OK;
 
     const int shapes[6][2] = {{128, 4}, {128, 8}, {256, 4}, {256, 8}, {128, 2}, {256, 2}};
-    const int ariths[3] = {1, 2, 3};
+    const int ariths[4] = {2, 3, 7, 8};
     std::vector<TuneChoice> round1;
     for (auto &sh : shapes)
         for (int am : ariths) {

@@ -17,6 +17,8 @@ void *tile_kernel_am3(int threads, int cpt, int kind);
 void *tile_kernel_am4(int threads, int cpt, int kind);
 void *tile_kernel_am5(int threads, int cpt, int kind);
 void *tile_kernel_am6(int threads, int cpt, int kind);
+void *tile_kernel_am7(int threads, int cpt, int kind);
+void *tile_kernel_am8(int threads, int cpt, int kind);
 
 namespace {
 
@@ -29,6 +31,8 @@ void *tile_kernel(int amode, int threads, int cpt, int kind) {
         case 4: return tile_kernel_am4(threads, cpt, kind);
         case 5: return tile_kernel_am5(threads, cpt, kind);
         case 6: return tile_kernel_am6(threads, cpt, kind);
+        case 7: return tile_kernel_am7(threads, cpt, kind);
+        case 8: return tile_kernel_am8(threads, cpt, kind);
         default: return nullptr;
     }
 }

@@ -18,7 +18,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int32_t kMaxSmem = 232448;  // 227 KB opt-in per CTA on sm_100/sm_103
 constexpr int32_t kSmemHeader = 256;  // mbarriers + neighbour push table
-constexpr int32_t kDefaultArith = 2;   // first add and the division on the integer pipes
+constexpr int32_t kDefaultArith = 7;   // modes 2 and 3 mixed cell by cell
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int32_t round_up(int32_t v, int32_t a) { return (v + a - 1) / a * a; }
@@ -128,8 +128,8 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
     p.tile_y = cfg->tile_y;
     p.tile_z = cfg->tile_z;
     p.amode = cfg->arith < 0 ? kDefaultArith : cfg->arith;
-    if (p.amode > 6) {
-        *err = "arith must be in [0, 6] (or -1 for the default)";
+    if (p.amode > 8) {
+        *err = "arith must be in [0, 8] (or -1 for the default)";
         return OD_EINVAL;
     }
     if (p.threads != 128 && p.threads != 256 && p.threads != 512) {

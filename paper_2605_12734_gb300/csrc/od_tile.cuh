@@ -278,7 +278,15 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
             const uint32_t w = rf[m];
             const int r = (int)(w & 0xFFFFu);
             bool ok;
-            double v = jacobi_update_fast<AM>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
+            // modes 7 and 8 mix the per-cell placement to balance the FP64 and
+            // integer pipes: 7 = every other cell with two window adds, 8 =
+            // one cell in four (m is a compile-time constant after unrolling)
+            constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
+            double v;
+            if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0))
+                v = jacobi_update_fast<3>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
+            else
+                v = jacobi_update_fast<AMa>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
             if (!ok)  // rare: an operand left the integer routines' domain
                 v = update_slow(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r]);
             if (w & kValid) {

@@ -68,7 +68,7 @@ def test_jobs_in_the_mix_match_alone_and_oracle(od):
 
 def test_budget_admission_and_release(od):
     e, sp = 48, (2, 2, 2)
-    need = od.plan(e, e, e, split=sp, threads=128, cells_per_thread=4, stages=4, arith=2)["arena_bytes"]
+    need = od.plan(e, e, e, split=sp, threads=128, cells_per_thread=4, stages=4, arith=7)["arena_bytes"]
     budget = int(need * 2.5)  # room for two jobs at a time
     with od.Server(budget) as srv:
         with pytest.raises(od.ODError) as ei:
