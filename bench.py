@@ -159,6 +159,22 @@ def profiled_traffic(args, plan):
 KERNEL_REV = 8
 
 
+def combine_ranks(ms: float, updates: float, world: int, device: str):
+    """Whole-job timing across replicas: the slowest rank's time (max over
+    ranks) and the updates of all ranks divided by it.  world == 1 needs no
+    process group."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms, updates], dtype=torch.float64, device=device)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms, updates = float(tmax[0].item()), float(tsum[1].item())
+    return ms, updates / (ms * 1e-3)
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -310,13 +326,9 @@ def run_ours(args):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     st1 = solver.stats()
-    if world > 1:
-        t = torch.tensor([ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = combine_ranks(ms, plan["cells"] * args.steps, world, f"cuda:{dev}")
     ms_step = ms / args.steps
     updates_step = plan["cells"]
-    value = updates_step * world / (ms_step * 1e-3)
     launches = st1["kernel_launches"] - st0["kernel_launches"]
 
     # roofline of the tile kernel (it does all of a step's arithmetic and HBM
