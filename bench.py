@@ -184,7 +184,7 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def oracle_cpu_baseline(edge: int, target_s: float = 12.0):
+def oracle_cpu_baseline(edge: int, target_s: float = 10.0):
     """Time the CPU oracle's monolithic sweep (its OpenMP z-plane split) on a
     bounded sample of the same workload: the full edge^3 field, as many
     iterations as fit in about target_s seconds."""
