@@ -68,6 +68,15 @@ def _load():
                                  _I64, _I64, _I64, _DP]
     lib.oracle_max_threads.restype = ctypes.c_int
     lib.oracle_max_threads.argtypes = []
+    lib.oracle2d_init_padded.restype = None
+    lib.oracle2d_init_padded.argtypes = [_I64, _I64, ctypes.c_uint64, ctypes.c_int, _DP]
+    lib.oracle2d_sweep.restype = ctypes.c_int
+    lib.oracle2d_sweep.argtypes = [_I64, _I64, _DP, ctypes.c_int, ctypes.c_int]
+    lib.oracle2d_sweep_decomposed.restype = ctypes.c_int
+    lib.oracle2d_sweep_decomposed.argtypes = [_I64, _I64, ctypes.c_int, ctypes.c_int, _I64P, _I64P, _DP,
+                                              ctypes.c_int]
+    lib.oracle2d_point.restype = ctypes.c_int
+    lib.oracle2d_point.argtypes = [_I64, _I64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _I64, _I64, _DP]
     _lib = lib
     return lib
 
@@ -160,3 +169,46 @@ def solve(nx: int, ny: int, nz: int, seed: int, init_mode: int, iters: int,
 
 def max_threads() -> int:
     return int(_load().oracle_max_threads())
+
+
+# ------------------------------------------------------------------ 2D (5-point)
+
+def init_padded_2d(nx: int, ny: int, seed: int, init_mode: int) -> np.ndarray:
+    """Padded 2D initial field, shape (ny+2, nx+2)."""
+    P = np.empty((ny + 2, nx + 2), dtype=np.float64)
+    _load().oracle2d_init_padded(nx, ny, seed & (2**64 - 1), init_mode, _dp(P))
+    return P
+
+
+def sweep_2d(P: np.ndarray, iters: int, threads: int = 1) -> np.ndarray:
+    Q = np.array(P, dtype=np.float64, copy=True, order="C")
+    ny, nx = (d - 2 for d in Q.shape)
+    if _load().oracle2d_sweep(nx, ny, _dp(Q), iters, threads) != 0:
+        raise MemoryError("oracle2d_sweep failed")
+    return Q
+
+
+def sweep_decomposed_2d(P: np.ndarray, ex, ey, iters: int) -> np.ndarray:
+    Q = np.array(P, dtype=np.float64, copy=True, order="C")
+    ny, nx = (d - 2 for d in Q.shape)
+    ex = np.ascontiguousarray(ex, dtype=np.int64)
+    ey = np.ascontiguousarray(ey, dtype=np.int64)
+    if ex[0] != 0 or ex[-1] != nx or ey[0] != 0 or ey[-1] != ny:
+        raise ValueError("cut lists must run from 0 to the interior extent")
+    rc = _load().oracle2d_sweep_decomposed(nx, ny, len(ex) - 1, len(ey) - 1, _ip(ex), _ip(ey), _dp(Q), iters)
+    if rc != 0:
+        raise ValueError(f"oracle2d_sweep_decomposed failed ({rc})")
+    return Q
+
+
+def point_2d(nx: int, ny: int, seed: int, init_mode: int, iters: int, x: int, y: int) -> float:
+    out = ctypes.c_double()
+    if _load().oracle2d_point(nx, ny, seed & (2**64 - 1), init_mode, iters, x, y, ctypes.byref(out)) != 0:
+        raise ValueError("oracle2d_point failed")
+    return out.value
+
+
+def solve_2d(nx: int, ny: int, seed: int, init_mode: int, iters: int, threads: int = 1) -> np.ndarray:
+    """Interior (x fastest) of the 2D field after `iters` Jacobi steps."""
+    Q = sweep_2d(init_padded_2d(nx, ny, seed, init_mode), iters, threads)
+    return np.ascontiguousarray(Q[1:-1, 1:-1]).ravel()

@@ -45,6 +45,9 @@
  *                          into the neighbours' ghost layers every step
  *   oracle_point           value of one interior cell after `iters` steps,
  *                          computed on its dependency cone only
+ *   oracle2d_*             the same for the 2D 5-point Jacobi (the paper's
+ *                          own application): init, sweep, decomposed sweep,
+ *                          point
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -344,4 +347,178 @@ int oracle_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ 2D
+ *
+ * The paper's own application (Sec. V "jacobi2d"): Jacobi on a 2D grid with a
+ * 5-point stencil, the mean of the four edge neighbours, summed x-, x+, y-,
+ * y+ left to right, then divided by 4 (exact power-of-two scaling; the IEEE
+ * quotient).  Padded array Q[(ny+2)][(nx+2)], shell fixed; initial field: the
+ * value of padded cell L = gx + (nx+2)*gy is the same SplitMix64 function
+ * of (seed, L) as in 3D. */
+
+#define PIDX2(nx, gx, gy) ((int64_t)(gx) + ((int64_t)(nx) + 2) * (int64_t)(gy))
+
+void oracle2d_init_padded(int64_t nx, int64_t ny, uint64_t seed, int init_mode, double *P)
+{
+    for (int64_t gy = 0; gy < ny + 2; ++gy)
+        for (int64_t gx = 0; gx < nx + 2; ++gx) {
+            int64_t L = PIDX2(nx, gx, gy);
+            int shell = gx == 0 || gy == 0 || gx == nx + 1 || gy == ny + 1;
+            P[L] = (shell || init_mode == 1) ? oracle_uniform(seed, (uint64_t)L) : 0.0;
+        }
+}
+
+static double stencil2d(const double *u, int64_t c, int64_t sx)
+{
+    double s = u[c - 1] + u[c + 1];
+    s = s + u[c - sx];
+    s = s + u[c + sx];
+    return s / 4.0;
+}
+
+int oracle2d_sweep(int64_t nx, int64_t ny, double *P, int iters, int threads)
+{
+    int64_t n = (nx + 2) * (ny + 2), sx = nx + 2;
+    double *Q = (double *)malloc((size_t)n * sizeof(double));
+    if (!Q) return -1;
+    memcpy(Q, P, (size_t)n * sizeof(double));
+    double *cur = P, *nxt = Q;
+    if (threads < 1) threads = 1;
+    for (int t = 0; t < iters; ++t) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(threads) schedule(static)
+#endif
+        for (int64_t gy = 1; gy <= ny; ++gy)
+            for (int64_t gx = 1; gx <= nx; ++gx) {
+                int64_t c = PIDX2(nx, gx, gy);
+                nxt[c] = stencil2d(cur, c, sx);
+            }
+        double *tmp = cur; cur = nxt; nxt = tmp;
+    }
+    if (cur != P) memcpy(P, cur, (size_t)n * sizeof(double));
+    free(Q);
+    return 0;
+}
+
+/* Block-decomposed 2D sweep: blocks cut at ex[0..px] x ey[0..py]; each block
+ * keeps a padded (bx+2)(by+2) copy per parity and, after computing, copies its
+ * new boundary rows/columns into the facing ghost cells of its neighbours. */
+int oracle2d_sweep_decomposed(int64_t nx, int64_t ny, int px, int py, const int64_t *ex, const int64_t *ey,
+                              double *P, int iters)
+{
+    int nb = px * py;
+    typedef struct { int64_t x0, y0, bx, by; double *buf[2]; } blk;
+    blk *B = (blk *)calloc((size_t)nb, sizeof(blk));
+    if (!B) return -1;
+    int rc = 0;
+#define BI2(b, lx, ly) ((int64_t)(lx) + ((b)->bx + 2) * (int64_t)(ly))
+    for (int cy = 0; cy < py; ++cy)
+        for (int cx = 0; cx < px; ++cx) {
+            blk *b = &B[cx + px * cy];
+            b->x0 = ex[cx]; b->bx = ex[cx + 1] - ex[cx];
+            b->y0 = ey[cy]; b->by = ey[cy + 1] - ey[cy];
+            if (b->bx < 1 || b->by < 1) { rc = -2; goto out2; }
+            for (int p = 0; p < 2; ++p) {
+                b->buf[p] = (double *)calloc((size_t)((b->bx + 2) * (b->by + 2)), sizeof(double));
+                if (!b->buf[p]) { rc = -1; goto out2; }
+                for (int64_t ly = 0; ly < b->by + 2; ++ly)
+                    for (int64_t lx = 0; lx < b->bx + 2; ++lx) {
+                        int edge = (lx == 0 || lx == b->bx + 1) + (ly == 0 || ly == b->by + 1);
+                        if (edge > 1) continue;
+                        b->buf[p][BI2(b, lx, ly)] = P[PIDX2(nx, b->x0 + lx, b->y0 + ly)];
+                    }
+            }
+        }
+    for (int t = 0; t < iters; ++t) {
+        int src = t & 1, dst = src ^ 1;
+        for (int c = 0; c < nb; ++c) {
+            blk *b = &B[c];
+            for (int64_t ly = 1; ly <= b->by; ++ly)
+                for (int64_t lx = 1; lx <= b->bx; ++lx) {
+                    int64_t i = BI2(b, lx, ly);
+                    b->buf[dst][i] = stencil2d(b->buf[src], i, b->bx + 2);
+                }
+        }
+        for (int cy = 0; cy < py; ++cy)
+            for (int cx = 0; cx < px; ++cx) {
+                blk *b = &B[cx + px * cy];
+                if (cx > 0) {
+                    blk *n = &B[(cx - 1) + px * cy];
+                    for (int64_t ly = 1; ly <= b->by; ++ly)
+                        n->buf[dst][BI2(n, n->bx + 1, ly)] = b->buf[dst][BI2(b, 1, ly)];
+                }
+                if (cx < px - 1) {
+                    blk *n = &B[(cx + 1) + px * cy];
+                    for (int64_t ly = 1; ly <= b->by; ++ly)
+                        n->buf[dst][BI2(n, 0, ly)] = b->buf[dst][BI2(b, b->bx, ly)];
+                }
+                if (cy > 0) {
+                    blk *n = &B[cx + px * (cy - 1)];
+                    for (int64_t lx = 1; lx <= b->bx; ++lx)
+                        n->buf[dst][BI2(n, lx, n->by + 1)] = b->buf[dst][BI2(b, lx, 1)];
+                }
+                if (cy < py - 1) {
+                    blk *n = &B[cx + px * (cy + 1)];
+                    for (int64_t lx = 1; lx <= b->bx; ++lx)
+                        n->buf[dst][BI2(n, lx, 0)] = b->buf[dst][BI2(b, lx, b->by)];
+                }
+            }
+    }
+    for (int c = 0; c < nb; ++c) {
+        blk *b = &B[c];
+        for (int64_t ly = 1; ly <= b->by; ++ly)
+            for (int64_t lx = 1; lx <= b->bx; ++lx)
+                P[PIDX2(nx, b->x0 + lx, b->y0 + ly)] = b->buf[iters & 1][BI2(b, lx, ly)];
+    }
+out2:
+    for (int c = 0; c < nb; ++c) {
+        free(B[c].buf[0]);
+        free(B[c].buf[1]);
+    }
+    free(B);
+#undef BI2
+    return rc;
+}
+
+/* Value of interior cell (x, y) after `iters` steps, on its dependency cone
+ * (a square of half-width iters-1-t around the target, clipped). */
+int oracle2d_point(int64_t nx, int64_t ny, uint64_t seed, int init_mode, int iters, int64_t x, int64_t y,
+                   double *out)
+{
+    if (x < 0 || y < 0 || x >= nx || y >= ny || iters < 0) return -1;
+    int64_t R = iters, c[2] = {x + 1, y + 1}, N[2] = {nx, ny}, lo[2], hi[2], n[2];
+    for (int a = 0; a < 2; ++a) {
+        lo[a] = c[a] - R < 0 ? 0 : c[a] - R;
+        hi[a] = c[a] + R > N[a] + 1 ? N[a] + 1 : c[a] + R;
+        n[a] = hi[a] - lo[a] + 1;
+    }
+    double *U = (double *)malloc((size_t)(n[0] * n[1]) * sizeof(double));
+    double *V = (double *)malloc((size_t)(n[0] * n[1]) * sizeof(double));
+    if (!U || !V) { free(U); free(V); return -1; }
+    for (int64_t j = 0; j < n[1]; ++j)
+        for (int64_t i = 0; i < n[0]; ++i) {
+            int64_t gx = lo[0] + i, gy = lo[1] + j, L = PIDX2(nx, gx, gy);
+            int shell = gx == 0 || gy == 0 || gx == nx + 1 || gy == ny + 1;
+            U[i + n[0] * j] = (shell || init_mode == 1) ? oracle_uniform(seed, (uint64_t)L) : 0.0;
+        }
+    memcpy(V, U, (size_t)(n[0] * n[1]) * sizeof(double));
+    for (int t = 0; t < iters; ++t) {
+        int64_t r = R - 1 - t, a0[2], a1[2];
+        for (int a = 0; a < 2; ++a) {
+            a0[a] = c[a] - r < 1 ? 1 : c[a] - r;
+            a1[a] = c[a] + r > N[a] ? N[a] : c[a] + r;
+        }
+        for (int64_t gy = a0[1]; gy <= a1[1]; ++gy)
+            for (int64_t gx = a0[0]; gx <= a1[0]; ++gx) {
+                int64_t i = (gx - lo[0]) + n[0] * (gy - lo[1]);
+                V[i] = stencil2d(U, i, n[0]);
+            }
+        double *tmp = U; U = V; V = tmp;
+    }
+    *out = U[(c[0] - lo[0]) + n[0] * (c[1] - lo[1])];
+    free(U);
+    free(V);
+    return 0;
 }
