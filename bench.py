@@ -36,9 +36,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="odf", choices=["odf", "uneven", "ceiling", "serve"],
+    ap.add_argument("--workload", default="odf", choices=["odf", "uneven", "ceiling", "serve", "jacobi2d"],
                     help="odf: 512^3 at --odf (default); uneven: 768x512x512 in ~300 uneven chares; "
-                         "ceiling: 1024^3 in 4096 chares; serve: Poisson stream of jobs into the server")
+                         "ceiling: 1024^3 in 4096 chares; serve: Poisson stream of jobs into the server; "
+                         "jacobi2d: the 2D 5-point Jacobi on 32768^2 in --odf chares (a power of two)")
     ap.add_argument("--jobs", type=int, default=300, help="serve: number of jobs")
     ap.add_argument("--rate", type=float, default=60.0, help="serve: Poisson arrival rate (jobs/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
@@ -138,6 +139,7 @@ SM_MAX_GHZ = 2.07
 FP64_LANES_PER_SM = 2
 FP64_NOMINAL_GFLOPS = 1250.0
 FLOPS_PER_UPDATE = 6  # 5 additions + 1 division
+FLOPS_PER_UPDATE_2D = 4  # 3 additions + 1 division
 
 
 def profiled_traffic(args, plan):
@@ -210,6 +212,29 @@ def oracle_cpu_baseline(edge: int, target_s: float = 10.0):
                       f"undecomposed C oracle sweep on {threads} OpenMP threads ({dt:.1f} s)"}
 
 
+def oracle_cpu_baseline_2d(edge: int, target_s: float = 10.0):
+    """The same for the 2D workload: the C oracle's 2D sweep of the full
+    edge^2 field, as many iterations as fit in about target_s seconds."""
+    import oracle
+    from paper_2605_12734_gb300 import inputs
+    oracle.build()
+    threads = oracle.max_threads()
+    P = oracle.init_padded_2d(edge, edge, 9, inputs.INIT_UNIFORM)
+    t0 = time.perf_counter()
+    oracle.sweep_2d(P, 1, threads)
+    t1 = time.perf_counter()
+    oracle.sweep_2d(P, 3, threads)
+    t3 = time.perf_counter()
+    per_iter = max((t3 - t1) - (t1 - t0), 1e-3) / 2
+    iters = max(1, min(1000, int(target_s / per_iter)))
+    t0 = time.perf_counter()
+    oracle.sweep_2d(P, iters, threads)
+    dt = time.perf_counter() - t0
+    return {"value": edge ** 2 * iters / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{edge}^2 field (U[0,1), seed 9), {iters} iterations of the undecomposed C oracle "
+                      f"2D sweep on {threads} OpenMP threads ({dt:.1f} s)"}
+
+
 # ----------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -246,12 +271,16 @@ def run_reference(args):
 
 # ----------------------------------------------------------------- our arm
 
-def time_path(pkg, edge, odf, path, steps, warmup, stream, tune_kw):
-    """Device-resident timing of `steps` iterations; returns (ms/step, stats)."""
+def time_path(pkg, edge, odf, path, steps, warmup, stream, tune_kw, make=None):
+    """Device-resident timing of `steps` iterations; returns (ms/step, stats).
+    make(path, **kw) builds the solver (default: edge^3 in odf cubic chares)."""
     import torch
-    p = round(odf ** (1 / 3))
-    s = pkg.Jacobi3D(edge, edge, edge, split=(p, p, p), seed=2, init_mode=1, path=path,
-                     stream=stream.cuda_stream, **tune_kw)
+    if make is None:
+        p = round(odf ** (1 / 3))
+        s = pkg.Jacobi3D(edge, edge, edge, split=(p, p, p), seed=2, init_mode=1, path=path,
+                         stream=stream.cuda_stream, **tune_kw)
+    else:
+        s = make(path, stream=stream.cuda_stream, **tune_kw)
     try:
         s.step(warmup)
         s.sync()
@@ -285,7 +314,7 @@ def run_ours(args):
         return run_serve(args, pkg, torch, rank, world, dev)
     edge, odf = args.edge, args.odf
     p = round(odf ** (1 / 3))
-    if p ** 3 != odf:
+    if p ** 3 != odf and args.workload != "jacobi2d":
         raise SystemExit("--odf must be a cube")
     stream = torch.cuda.Stream(device=dev)
     tune_kw = dict(threads=args.threads, cells_per_thread=args.cpt, stages=args.stages,
@@ -299,12 +328,20 @@ def run_ours(args):
     elif args.workload == "ceiling":
         w = inputs.ceiling_1024()
         dims, dec, name = (w.nx, w.ny, w.nz), dict(split=w.split), w.name
+    elif args.workload == "jacobi2d":
+        w = inputs.jacobi2d_32768(odf)
+        dims, dec, name = (w.nx, w.ny, 1), dict(split=w.split[:2]), w.name
     else:
         dims, dec, name = (edge, edge, edge), dict(split=(p, p, p)), f"jacobi3d-{edge}^3-odf{odf}"
     seed = 2 if args.workload == "odf" else w.seed
+    two_d = args.workload == "jacobi2d"
 
-    solver = pkg.Jacobi3D(*dims, seed=seed, init_mode=1, path=args.path, stream=stream.cuda_stream,
-                          **dec, **tune_kw)
+    def make(path, **kw):
+        if two_d:
+            return pkg.Jacobi2D(dims[0], dims[1], seed=seed, init_mode=1, path=path, **dec, **kw)
+        return pkg.Jacobi3D(*dims, seed=seed, init_mode=1, path=path, **dec, **kw)
+
+    solver = make(args.path, stream=stream.cuda_stream, **tune_kw)
     plan = solver.stats()["plan"]
     solver.step(args.warmup)
     solver.sync()
@@ -337,7 +374,11 @@ def run_ours(args):
     # GPU's FP64 rate is 1.25 TFLOP/s nominal.  The kernel runs fp64_adds(m) of
     # the adds on the FP64 pipe and the rest, with the division, exactly on
     # the integer pipes.
-    fp64_adds = {0: 5, 1: 5, 2: 4, 3: 3, 4: 2, 5: 1, 6: 0, 7: 3.5, 8: 3.75}[plan["arith"]]
+    if two_d:  # 3 adds; modes 4..6 all run the three adds in the window
+        fp64_adds = {0: 3, 1: 3, 2: 2, 3: 1, 4: 0, 5: 0, 6: 0, 7: 1.5, 8: 1.75}[plan["arith"]]
+    else:
+        fp64_adds = {0: 5, 1: 5, 2: 4, 3: 3, 4: 2, 5: 1, 6: 0, 7: 3.5, 8: 3.75}[plan["arith"]]
+    fpu = FLOPS_PER_UPDATE_2D if two_d else FLOPS_PER_UPDATE
     fp64_pipe = FP64_LANES_PER_SM * SMS * SM_MAX_GHZ  # G FP64 instructions/s
     hbm_peak, peak_kind = measured_peaks()
     bytes_step = plan["bytes_per_step"]
@@ -346,16 +387,25 @@ def run_ours(args):
            "frac": bytes_step / (ms_step * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
            "bytes_per_step": bytes_step,
            "note": "algorithmic bytes: 16 B/cell + 16 B per internal ghost cell + 8 B per Dirichlet ghost cell"}
-    roofline = {"bound": "alu", "achieved": FLOPS_PER_UPDATE * ups / 1e9, "peak": FP64_NOMINAL_GFLOPS,
-                "unit": "GFLOP/s", "frac": FLOPS_PER_UPDATE * ups / 1e9 / FP64_NOMINAL_GFLOPS, "traffic": None,
-                "note": ("algorithmic FP64 work: 5 adds + 1 division per update; peak: GB300 FP64 1.25 TFLOP/s "
-                         "nominal (recipe), = 2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz x 2 flops per FMA; "
-                         f"this kernel runs {fp64_adds} adds per update on the FP64 pipe and the rest with the "
-                         "division, bit-exactly, on the integer pipes"),
+    nadd = 3 if two_d else 5
+    roofline = {"bound": "alu", "achieved": fpu * ups / 1e9, "peak": FP64_NOMINAL_GFLOPS,
+                "unit": "GFLOP/s", "frac": fpu * ups / 1e9 / FP64_NOMINAL_GFLOPS, "traffic": None,
+                "note": (f"algorithmic FP64 work: {nadd} adds + 1 division per update; peak: GB300 FP64 "
+                         "1.25 TFLOP/s nominal (recipe), = 2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz x 2 flops "
+                         f"per FMA; this kernel runs {fp64_adds} adds per update on the FP64 pipe and the rest "
+                         "with the division, bit-exactly, on the integer pipes"),
                 "fp64_pipe": {"adds_per_update": fp64_adds, "peak_ginst_per_s": fp64_pipe,
                               "busy_frac_est": fp64_adds * ups / 1e9 / fp64_pipe},
                 "hbm": hbm}
-    traffic = profiled_traffic(args, plan)
+    if two_d and hbm["frac"] > roofline["frac"]:
+        # the 2D update is light enough that HBM is the nearer roof
+        roofline = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm["frac"], "traffic": None, "peak_kind": peak_kind,
+                    "note": hbm["note"] + "; the FP64 roof is reported under 'alu'",
+                    "alu": {"achieved": fpu * ups / 1e9, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
+                            "frac": fpu * ups / 1e9 / FP64_NOMINAL_GFLOPS,
+                            "fp64_adds_per_update": fp64_adds}}
+    traffic = profiled_traffic(args, plan) if not two_d else None
     if traffic is not None:
         roofline["traffic"] = traffic
         roofline["traffic_note"] = "DRAM bytes per iteration (ncu, one persistent launch of this kernel build)"
@@ -389,16 +439,32 @@ def run_ours(args):
     solver.close()
 
     baseline = None
-    if args.baseline_steps > 0 and rank == 0 and args.workload == "odf":
+    if args.baseline_steps > 0 and rank == 0 and args.workload in ("odf", "jacobi2d"):
         ms_b, b0, b1 = time_path(pkg, edge, odf, "per_chare", args.baseline_steps, 1, stream,
-                                 dict(device=dev))
+                                 dict(device=dev), make=make if two_d else None)
         baseline = {"path": "per_chare", "ms_per_step": ms_b, "value": updates_step / (ms_b * 1e-3),
                     "steps": args.baseline_steps,
                     "api_calls_per_step": (b1["api_calls"] - b0["api_calls"]) / args.baseline_steps,
                     "kernels_per_step": (b1["kernel_launches"] - b0["kernel_launches"]) / args.baseline_steps}
 
     sweep = None
-    if args.sweep and rank == 0:
+    if args.sweep and rank == 0 and two_d:
+        sweep = []
+        for o in (1, 4, 16, 64, 256, 1024, 4096):
+            w2 = inputs.jacobi2d_32768(o)
+            for path in ("fused", "persistent", "graph", "per_chare"):
+                k = args.steps if path in ("fused", "persistent") else max(2, min(10, args.steps))
+                if path in ("graph", "per_chare") and o >= 1024:
+                    k = 2
+
+                def make_o(pth, **kw):
+                    return pkg.Jacobi2D(w2.nx, w2.ny, seed=seed, init_mode=1, path=pth, split=w2.split[:2], **kw)
+                ms_p, _, _ = time_path(pkg, edge, o, path, k, 2, stream, dict(device=dev), make=make_o)
+                info = pkg.plan_2d(w2.nx, w2.ny, split=w2.split[:2])
+                sweep.append({"odf": o, "path": path, "ms_per_step": ms_p, "steps": k,
+                              "updates_per_s": info["cells"] / (ms_p * 1e-3),
+                              "alg_GBps": info["bytes_per_step"] / (ms_p * 1e-3) / 1e9})
+    elif args.sweep and rank == 0:
         sweep = []
         for o in (1, 8, 64, 512, 4096):
             for path in ("fused", "persistent", "graph", "per_chare"):
@@ -414,7 +480,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_cpu_baseline(edge if args.workload == "odf" else 512)
+        cpu = oracle_cpu_baseline_2d(dims[0]) if two_d else oracle_cpu_baseline(edge if args.workload == "odf" else 512)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -422,6 +488,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": name, "nx": dims[0], "ny": dims[1], "nz": dims[2],
                            "odf": plan["nchares"], "chare_edge": (edge // p) if args.workload == "odf" else None,
+                           "stencil": "2d5" if two_d else "3d7",
                            "path": args.path, "seed": seed, "tuned": bool(st1.get("tuned")),
                            "init": "U[0,1) everywhere, Dirichlet shell fixed",
                            "l2": f"no flush: the two parity buffers ({plan['arena_bytes'] / 2**30:.1f} GiB "

@@ -86,6 +86,17 @@ typedef enum {
 #define OD_INIT_ZERO_INTERIOR 0
 #define OD_INIT_UNIFORM 1
 
+/* Stencils: the 3D 7-point Jacobi, and the paper's own 2D 5-point Jacobi
+ * (Sec. V "jacobi2d"): u'[i,j] = ((((u[i-1]+u[i+1]) + u[j-1]) + u[j+1]) / 4 on
+ * an nx*ny grid (nz = 1, one block along z), with the same seeded field,
+ * Dirichlet shell and paths; the padded 2D cell L = gx + (nx+2)*gy gets
+ * SplitMix64 output L+1.  A 2D configuration splits x by px / cuts_x and y by
+ * py / cuts_y; od_read / od_write move nx*ny doubles, x fastest.  The tile
+ * shape fields apply with tile_y capping a tile's row segment (cells along
+ * x) and tile_z its rows. */
+#define OD_STENCIL_3D7 0
+#define OD_STENCIL_2D5 1
+
 /* Problem, decomposition and execution settings.  Fill with
  * od_config_default() first, then set fields. */
 typedef struct od_config {
@@ -140,6 +151,8 @@ typedef struct od_config {
                                     library allocates with cudaMalloc */
     uint64_t arena_bytes;        /* size of `arena` in bytes */
     uint64_t spin_limit_ns;      /* device-side wait limit (0 = 2 000 000 000) */
+    int32_t stencil;             /* OD_STENCIL_3D7 (default) or OD_STENCIL_2D5 */
+    int32_t reserved;
 } od_config;
 
 /* Host-only summary of a configuration's decomposition and memory. */
@@ -185,7 +198,9 @@ OD_API od_status od_plan(const od_config *cfg, od_plan_info *out);
 /* Chare boxes of a configuration, host-only: for chare c (x fastest:
  * c = cx + px*(cy + py*cz)) writes box[6c..6c+5] = x0,bx,y0,by,z0,bz and
  * nbr[6c..6c+5] = neighbour chare on the x-,x+,y-,y+,z-,z+ side or -1 on the
- * domain boundary.  `capacity` = chares the arrays hold. */
+ * domain boundary.  For OD_STENCIL_2D5 the boxes are x0,bx,y0,by,0,1 and the
+ * neighbours x-,x+,y-,y+,-1,-1 of the 2D grid.  `capacity` = chares the
+ * arrays hold. */
 OD_API od_status od_decompose(const od_config *cfg, int64_t *box, int32_t *nbr, int64_t capacity);
 
 /* Allocate device state on cfg->device, build the chare/tile tables, tune if
@@ -233,7 +248,9 @@ OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
  * op 1: out[i] = a[i] + b[i] (b unused for op 0); op 2 / 3: the same on the
  * FP64 pipe (device only); op 10+m (m = 0..6): the whole Jacobi update
  * (((((a0+a1)+a2)+a3)+a4)+a5)/6 of the six operands a[6i..6i+5] in
- * arithmetic mode m (see od_config.arith), b unused.  od_arith_host runs the routines on the host CPU
+ * arithmetic mode m (see od_config.arith), b unused; op 20+m (m = 0..4): the
+ * 2D update (((a0+a1)+a2)+a3)/4 of a[4i..4i+3] in mode m (m = 4: three window
+ * adds).  od_arith_host runs the routines on the host CPU
  * over host arrays; od_arith_device runs them in a kernel over device arrays
  * of the current device and synchronises.  n >= 0 elements. */
 OD_API od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n);
@@ -291,7 +308,8 @@ OD_API void od_server_config_default(od_server_config *cfg);
 OD_API od_status od_server_create(od_server **out, const od_server_config *cfg);
 /* Queue a job: the decomposition and seed of *job (cut lists are copied;
  * path, tile shape, stream and arena fields are ignored) and its iteration
- * count.  OD_EBUDGET if the job alone exceeds the whole budget. */
+ * count.  OD_EBUDGET if the job alone exceeds the whole budget; OD_EINVAL for
+ * a stencil other than OD_STENCIL_3D7 (a batched launch shares one kernel). */
 OD_API od_status od_server_submit(od_server *s, const od_config *job, int32_t iters, uint64_t *job_id);
 /* Wait up to timeout_s seconds for the job to be done or failed; *state is
  * its state on return (OD_OK also on timeout). */

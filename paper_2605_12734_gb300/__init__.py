@@ -21,8 +21,10 @@ import numpy as np
 from . import _native
 from ._native import ODError, PATHS, check, lib, od_config, od_plan_info, od_stats
 
-__all__ = ["Jacobi3D", "Server", "ODError", "PATHS", "make_config", "plan", "decompose", "lib", "arith_host",
-           "arith_device", "jacobi_noalloc"]
+STENCILS = {"3d7": 0, "2d5": 1}
+
+__all__ = ["Jacobi3D", "Jacobi2D", "Server", "STENCILS", "ODError", "PATHS", "make_config", "plan", "decompose", "lib", "arith_host",
+           "arith_device", "jacobi_noalloc", "plan_2d", "decompose_2d"]
 
 
 def _cuts_array(cuts):
@@ -37,13 +39,18 @@ def make_config(nx: int, ny: int, nz: int, *, split=(1, 1, 1), cuts=None, seed: 
                 tile_y: int = 0, tile_z: int = 0, threads: int = 0, cells_per_thread: int = 0,
                 stages: int = 0, arith: int = -1, order: int = 0, stream_pool: int = 0, device: int = 0,
                 stream: int | None = None, arena: int | None = None, arena_bytes: int = 0,
-                spin_limit_ns: int = 0):
+                spin_limit_ns: int = 0, stencil: str | int = "3d7"):
     """Build an od_config (returns (config, keepalive) -- keep both alive while
-    the config is used, the cut arrays are referenced by pointer)."""
+    the config is used, the cut arrays are referenced by pointer).  For the
+    2D stencil ("2d5") nz is 1 and split / cuts may give two axes."""
     cfg = od_config()
     lib().od_config_default(ctypes.byref(cfg))
     cfg.nx, cfg.ny, cfg.nz = int(nx), int(ny), int(nz)
+    split = tuple(split) + (1,) * (3 - len(split))
+    if cuts is not None:
+        cuts = tuple(cuts) + (None,) * (3 - len(cuts))
     cfg.px, cfg.py, cfg.pz = (int(v) for v in split)
+    cfg.stencil = STENCILS[stencil] if isinstance(stencil, str) else int(stencil)
     keep = []
     if cuts is not None:
         for axis, cl in zip("xyz", cuts):
@@ -88,11 +95,11 @@ def decompose(nx, ny, nz, **kw):
 
 def arith_host(op: int, a: np.ndarray, b: np.ndarray | None = None) -> np.ndarray:
     """Run the kernels' exact integer-pipe arithmetic on the host: op 0
-    a/6, op 1 a+b, op 10+m the Jacobi update in arithmetic mode m over six
-    operands per element (float64 arrays)."""
+    a/6, op 1 a+b, op 10+m the 3D Jacobi update in arithmetic mode m over six
+    operands per element, op 20+m the 2D update over four (float64 arrays)."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = a if b is None else np.ascontiguousarray(b, dtype=np.float64)
-    n = a.size // 6 if op >= 10 else a.size
+    n = a.size // 4 if op >= 20 else a.size // 6 if op >= 10 else a.size
     out = np.empty(n, dtype=np.float64)
     check(lib().od_arith_host(int(op), a.ctypes.data, b.ctypes.data, out.ctypes.data, n), "od_arith_host")
     return out
@@ -103,7 +110,7 @@ def arith_device(op: int, a, b=None):
     pipe's IEEE division / add."""
     import torch
     b = a if b is None else b
-    n = a.numel() // 6 if op >= 10 else a.numel()
+    n = a.numel() // 4 if op >= 20 else a.numel() // 6 if op >= 10 else a.numel()
     out = torch.empty(n, dtype=torch.float64, device=a.device)
     check(lib().od_arith_device(int(op), a.data_ptr(), b.data_ptr(), out.data_ptr(), n), "od_arith_device")
     return out
@@ -207,6 +214,25 @@ class Jacobi3D:
             self.close()
         except Exception:
             pass
+
+
+class Jacobi2D(Jacobi3D):
+    """The 2D 5-point Jacobi (the paper's own application) on an nx x ny grid
+    split into px x py chares; read/write move nx*ny doubles, x fastest."""
+
+    def __init__(self, nx: int, ny: int, *, torch_arena: bool = True, **kw):
+        kw["stencil"] = "2d5"
+        super().__init__(nx, ny, 1, torch_arena=torch_arena, **kw)
+
+
+def plan_2d(nx, ny, **kw) -> dict:
+    return plan(nx, ny, 1, stencil="2d5", **kw)
+
+
+def decompose_2d(nx, ny, **kw):
+    """2D chare boxes (n,4: x0,bx,y0,by) and neighbours (n,4: x-,x+,y-,y+)."""
+    box, nbr = decompose(nx, ny, 1, stencil="2d5", **kw)
+    return box[:, :4].copy(), nbr[:, :4].copy()
 
 
 class Server:

@@ -13,6 +13,7 @@ OD_OK, OD_EINVAL, OD_ENOMEM, OD_ECUDA, OD_ETIMEOUT, OD_EBUDGET, OD_ESTATE, OD_EN
 STATUS_NAMES = {0: "OD_OK", 1: "OD_EINVAL", 2: "OD_ENOMEM", 3: "OD_ECUDA", 4: "OD_ETIMEOUT",
                 5: "OD_EBUDGET", 6: "OD_ESTATE", 7: "OD_ENOTFOUND"}
 OD_PATH_PER_CHARE, OD_PATH_FUSED, OD_PATH_GRAPH, OD_PATH_PERSISTENT = range(4)
+OD_STENCIL_3D7, OD_STENCIL_2D5 = 0, 1
 PATHS = {"per_chare": OD_PATH_PER_CHARE, "fused": OD_PATH_FUSED, "graph": OD_PATH_GRAPH,
          "persistent": OD_PATH_PERSISTENT}
 
@@ -33,6 +34,7 @@ class od_config(ctypes.Structure):
         ("tile_y", _i32), ("tile_z", _i32), ("threads", _i32), ("cells_per_thread", _i32),
         ("stages", _i32), ("arith", _i32), ("order", _i32), ("stream_pool", _i32), ("device", _i32),
         ("stream", _vp), ("arena", _vp), ("arena_bytes", _u64), ("spin_limit_ns", _u64),
+        ("stencil", _i32), ("reserved", _i32),
     ]
 
 

@@ -29,6 +29,8 @@ SOURCES = ["od_kernels.cu", "od_api.cu", "od_plan.cpp", "od_noalloc.cu", "od_ser
 # the tile kernels, compiled once per arithmetic mode (-DOD_AMODE=m)
 TILE_SOURCE = "od_tiles.cu"
 AMODES = range(9)
+# the 2D 5-point kernels (-DOD_STENCIL=1): modes 4..6 coincide there (three adds)
+AMODES_2D = (0, 1, 2, 3, 4, 7, 8)
 HEADERS = ["od_internal.h", "od_kernels.h", "od_plan.h", "od_tile.cuh", "od_arith.cuh", "od_ctx.h"]
 
 
@@ -61,6 +63,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     units = [(os.path.join(CSRC, s), [], os.path.basename(s)) for s in SOURCES]
     units += [(os.path.join(CSRC, TILE_SOURCE), [f"-DOD_AMODE={m}"], f"od_tiles_am{m}")
               for m in AMODES]
+    units += [(os.path.join(CSRC, TILE_SOURCE), [f"-DOD_AMODE={m}", "-DOD_STENCIL=1"], f"od_tiles2d_am{m}")
+              for m in AMODES_2D]
     for src, defs, stem in units:
         obj = os.path.join(BUILD, stem + ".o")
         objs.append(obj)

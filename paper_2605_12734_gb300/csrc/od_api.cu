@@ -79,6 +79,7 @@ KArgs base_args_impl(const od_ctx *c) {
     a.stage_doubles = c->plan.stage_doubles;
     a.stall_tile = c->stall_tile;
     a.spin_ns = c->spin_ns;
+    a.stencil = c->plan.stencil;
     return a;
 }
 
@@ -102,7 +103,7 @@ od_status enqueue_persistent(od_ctx *c, int32_t iters) {
     const od::Plan &p = c->plan;
     const int64_t nt = (int64_t)p.tiles.size();
     int bps = 0;
-    OD_CUDA(od::persistent_occupancy(p.threads, p.cpt, p.amode, p.smem_bytes, &bps));
+    OD_CUDA(od::persistent_occupancy(p.threads, p.cpt, p.amode, p.smem_bytes, p.stencil, &bps));
     if (bps < 1) return fail(OD_EINVAL, "persistent kernel does not fit on an SM with this tiling");
     int grid = (int)std::min<int64_t>(nt, (int64_t)bps * c->num_sms);
     c->persistent_grid = grid;
@@ -365,8 +366,8 @@ std::string tune_key(const od_config *cfg, const od::Plan &p, int device) {
     mix(-1);
     for (auto v : p.ez) mix(v);
     char buf[256];
-    snprintf(buf, sizeof buf, "%s/%d/path%d/%lldx%lldx%lld/%016llx", name.c_str(), sms, cfg->path,
-             (long long)p.nx, (long long)p.ny, (long long)p.nz, (unsigned long long)h);
+    snprintf(buf, sizeof buf, "%s/%d/path%d/st%d/%lldx%lldx%lld/%016llx", name.c_str(), sms, cfg->path,
+             p.stencil, (long long)p.nx, (long long)p.ny, (long long)p.nz, (unsigned long long)h);
     return buf;
 }
 
@@ -560,16 +561,20 @@ void od_config_default(od_config *cfg) {
 
 od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n) {
     if (n < 0 || (n > 0 && (!a || !out || (op == 1 && !b)))) return fail(OD_EINVAL, "bad arguments");
-    if (op != 0 && op != 1 && !(op >= 10 && op <= 16))
-        return fail(OD_EINVAL, "host op must be 0 (div6), 1 (add) or 10..16 (update)");
+    if (op != 0 && op != 1 && !(op >= 10 && op <= 16) && !(op >= 20 && op <= 24))
+        return fail(OD_EINVAL, "host op must be 0 (div6), 1 (add), 10..16 (3D update) or 20..24 (2D update)");
     for (int64_t i = 0; i < n; ++i)
-        out[i] = op == 0 ? od::div6(a[i]) : op == 1 ? od::add(a[i], b[i]) : od::jacobi_update_mode(op - 10, a + 6 * i);
+        out[i] = op == 0   ? od::div6(a[i])
+                 : op == 1 ? od::add(a[i], b[i])
+                 : op < 20 ? od::jacobi_update_mode(op - 10, a + 6 * i)
+                           : od::jacobi2d_update_mode(op - 20, a + 4 * i);
     return OD_OK;
 }
 
 od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n) {
     if (n < 0 || (n > 0 && (!a || !out || ((op == 1 || op == 3) && !b)))) return fail(OD_EINVAL, "bad arguments");
-    if (!((op >= 0 && op <= 3) || (op >= 10 && op <= 16))) return fail(OD_EINVAL, "op must be 0..3 or 10..16");
+    if (!((op >= 0 && op <= 3) || (op >= 10 && op <= 16) || (op >= 20 && op <= 24)))
+        return fail(OD_EINVAL, "op must be 0..3, 10..16 or 20..24");
     if (n == 0) return OD_OK;
     OD_CUDA(od::launch_arith(op, a, b, out, n, 0));
     OD_CUDA(cudaStreamSynchronize(0));
@@ -596,6 +601,12 @@ od_status od_decompose(const od_config *cfg, int64_t *box, int32_t *nbr, int64_t
     for (size_t c = 0; c < p.ch.size(); ++c) {
         const od::HostChare &h = p.ch[c];
         int64_t *b = box + 6 * c;
+        if (p.stencil == OD_STENCIL_2D5) {  // report the 2D grid, not its internal (nx, 1, ny) layout
+            b[0] = h.x0; b[1] = h.bx; b[2] = h.z0; b[3] = h.bz; b[4] = 0; b[5] = 1;
+            const int32_t f2[6] = {h.nbr[OD_FACE_XLO], h.nbr[OD_FACE_XHI], h.nbr[OD_FACE_ZLO], h.nbr[OD_FACE_ZHI], -1, -1};
+            for (int f = 0; f < 6; ++f) nbr[6 * c + f] = f2[f];
+            continue;
+        }
         b[0] = h.x0; b[1] = h.bx; b[2] = h.y0; b[3] = h.by; b[4] = h.z0; b[5] = h.bz;
         for (int f = 0; f < 6; ++f) nbr[6 * c + f] = h.nbr[f];
     }
@@ -653,7 +664,7 @@ od_status od_create(od_ctx **out, const od_config *cfg_in) {
         }                                                 \
     } while (0)
     OD_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-    if (!od::tile_shape_supported(p.threads, p.cpt, p.amode)) {
+    if (!od::tile_shape_supported(p.threads, p.cpt, p.amode, p.stencil)) {
         release(c);
         return fail(OD_EINVAL, "unsupported threads / cells_per_thread");
     }
@@ -694,6 +705,7 @@ od_status od_create(od_ctx **out, const od_config *cfg_in) {
         ChareDev &d = c->h_ch[i];
         memset(&d, 0, sizeof d);
         d.bx = h.bx; d.by = h.by; d.bz = h.bz; d.pitch = h.pitch;
+        d.rows = h.rows; d.row0 = h.row0;
         for (int f = 0; f < 6; ++f) d.nbr[f] = h.nbr[f];
         for (int f = 0; f < 7; ++f) d.foff[f] = h.foff[f];
         d.x0 = h.x0; d.y0 = h.y0; d.z0 = h.z0;
@@ -715,7 +727,7 @@ od_status od_create(od_ctx **out, const od_config *cfg_in) {
                                cudaMemcpyHostToDevice, c->stream));
     OD_TRY(cudaMemcpyAsync(c->d_order, p.order.data(), p.order.size() * sizeof(int32_t),
                            cudaMemcpyHostToDevice, c->stream));
-    OD_TRY(od::prepare_tile_kernels(p.threads, p.cpt, p.amode, p.smem_bytes));
+    OD_TRY(od::prepare_tile_kernels(p.threads, p.cpt, p.amode, p.smem_bytes, p.stencil));
     // per-chare path resources
     int P = cfg->stream_pool > 0 ? cfg->stream_pool : 32;
     P = (int)std::min<int64_t>(P, (int64_t)p.ch.size());
@@ -728,7 +740,8 @@ od_status od_create(od_ctx **out, const od_config *cfg_in) {
     OD_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     c->ev.resize(2 * p.ch.size(), nullptr);
     for (auto &e : c->ev) OD_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    OD_TRY(od::launch_init(c->d_ch, (int)p.ch.size(), p.nx, p.ny, p.nz, cfg->seed, cfg->init_mode, c->stream));
+    OD_TRY(od::launch_init(c->d_ch, (int)p.ch.size(), p.nx, p.ny, p.nz, cfg->seed, cfg->init_mode, p.stencil,
+                           c->stream));
     OD_TRY(cudaStreamSynchronize(c->stream));
 #undef OD_TRY
     *out = c;

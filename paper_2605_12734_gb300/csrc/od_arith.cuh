@@ -365,6 +365,80 @@ OD_HD double jacobi_update(double W, double E, double S, double N, double D, dou
     return ok ? v : jacobi_update_ieee<false>(W, E, S, N, D, U);
 }
 
+// ---------------------------------------------------------------- 2D update
+//
+// The paper's own application: the 5-point update (((W+E)+S)+N)/4.  Division
+// by 4 is an exact power-of-two scaling: for a normal result it only lowers
+// the exponent by two, which the integer pipes do in one subtraction.
+
+// s / 4 by the exponent; ok = false when s is zero, subnormal, infinite, NaN
+// or so small that s/4 would be subnormal (biased exponent < 3).
+OD_HD double div4_fast(double s, bool &ok) {
+    const uint64_t b = f64_bits(s);
+    const uint32_t es = (uint32_t)(b >> 52) & 0x7FFu;
+    ok = es - 3u <= 2043u;
+    return f64_from(b - (2ull << 52));
+}
+
+template <bool INT_DIV>
+OD_HD double jacobi2d_update_ieee(double W, double E, double S, double N) {
+    double s = ieee_add(W, E);
+    s = ieee_add(s, S);
+    s = ieee_add(s, N);
+    if (INT_DIV) {
+        bool ok;
+        const double v = div4_fast(s, ok);
+        if (ok) return v;
+    }
+    return ieee_div(s, 4.0);
+}
+
+// Same placement modes as jacobi_update_fast (the chain takes at most the
+// three adds there are); ok = false sends the cell to jacobi2d_update_ieee.
+template <int AM>
+OD_HD double jacobi2d_update_fast(double W, double E, double S, double N, bool &ok) {
+    constexpr int K0 = AM > 1 ? AM - 1 : 0;
+    constexpr int K = K0 > 3 ? 3 : K0;
+    if constexpr (AM == 0) {
+        ok = true;
+        return jacobi2d_update_ieee<false>(W, E, S, N);
+    } else if constexpr (K == 0) {
+        double s = ieee_add(W, E);
+        s = ieee_add(s, S);
+        s = ieee_add(s, N);
+        return div4_fast(s, ok);
+    } else {
+        const double x[4] = {W, E, S, N};
+        bool good;
+        uint32_t emax, p;
+        const uint64_t Wd = window_chain<K>(x, good, emax, p);
+        double s = pack_window(Wd, emax, p);
+#pragma unroll
+        for (int t = K + 1; t <= 3; ++t) s = ieee_add(s, x[t]);
+        bool okd;
+        const double v = div4_fast(s, okd);
+        ok = good & okd;
+        return v;
+    }
+}
+
+template <int AM>
+OD_HD double jacobi2d_update(double W, double E, double S, double N) {
+    bool ok;
+    const double v = jacobi2d_update_fast<AM>(W, E, S, N, ok);
+    return ok ? v : jacobi2d_update_ieee<false>(W, E, S, N);
+}
+
+OD_HD double jacobi2d_update_mode(int am, const double *x) {
+    switch (am) {
+        case 0: return jacobi2d_update<0>(x[0], x[1], x[2], x[3]);
+        case 1: return jacobi2d_update<1>(x[0], x[1], x[2], x[3]);
+        case 2: return jacobi2d_update<2>(x[0], x[1], x[2], x[3]);
+        case 3: return jacobi2d_update<3>(x[0], x[1], x[2], x[3]);
+        default: return jacobi2d_update<4>(x[0], x[1], x[2], x[3]);
+    }
+}
+
 // Run-time dispatch of jacobi_update (tests).
 OD_HD double jacobi_update_mode(int am, const double *x) {
     switch (am) {

@@ -14,6 +14,13 @@
 // Edge and corner ghost cells of the padded box exist but are never read by
 // a 7-point stencil.
 //
+// The 2D 5-point stencil runs on the internal grid (nx, 1, ny): a chare's 2D
+// rows are its "planes", and a plane is a single row (rows = 1, no y-ghost
+// rows), so A[p] is the chare's padded 2D block, (bz+2) rows x pitch:
+// interior cell (i, k) is A[p][(k+1)*pitch + i+1].  In general a plane holds
+// `rows` rows and interior row j sits at row j + row0 of it: rows = by+2,
+// row0 = 1 in 3D; rows = 1, row0 = 0 in 2D.
+//
 // A neighbour "delivers" a face by storing straight into these ghost cells
 // (the chare's mailbox).  Faces on the domain boundary hold the Dirichlet
 // shell in both parities and are never written after initialisation.
@@ -35,6 +42,7 @@
 struct ChareDev {
     int32_t bx, by, bz;     // interior extents
     int32_t pitch;          // row stride of A, doubles
+    int32_t rows, row0;     // rows per plane; row of interior row 0 in a plane
     int32_t nbr[6];         // neighbour per face or -1 (Dirichlet)
     int32_t foff[7];        // face offsets inside send/recv buffers (doubles)
     int64_t x0, y0, z0;     // global interior offset of cell (0,0,0)
@@ -43,11 +51,12 @@ struct ChareDev {
     double *recv[2];        // per-chare path: faces from neighbours, 2 slots
 };
 
-// One compute task: rows [j0,j0+nj) x planes [k0,k0+nk) of chare c, all bx
-// columns.
+// One compute task: columns [i0,i0+ni) x rows [j0,j0+nj) x planes
+// [k0,k0+nk) of chare c (3D tiles take whole rows: i0 = 0, ni = bx).
 struct TileDev {
     int32_t c, j0, nj, k0, nk;
-    int32_t pad[3];
+    int32_t i0, ni;
+    int32_t pad;
 };
 
 // Error record written by kernels (first error wins).
@@ -76,6 +85,8 @@ struct KArgs {
     int32_t order_mode;      // persistent: 1 = reverse order on odd steps
     int32_t stages;          // TMA ring depth
     int32_t stage_doubles;   // doubles per ring slot
+    int32_t stencil;         // OD_STENCIL_3D7 or OD_STENCIL_2D5
+    int32_t pad0;
     int64_t stall_tile;      // fault injection (-1 = off)
     uint64_t spin_ns;        // bound on every device-side wait
 };

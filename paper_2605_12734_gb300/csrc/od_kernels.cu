@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "od.h"
 #include "od_arith.cuh"
 #include "od_internal.h"
 #include "od_kernels.h"
@@ -19,10 +20,30 @@ void *tile_kernel_am5(int threads, int cpt, int kind);
 void *tile_kernel_am6(int threads, int cpt, int kind);
 void *tile_kernel_am7(int threads, int cpt, int kind);
 void *tile_kernel_am8(int threads, int cpt, int kind);
+void *tile_kernel2d_am0(int threads, int cpt, int kind);
+void *tile_kernel2d_am1(int threads, int cpt, int kind);
+void *tile_kernel2d_am2(int threads, int cpt, int kind);
+void *tile_kernel2d_am3(int threads, int cpt, int kind);
+void *tile_kernel2d_am4(int threads, int cpt, int kind);
+void *tile_kernel2d_am7(int threads, int cpt, int kind);
+void *tile_kernel2d_am8(int threads, int cpt, int kind);
 
 namespace {
 
-void *tile_kernel(int amode, int threads, int cpt, int kind) {
+void *tile_kernel(int stencil, int amode, int threads, int cpt, int kind) {
+    if (stencil == OD_STENCIL_2D5) switch (amode) {
+        // the 2D update has three adds, so modes 4..6 (three or more window
+        // adds) are the same kernel
+        case 0: return tile_kernel2d_am0(threads, cpt, kind);
+        case 1: return tile_kernel2d_am1(threads, cpt, kind);
+        case 2: return tile_kernel2d_am2(threads, cpt, kind);
+        case 3: return tile_kernel2d_am3(threads, cpt, kind);
+        case 4: case 5: case 6: return tile_kernel2d_am4(threads, cpt, kind);
+        case 7: return tile_kernel2d_am7(threads, cpt, kind);
+        case 8: return tile_kernel2d_am8(threads, cpt, kind);
+        default: return nullptr;
+    }
+    if (stencil != OD_STENCIL_3D7) return nullptr;
     switch (amode) {
         case 0: return tile_kernel_am0(threads, cpt, kind);
         case 1: return tile_kernel_am1(threads, cpt, kind);
@@ -59,12 +80,13 @@ __device__ __forceinline__ double field_init(int64_t gx, int64_t gy, int64_t gz,
 
 // Classify element e of a chare's padded array: returns false for padding
 // and for edge/corner ghosts (never read), else the padded global
-// coordinates of the cell it holds.
+// coordinates of the cell it holds (a 2D chare has no y-ghost rows: its
+// cells all get padded y index 1).
 __device__ __forceinline__ bool padded_cell(const ChareDev &C, int64_t e, int64_t *gx, int64_t *gy,
                                             int64_t *gz) {
     const int col = (int)(e % C.pitch);
     const int64_t row = e / C.pitch;
-    const int jp = (int)(row % (C.by + 2)), kp = (int)(row / (C.by + 2));
+    const int jp = (int)(row % C.rows) + 1 - C.row0, kp = (int)(row / C.rows);
     if (col > C.bx + 1) return false;
     const int ghosts = (col == 0 || col == C.bx + 1) + (jp == 0 || jp == C.by + 1) + (kp == 0 || kp == C.bz + 1);
     if (ghosts > 1) return false;
@@ -75,16 +97,25 @@ __device__ __forceinline__ bool padded_cell(const ChareDev &C, int64_t e, int64_
 }
 
 // A2: the initial field in both parities, interior and every ghost cell.
+// For the 2D stencil (internal grid (nx, 1, ny)) a cell takes its 2D padded
+// index gx + (nx+2)*gz.
 __global__ void k_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
-                       int mode) {
+                       int mode, int stencil) {
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
-        const int64_t na = (int64_t)(C.bz + 2) * (C.by + 2) * C.pitch;
+        const int64_t na = (int64_t)(C.bz + 2) * C.rows * C.pitch;
         for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na;
              e += (int64_t)gridDim.x * blockDim.x) {
             int64_t gx, gy, gz;
             double v = 0.0;
-            if (padded_cell(C, e, &gx, &gy, &gz)) v = field_init(gx, gy, gz, nx, ny, nz, seed, mode);
+            if (padded_cell(C, e, &gx, &gy, &gz)) {
+                if (stencil == OD_STENCIL_2D5) {
+                    const bool shell = gx == 0 || gz == 0 || gx == nx + 1 || gz == nz + 1;
+                    if (shell || mode != 0) v = field_uniform(seed, (uint64_t)(gx + (nx + 2) * gz));
+                } else {
+                    v = field_init(gx, gy, gz, nx, ny, nz, seed, mode);
+                }
+            }
             C.A[0][e] = v;
             C.A[1][e] = v;
         }
@@ -94,21 +125,21 @@ __global__ void k_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int6
 // Offset in A of face element q of face f: `ghost` = false gives the
 // chare's own boundary cell (pack), true the ghost cell facing it (unpack).
 __device__ __forceinline__ int64_t face_offset(const ChareDev &C, int f, int q, bool ghost) {
-    const int bx = C.bx, by = C.by, bz = C.bz, pitch = C.pitch;
-    const int64_t plane = (int64_t)(by + 2) * pitch;
+    const int bx = C.bx, by = C.by, bz = C.bz, pitch = C.pitch, r0 = C.row0;
+    const int64_t plane = (int64_t)C.rows * pitch;
     if (f < 2) {
         const int k = q / by, j = q - k * by;
         const int col = f == OD_FACE_XLO ? (ghost ? 0 : 1) : (ghost ? bx + 1 : bx);
-        return (k + 1) * plane + (int64_t)(j + 1) * pitch + col;
+        return (k + 1) * plane + (int64_t)(j + r0) * pitch + col;
     }
-    if (f < 4) {
+    if (f < 4) {  // (3D only: a 2D chare has no y faces)
         const int k = q / bx, i = q - k * bx;
         const int row = f == OD_FACE_YLO ? (ghost ? 0 : 1) : (ghost ? by + 1 : by);
         return (k + 1) * plane + (int64_t)row * pitch + i + 1;
     }
     const int j = q / bx, i = q - j * bx;
     const int pl = f == OD_FACE_ZLO ? (ghost ? 0 : 1) : (ghost ? bz + 1 : bz);
-    return (int64_t)pl * plane + (int64_t)(j + 1) * pitch + i + 1;
+    return (int64_t)pl * plane + (int64_t)(j + r0) * pitch + i + 1;
 }
 
 // Per-chare path, A4: new boundary planes of parity p -> contiguous send
@@ -142,14 +173,14 @@ __global__ void k_gather(const ChareDev *ch, int nch, int p, int64_t nx, int64_t
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
         const int64_t n = (int64_t)C.bx * C.by * C.bz;
-        const int64_t plane = (int64_t)(C.by + 2) * C.pitch;
+        const int64_t plane = (int64_t)C.rows * C.pitch;
         for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
              e += (int64_t)gridDim.x * blockDim.x) {
             const int i = (int)(e % C.bx);
             const int64_t r = e / C.bx;
             const int j = (int)(r % C.by), k = (int)(r / C.by);
             g[(C.z0 + k) * ny * nx + (C.y0 + j) * nx + C.x0 + i] =
-                C.A[p][(k + 1) * plane + (int64_t)(j + 1) * C.pitch + i + 1];
+                C.A[p][(k + 1) * plane + (int64_t)(j + C.row0) * C.pitch + i + 1];
         }
     }
 }
@@ -160,7 +191,7 @@ __global__ void k_scatter(const ChareDev *ch, int nch, int p, int64_t nx, int64_
                           const double *g) {
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
-        const int64_t na = (int64_t)(C.bz + 2) * (C.by + 2) * C.pitch;
+        const int64_t na = (int64_t)(C.bz + 2) * C.rows * C.pitch;
         for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na;
              e += (int64_t)gridDim.x * blockDim.x) {
             int64_t gx, gy, gz;
@@ -182,7 +213,9 @@ __global__ void k_arith(int op, const double *a, const double *b, double *out, i
             case 1: r = add(a[i], b[i]); break;
             case 2: r = __ddiv_rn(a[i], 6.0); break;
             case 3: r = __dadd_rn(a[i], b[i]); break;
-            default: r = jacobi_update_mode(op - 10, a + 6 * i); break;
+            default:
+                r = op < 20 ? jacobi_update_mode(op - 10, a + 6 * i) : jacobi2d_update_mode(op - 20, a + 4 * i);
+                break;
         }
         out[i] = r;
     }
@@ -198,17 +231,17 @@ int io_grid_x(int nch) {
 
 }  // namespace
 
-bool tile_shape_supported(int threads, int cpt, int amode) {
-    return tile_kernel(amode, threads, cpt, 0) != nullptr;
+bool tile_shape_supported(int threads, int cpt, int amode, int stencil) {
+    return tile_kernel(stencil, amode, threads, cpt, 0) != nullptr;
 }
 
 // The dynamic shared-memory cap is per kernel function and shared by every
 // context in the process, so it is raised once to what the hardware allows
 // (227 KB per CTA less the kernel's static shared memory) and never lowered:
 // the launch's own size decides occupancy, the cap only permits it.
-cudaError_t prepare_tile_kernels(int threads, int cpt, int amode, int smem_bytes) {
-    void *fns[4] = {tile_kernel(amode, threads, cpt, 0), tile_kernel(amode, threads, cpt, 1),
-                    tile_kernel(amode, threads, cpt, 2), tile_kernel(amode, threads, cpt, 3)};
+cudaError_t prepare_tile_kernels(int threads, int cpt, int amode, int smem_bytes, int stencil) {
+    void *fns[4] = {tile_kernel(stencil, amode, threads, cpt, 0), tile_kernel(stencil, amode, threads, cpt, 1),
+                    tile_kernel(stencil, amode, threads, cpt, 2), tile_kernel(stencil, amode, threads, cpt, 3)};
     for (void *f : fns) {
         if (!f) return cudaErrorInvalidValue;
         cudaFuncAttributes fa;
@@ -226,7 +259,7 @@ cudaError_t prepare_tile_kernels(int threads, int cpt, int amode, int smem_bytes
 
 cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, int amode, bool push, int smem_bytes,
                          cudaStream_t s) {
-    void *f = tile_kernel(amode, threads, cpt, push ? 1 : 0);
+    void *f = tile_kernel(a.stencil, amode, threads, cpt, push ? 1 : 0);
     if (!f) return cudaErrorInvalidValue;
     if (grid <= 0) return cudaSuccess;
     void *args[] = {(void *)&a};
@@ -235,7 +268,7 @@ cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, int amo
 
 cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, int amode, int smem_bytes,
                               cudaStream_t s) {
-    void *f = tile_kernel(amode, threads, cpt, 2);
+    void *f = tile_kernel(a.stencil, amode, threads, cpt, 2);
     if (!f) return cudaErrorInvalidValue;
     if (grid <= 0) return cudaSuccess;
     void *args[] = {(void *)&a};
@@ -243,23 +276,24 @@ cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, in
 }
 
 cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int grid, int threads,
-                               int cpt, int amode, int smem_bytes, cudaStream_t s) {
-    void *f = tile_kernel(amode, threads, cpt, 3);
+                               int cpt, int amode, int smem_bytes, int stencil, cudaStream_t s) {
+    void *f = tile_kernel(stencil, amode, threads, cpt, 3);
     if (!f) return cudaErrorInvalidValue;
     if (grid <= 0 || njobs <= 0) return cudaSuccess;
     void *args[] = {(void *)&jobs, (void *)&first, (void *)&njobs};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, (size_t)smem_bytes, s);
 }
 
-cudaError_t persistent_occupancy(int threads, int cpt, int amode, int smem_bytes, int *blocks_per_sm) {
-    void *f = tile_kernel(amode, threads, cpt, 2);
+cudaError_t persistent_occupancy(int threads, int cpt, int amode, int smem_bytes, int stencil,
+                                 int *blocks_per_sm) {
+    void *f = tile_kernel(stencil, amode, threads, cpt, 2);
     if (!f) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, (size_t)smem_bytes);
 }
 
 cudaError_t launch_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
-                        int mode, cudaStream_t s) {
-    k_init<<<dim3(io_grid_x(nch), io_grid_y(nch)), 256, 0, s>>>(ch, nch, nx, ny, nz, seed, mode);
+                        int mode, int stencil, cudaStream_t s) {
+    k_init<<<dim3(io_grid_x(nch), io_grid_y(nch)), 256, 0, s>>>(ch, nch, nx, ny, nz, seed, mode, stencil);
     return cudaGetLastError();
 }
 

@@ -8,13 +8,15 @@
 namespace od {
 
 // Tile kernels exist for (threads, cells per thread) in {128}x{2,4,8},
-// {256}x{1,2,4,8}, {512}x{1,2} and arithmetic modes 0..6 (od_tile.cuh).
-bool tile_shape_supported(int threads, int cpt, int amode);
+// {256}x{1,2,4,8}, {512}x{1,2}, arithmetic modes 0..8 and both stencils
+// (OD_STENCIL_3D7, OD_STENCIL_2D5) (od_tile.cuh).
+bool tile_shape_supported(int threads, int cpt, int amode, int stencil);
 
 // Raise the dynamic shared-memory limit of the tile kernels of one shape.
-cudaError_t prepare_tile_kernels(int threads, int cpt, int amode, int smem_bytes);
+cudaError_t prepare_tile_kernels(int threads, int cpt, int amode, int smem_bytes, int stencil);
 
-// One CTA per tile, tiles [a.tile_begin, a.tile_begin + grid).  push = 1 also
+// One CTA per tile, tiles [a.tile_begin, a.tile_begin + grid), of stencil
+// a.stencil (so for launch_persistent).  push = 1 also
 // stores each new boundary value into the neighbour's ghost layer.
 cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, int amode, bool push, int smem_bytes,
                          cudaStream_t s);
@@ -23,15 +25,16 @@ cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, int amo
 // array) is job j's KArgs with its source parity, first[j] its first block
 // (device array of njobs+1 prefix sums, first[njobs] = grid).
 cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int grid, int threads,
-                               int cpt, int amode, int smem_bytes, cudaStream_t s);
+                               int cpt, int amode, int smem_bytes, int stencil, cudaStream_t s);
 
 // Persistent ticket kernel over a.iters steps.
 cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, int amode, int smem_bytes,
                               cudaStream_t s);
-cudaError_t persistent_occupancy(int threads, int cpt, int amode, int smem_bytes, int *blocks_per_sm);
+cudaError_t persistent_occupancy(int threads, int cpt, int amode, int smem_bytes, int stencil,
+                                 int *blocks_per_sm);
 
 cudaError_t launch_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
-                        int mode, cudaStream_t s);
+                        int mode, int stencil, cudaStream_t s);
 cudaError_t launch_pack(const ChareDev *ch, int c, int parity, int elems, cudaStream_t s);
 cudaError_t launch_unpack(const ChareDev *ch, int c, int parity, int slot, int elems, cudaStream_t s);
 cudaError_t launch_gather(const ChareDev *ch, int nch, int parity, int64_t nx, int64_t ny, double *g,

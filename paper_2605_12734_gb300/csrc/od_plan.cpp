@@ -66,7 +66,7 @@ struct Box {
 
 Box tile_box(const HostChare &c, const TileDev &t) {
     Box b;
-    b.lo[0] = c.x0;           b.hi[0] = c.x0 + c.bx;
+    b.lo[0] = c.x0 + t.i0;    b.hi[0] = b.lo[0] + t.ni;
     b.lo[1] = c.y0 + t.j0;    b.hi[1] = b.lo[1] + t.nj;
     b.lo[2] = c.z0 + t.k0;    b.hi[2] = b.lo[2] + t.nk;
     return b;
@@ -150,11 +150,31 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         *err = "tile sizes must be >= 0";
         return OD_EINVAL;
     }
-    p.nx = cfg->nx; p.ny = cfg->ny; p.nz = cfg->nz;
-    if (!edges_from(cfg->nx, cfg->px, cfg->cuts_x, cfg->ncuts_x, "x", &p.ex, err) ||
-        !edges_from(cfg->ny, cfg->py, cfg->cuts_y, cfg->ncuts_y, "y", &p.ey, err) ||
-        !edges_from(cfg->nz, cfg->pz, cfg->cuts_z, cfg->ncuts_z, "z", &p.ez, err))
+    if (cfg->stencil != OD_STENCIL_3D7 && cfg->stencil != OD_STENCIL_2D5) {
+        *err = "unknown stencil";
         return OD_EINVAL;
+    }
+    p.stencil = cfg->stencil;
+    if (p.stencil == OD_STENCIL_2D5) {
+        // A 2D nx x ny grid is laid out as the 3D grid (nx, 1, ny): the 2D rows
+        // are the planes the kernels stream, and the (unused) y-ghost rows of
+        // every plane keep the 3D layout and I/O kernels valid unchanged.
+        if (cfg->nz != 1 || (cfg->cuts_z && cfg->ncuts_z != 1) || (!cfg->cuts_z && cfg->pz > 1)) {
+            *err = "the 2D stencil needs nz = 1 and a single block along z";
+            return OD_EINVAL;
+        }
+        p.nx = cfg->nx; p.ny = 1; p.nz = cfg->ny;
+        if (!edges_from(cfg->nx, cfg->px, cfg->cuts_x, cfg->ncuts_x, "x", &p.ex, err) ||
+            !edges_from(cfg->ny, cfg->py, cfg->cuts_y, cfg->ncuts_y, "y", &p.ez, err))
+            return OD_EINVAL;
+        p.ey = {0, 1};
+    } else {
+        p.nx = cfg->nx; p.ny = cfg->ny; p.nz = cfg->nz;
+        if (!edges_from(cfg->nx, cfg->px, cfg->cuts_x, cfg->ncuts_x, "x", &p.ex, err) ||
+            !edges_from(cfg->ny, cfg->py, cfg->cuts_y, cfg->ncuts_y, "y", &p.ey, err) ||
+            !edges_from(cfg->nz, cfg->pz, cfg->cuts_z, cfg->ncuts_z, "z", &p.ez, err))
+            return OD_EINVAL;
+    }
     p.px = (int32_t)p.ex.size() - 1;
     p.py = (int32_t)p.ey.size() - 1;
     p.pz = (int32_t)p.ez.size() - 1;
@@ -163,7 +183,14 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         *err = "more than 2^24 chares";
         return OD_EINVAL;
     }
-    if (auto_shape) {
+    if (auto_shape && p.stencil == OD_STENCIL_2D5) {
+        // 2D tiles are row segments of up to threads x cpt cells: 128 x 4, or
+        // 128 x 2 when every chare row fits in 256 cells
+        int64_t wmax = 0;
+        for (int64_t e = 1; e < (int64_t)p.ex.size(); ++e) wmax = std::max(wmax, p.ex[e] - p.ex[e - 1]);
+        p.threads = 128;
+        p.cpt = wmax <= 256 ? 2 : 4;
+    } else if (auto_shape) {
         // smallest CTA shape that holds two rows of the widest chare (one if
         // none does): 128 x 4, 256 x 4, 256 x 8 cells
         int64_t wmax = 0;
@@ -178,7 +205,7 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         p.threads = shapes[pick][0];
         p.cpt = shapes[pick][1];
     }
-    for (int64_t e = 1; e < (int64_t)p.ex.size(); ++e)
+    for (int64_t e = 1; e < (int64_t)p.ex.size() && p.stencil == OD_STENCIL_3D7; ++e)
         if (p.ex[e] - p.ex[e - 1] > (int64_t)p.threads * p.cpt) {
             char buf[200];
             snprintf(buf, sizeof buf,
@@ -201,28 +228,67 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
                 h.y0 = p.ey[cy]; h.by = (int32_t)(p.ey[cy + 1] - p.ey[cy]);
                 h.z0 = p.ez[cz]; h.bz = (int32_t)(p.ez[cz + 1] - p.ez[cz]);
                 h.pitch = round_up(h.bx + 2, 2);
+                h.rows = p.stencil == OD_STENCIL_2D5 ? 1 : h.by + 2;
+                h.row0 = p.stencil == OD_STENCIL_2D5 ? 0 : 1;
                 h.nbr[OD_FACE_XLO] = cx > 0 ? (int32_t)(c - 1) : -1;
                 h.nbr[OD_FACE_XHI] = cx < p.px - 1 ? (int32_t)(c + 1) : -1;
                 h.nbr[OD_FACE_YLO] = cy > 0 ? (int32_t)(c - p.px) : -1;
                 h.nbr[OD_FACE_YHI] = cy < p.py - 1 ? (int32_t)(c + p.px) : -1;
                 h.nbr[OD_FACE_ZLO] = cz > 0 ? (int32_t)(c - (int64_t)p.px * p.py) : -1;
                 h.nbr[OD_FACE_ZHI] = cz < p.pz - 1 ? (int32_t)(c + (int64_t)p.px * p.py) : -1;
-                int32_t fs[6] = {h.by * h.bz, h.by * h.bz, h.bx * h.bz, h.bx * h.bz, h.bx * h.by, h.bx * h.by};
+                const int64_t bx = h.bx, by = h.by, bz = h.bz;
+                int64_t fs[6] = {by * bz, by * bz, bx * bz, bx * bz, bx * by, bx * by};
+                if (p.stencil == OD_STENCIL_2D5) fs[OD_FACE_YLO] = fs[OD_FACE_YHI] = 0;  // no y faces in 2D
+                if (fs[0] + fs[1] + fs[2] + fs[3] + fs[4] + fs[5] > 0x7fffffffll) {
+                    *err = "a block's faces exceed 2^31 cells; use more blocks";
+                    return OD_EINVAL;
+                }
                 h.foff[0] = 0;
-                for (int f = 0; f < 6; ++f) h.foff[f + 1] = h.foff[f] + fs[f];
+                for (int f = 0; f < 6; ++f) h.foff[f + 1] = h.foff[f] + (int32_t)fs[f];
                 for (int f = 0; f < 6; ++f) {
                     if (h.nbr[f] >= 0) p.face_internal += fs[f];
                     else p.face_dirichlet += fs[f];
                 }
             }
-    p.cells = cfg->nx * cfg->ny * cfg->nz;
+    p.cells = p.nx * p.ny * p.nz;
     p.bytes_per_step = 16.0 * (double)p.cells + 16.0 * (double)p.face_internal +
                        8.0 * (double)p.face_dirichlet;
 
     // tiles: full rows, balanced row slabs and plane chunks
     std::vector<int32_t> js, jl, ks, kl;
     int32_t max_stage = 0;
-    for (size_t c = 0; c < p.ch.size(); ++c) {
+    for (size_t c = 0; c < p.ch.size() && p.stencil == OD_STENCIL_2D5; ++c) {
+        // 2D: tiles of one row segment (x range) x a run of rows (planes); the
+        // segment start is even so its bulk copy stays 16-byte aligned
+        HostChare &h = p.ch[c];
+        int32_t cap = p.threads * p.cpt;
+        if (p.tile_y > 0) cap = std::min(cap, p.tile_y);  // tile_y caps the segment for 2D
+        const int32_t nseg = (h.bx + cap - 1) / cap;
+        const int32_t w = round_up((h.bx + nseg - 1) / nseg, 2);
+        int32_t tz = p.tile_z > 0 ? p.tile_z : 32;
+        tz = std::min(tz, h.bz);
+        balanced_parts(h.bz, tz, &ks, &kl);
+        h.tile_begin = (int32_t)p.tiles.size();
+        for (size_t a = 0; a < ks.size(); ++a)
+            for (int32_t i0 = 0; i0 < h.bx; i0 += w) {
+                TileDev t;
+                memset(&t, 0, sizeof t);
+                t.c = (int32_t)c;
+                t.j0 = 0; t.nj = 1;
+                t.k0 = ks[a]; t.nk = kl[a];
+                t.i0 = i0; t.ni = std::min(w, h.bx - i0);
+                p.tiles.push_back(t);
+                max_stage = std::max(max_stage, round_up(t.ni + 4, 16));
+                p.max_nj = std::max(p.max_nj, t.ni);
+                p.max_nk = std::max(p.max_nk, t.nk);
+                if (p.tiles.size() > (size_t)0x7fffffff) {
+                    *err = "too many tiles";
+                    return OD_EINVAL;
+                }
+            }
+        h.tile_end = (int32_t)p.tiles.size();
+    }
+    for (size_t c = 0; c < p.ch.size() && p.stencil == OD_STENCIL_3D7; ++c) {
         HostChare &h = p.ch[c];
         int32_t nj_cap = (p.threads * p.cpt) / h.bx;
         if (p.tile_y > 0) nj_cap = std::min(nj_cap, p.tile_y);
@@ -239,6 +305,7 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
                 t.c = (int32_t)c;
                 t.j0 = js[b]; t.nj = jl[b];
                 t.k0 = ks[a]; t.nk = kl[a];
+                t.i0 = 0; t.ni = h.bx;
                 p.tiles.push_back(t);
                 max_stage = std::max(max_stage, stage_doubles_for(t.nj, h.pitch));
                 p.max_nj = std::max(p.max_nj, t.nj);
@@ -253,7 +320,7 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
     p.stage_doubles = max_stage;
     // the tile kernels pack a cell's ring offset into 16 bits and its tile row
     // into 11 bits
-    if (p.stage_doubles >= 65536 || p.max_nj > 2048) {
+    if (p.stage_doubles >= 65536 || (p.stencil == OD_STENCIL_3D7 && p.max_nj > 2048)) {
         *err = "tile too large for the kernels' cell encoding; lower tile_y";
         return OD_EINVAL;
     }
@@ -304,7 +371,7 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
     p.off_dep_idx = take(std::max<size_t>(1, p.dep_idx.size()) * sizeof(int32_t));
     p.off_order = take(p.order.size() * sizeof(int32_t));
     for (auto &h : p.ch) {
-        size_t a_bytes = (size_t)(h.bz + 2) * (size_t)(h.by + 2) * (size_t)h.pitch * 8;
+        size_t a_bytes = (size_t)(h.bz + 2) * (size_t)h.rows * (size_t)h.pitch * 8;
         size_t f_bytes = (size_t)h.foff[6] * 8;
         for (int s = 0; s < 2; ++s) h.offA[s] = take(a_bytes);
         h.offSend = take(f_bytes);

@@ -16,6 +16,7 @@ struct HostChare {
     int32_t cx, cy, cz;
     int64_t x0, y0, z0;
     int32_t bx, by, bz, pitch;
+    int32_t rows, row0;             // plane layout (see ChareDev)
     int32_t nbr[6];
     int32_t foff[7];
     size_t offA[2];
@@ -24,7 +25,8 @@ struct HostChare {
 };
 
 struct Plan {
-    int64_t nx = 0, ny = 0, nz = 0;
+    int32_t stencil = 0;                      // OD_STENCIL_*; 2D runs as (nx, 1, ny)
+    int64_t nx = 0, ny = 0, nz = 0;           // internal (3D) extents
     int32_t px = 0, py = 0, pz = 0;
     std::vector<int64_t> ex, ey, ez;          // block edges per axis
     std::vector<HostChare> ch;

@@ -252,7 +252,7 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
     cudaMemcpyAsync(s->d_first[slot], hf.data(), hf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s->compute);
     const int smem = 256 + s->stages * max_sd * 8;
     cudaError_t e = od::launch_tiles_multi(s->d_jobs[slot], s->d_first[slot], (int32_t)in.size(), grid, s->threads,
-                                           s->cpt, s->arith, smem, s->compute);
+                                           s->cpt, s->arith, smem, OD_STENCIL_3D7, s->compute);
     if (e != cudaSuccess) {
         s->worker_error = std::string("k_tiles_multi: ") + cudaGetErrorString(e);
         return false;
@@ -337,7 +337,7 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
         return fail(st, m);
     };
     if (cudaSetDevice(s->device) != cudaSuccess) return bail(OD_ECUDA, "cannot select the CUDA device");
-    if (!od::tile_shape_supported(s->threads, s->cpt, s->arith)) return bail(OD_EINVAL, "unsupported tile shape");
+    if (!od::tile_shape_supported(s->threads, s->cpt, s->arith, OD_STENCIL_3D7)) return bail(OD_EINVAL, "unsupported tile shape");
     if (cfg->pool) {
         if ((uintptr_t)cfg->pool & 255u) return bail(OD_EINVAL, "pool must be 256-byte aligned");
         s->pool_base = (char *)cfg->pool;
@@ -358,7 +358,7 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
             cudaMalloc(&s->d_first[k], (size_t)(s->max_jobs + 1) * sizeof(int32_t)) != cudaSuccess)
             return bail(OD_ENOMEM, "cannot allocate launch tables");
     s->smem_cap = 200 * 1024;
-    if (od::prepare_tile_kernels(s->threads, s->cpt, s->arith, s->smem_cap) != cudaSuccess)
+    if (od::prepare_tile_kernels(s->threads, s->cpt, s->arith, s->smem_cap, OD_STENCIL_3D7) != cudaSuccess)
         return bail(OD_ECUDA, "cannot configure the tile kernels");
     s->worker = std::thread(worker_main, s);
     *out = s;
@@ -367,6 +367,8 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
 
 od_status od_server_submit(od_server *s, const od_config *job, int32_t iters, uint64_t *job_id) {
     if (!s || !job || !job_id || iters < 0) return fail(OD_EINVAL, "bad arguments");
+    // one batched launch shares one kernel, the 3D 7-point one
+    if (job->stencil != OD_STENCIL_3D7) return fail(OD_EINVAL, "the serving loop runs 3D 7-point jobs only");
     Job *j = new Job();
     j->cfg = *job;
     const int32_t *cp[3] = {job->cuts_x, job->cuts_y, job->cuts_z};

@@ -26,6 +26,7 @@
 
 #include <type_traits>
 
+#include "od.h"
 #include "od_arith.cuh"
 #include "od_internal.h"
 
@@ -329,6 +330,166 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     return true;
 }
 
+// IEEE form of the 2D update (out of line, as update_slow).
+static __device__ __noinline__ double update2d_slow(double W, double E, double S, double N) {
+    return jacobi2d_update_ieee<false>(W, E, S, N);
+}
+
+// The 2D 5-point sweep (the paper's Jacobi2D, Sec. V) on the internal grid
+// (nx, 1, ny): a chare's 2D rows are its planes, one row each, so A is the
+// padded 2D block and plane k (interior row k) starts at (k+1)*pitch.  A tile
+// is one row segment, columns [i0, i0+ni), over planes [k0, k0+nk).  Per
+// plane one bulk copy brings columns i0 .. i0+ni+1 (the segment plus its
+// x-halo, rounded up to an even count; i0 and pitch are even, so the copy
+// starts 16-byte aligned) into a ring slot; slot offset r = i+1 holds column
+// i0+i+1, i.e. the tile's cell i.
+// The update reads W = slot[r-1], E = slot[r+1] of plane k, S = plane k-1,
+// N = plane k+1 at r, summed in that order and divided by 4.
+template <int NT, int CPT, bool PUSH, int AM>
+__device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp, Ring &ring, PushInfo *pi,
+                                            int step) {
+    const TileDev T = a.tiles[tile_id];
+    const ChareDev &C = a.ch[T.c];
+    const int bx = C.bx, bz = C.bz, pitch = C.pitch;
+    const int plane = pitch;
+    const int dp = sp ^ 1;
+    const double *__restrict__ src = C.A[sp] + T.i0;  // column i0 of the lower ghost row
+    double *__restrict__ dst = C.A[dp] + T.i0;
+    const uint32_t run_bytes = (uint32_t)((T.ni + 3) & ~1) * 8u;
+    const int S = a.stages, SD = a.stage_doubles;
+    const int kb = T.k0 - 1, ke = T.k0 + T.nk;
+    const int tid = threadIdx.x;
+    const uint32_t seq0 = ring.seq;
+
+    auto slot = [&](int p) -> uint32_t { return (seq0 + (uint32_t)(p - kb)) % (uint32_t)S; };
+    auto phase = [&](int p) -> uint32_t { return ((seq0 + (uint32_t)(p - kb)) / (uint32_t)S) & 1u; };
+    auto issue = [&](int p) {
+        const uint32_t s = slot(p);
+        uint64_t *bar = ring.bars + s;
+        mbar_expect_tx(bar, run_bytes);
+        bulk_g2s(ring.base + (size_t)s * SD, src + (size_t)(p + 1) * plane, run_bytes, bar);
+    };
+    int issued_hi = kb - 1;
+    auto drain = [&](int from) {
+        if (tid == 0)
+            for (int p = from; p <= issued_hi; ++p) mbar_wait_bounded(ring.bars + slot(p), phase(p), a.spin_ns);
+        ring.seq = seq0 + (uint32_t)(issued_hi - kb + 1);
+    };
+
+    if (tid == 0) {
+        const int last = min(ke, kb + S - 1);
+        for (int p = kb; p <= last; ++p) issue(p);
+        if (PUSH) {
+            PushInfo q;
+            q.xlo = q.xhi = q.ylo = q.yhi = q.zlo = q.zhi = nullptr;
+            q.xlo_pitch = q.xlo_plane = q.xhi_pitch = q.xhi_plane = q.ylo_plane = q.yhi_plane = 0;
+            if (C.nbr[OD_FACE_XLO] >= 0) {  // column 0 -> its ghost column bx_n+1
+                const ChareDev &N = a.ch[C.nbr[OD_FACE_XLO]];
+                q.xlo_plane = N.pitch;
+                q.xlo = N.A[dp] + (N.bx + 1);
+            }
+            if (C.nbr[OD_FACE_XHI] >= 0) {  // column bx-1 -> its ghost column 0
+                const ChareDev &N = a.ch[C.nbr[OD_FACE_XHI]];
+                q.xhi_plane = N.pitch;
+                q.xhi = N.A[dp];
+            }
+            if (C.nbr[OD_FACE_ZLO] >= 0) {  // row 0 -> its ghost row bz_n+1 (same bx, same pitch)
+                const ChareDev &N = a.ch[C.nbr[OD_FACE_ZLO]];
+                q.zlo = N.A[dp] + (size_t)(N.bz + 1) * plane + T.i0;
+            }
+            if (C.nbr[OD_FACE_ZHI] >= 0) q.zhi = a.ch[C.nbr[OD_FACE_ZHI]].A[dp] + T.i0;
+            *pi = q;
+        }
+    }
+    issued_hi = min(ke, kb + S - 1);
+
+    // this thread's cells q = tid + m*NT of the segment; a slot past its end
+    // repeats cell 0 and stores nothing
+    uint32_t rf[CPT];
+#pragma unroll
+    for (int m = 0; m < CPT; ++m) {
+        const int q0 = tid + m * NT;
+        const bool valid = q0 < T.ni;
+        const int q = valid ? q0 : 0;
+        uint32_t w = (uint32_t)(q + 1);
+        if (valid) {
+            w |= kValid;
+            if (PUSH) {
+                if (T.i0 + q == 0 && C.nbr[OD_FACE_XLO] >= 0) w |= kXlo;
+                if (T.i0 + q == bx - 1 && C.nbr[OD_FACE_XHI] >= 0) w |= kXhi;
+            }
+        }
+        rf[m] = w;
+    }
+
+    bool fail = !mbar_wait_bounded(ring.bars + slot(kb), phase(kb), a.spin_ns);
+    if (!fail) fail = !mbar_wait_bounded(ring.bars + slot(kb + 1), phase(kb + 1), a.spin_ns);
+    if (__syncthreads_or(fail)) {
+        if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
+        drain(kb);
+        return false;
+    }
+
+    auto compute_plane = [&](auto zp_tag, int k, double *zp) {
+        constexpr bool ZP = decltype(zp_tag)::value;
+        const double *sd = ring.base + (size_t)slot(k - 1) * SD;
+        const double *sc = ring.base + (size_t)slot(k) * SD;
+        const double *su = ring.base + (size_t)slot(k + 1) * SD;
+        double *dpl = dst + (size_t)(k + 1) * plane;
+#pragma unroll
+        for (int m = 0; m < CPT; ++m) {
+            const uint32_t w = rf[m];
+            const int r = (int)(w & 0xFFFFu);
+            bool ok;
+            constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
+            double v;
+            if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0))
+                v = jacobi2d_update_fast<3>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
+            else
+                v = jacobi2d_update_fast<AMa>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
+            if (!ok) v = update2d_slow(sc[r - 1], sc[r + 1], sd[r], su[r]);
+            if (w & kValid) {
+                dpl[r] = v;
+                if (PUSH) {
+                    if (w & kXlo) pi->xlo[(size_t)(k + 1) * pi->xlo_plane] = v;
+                    if (w & kXhi) pi->xhi[(size_t)(k + 1) * pi->xhi_plane] = v;
+                    if (ZP) zp[r] = v;
+                }
+            }
+        }
+    };
+
+    for (int k = T.k0; k < ke; ++k) {
+        fail = !mbar_wait_bounded(ring.bars + slot(k + 1), phase(k + 1), a.spin_ns);
+        if (!fail) {
+            double *z0 = (PUSH && k == 0) ? pi->zlo : nullptr;
+            double *z1 = (PUSH && k == bz - 1) ? pi->zhi : nullptr;
+            if (z0) compute_plane(std::true_type(), k, z0);
+            if (z1) compute_plane(std::true_type(), k, z1);
+            if (!z0 && !z1) compute_plane(std::false_type(), k, nullptr);
+        }
+        if (__syncthreads_or(fail)) {
+            if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
+            drain(k + 1);
+            return false;
+        }
+        if (k - 1 + S <= ke) {
+            if (tid == 0) issue(k - 1 + S);
+            issued_hi = k - 1 + S;
+        }
+    }
+    ring.seq = seq0 + (uint32_t)(ke - kb + 1);
+    return true;
+}
+
+// Stencil dispatch at compile time: ST = OD_STENCIL_3D7 or OD_STENCIL_2D5.
+template <int NT, int CPT, bool PUSH, int AM, int ST>
+__device__ __forceinline__ bool run_any_tile(const KArgs &a, int tile_id, int sp, Ring &ring, PushInfo *pi,
+                                             int step) {
+    if constexpr (ST == OD_STENCIL_2D5) return run_tile_2d<NT, CPT, PUSH, AM>(a, tile_id, sp, ring, pi, step);
+    else return run_tile<NT, CPT, PUSH, AM>(a, tile_id, sp, ring, pi, step);
+}
+
 template <int NT>
 __device__ __forceinline__ Ring ring_setup(const KArgs &a, unsigned char *smem) {
     Ring r;
@@ -352,7 +513,7 @@ __device__ __forceinline__ Ring ring_setup(const KArgs &a, unsigned char *smem) 
 #endif
 constexpr int min_blocks(int nt) { return OD_MIN_THREADS_PER_SM / nt; }
 
-template <int NT, int CPT, bool PUSH, int AM>
+template <int NT, int CPT, bool PUSH, int AM, int ST>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (blockDim.x != NT) {
@@ -360,15 +521,15 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles(const KArgs a) {
         return;
     }
     Ring ring = ring_setup<NT>(a, smem);
-    run_tile<NT, CPT, PUSH, AM>(a, a.tile_begin + (int)blockIdx.x, a.parity, ring,
-                                reinterpret_cast<PushInfo *>(smem + kSmemPush), -1);
+    run_any_tile<NT, CPT, PUSH, AM, ST>(a, a.tile_begin + (int)blockIdx.x, a.parity, ring,
+                                        reinterpret_cast<PushInfo *>(smem + kSmemPush), -1);
 }
 
 // Continuous batching: one fused step of several independent jobs in one
 // launch.  jobs[j] holds job j's tables and source parity; job j owns blocks
 // [first[j], first[j+1]); every block runs one tile of its job.  All jobs
 // share the launch's CTA shape, ring depth and slot size.
-template <int NT, int CPT, int AM>
+template <int NT, int CPT, int AM, int ST>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles_multi(const KArgs *jobs, const int32_t *first,
                                                                    int32_t njobs) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -389,8 +550,8 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles_multi(const KArgs 
         return;
     }
     Ring ring = ring_setup<NT>(a, smem);
-    run_tile<NT, CPT, true, AM>(a, (int)blockIdx.x - first[s_job], a.parity, ring,
-                                reinterpret_cast<PushInfo *>(smem + kSmemPush), -1);
+    run_any_tile<NT, CPT, true, AM, ST>(a, (int)blockIdx.x - first[s_job], a.parity, ring,
+                                        reinterpret_cast<PushInfo *>(smem + kSmemPush), -1);
 }
 
 // Persistent kernel: CTAs take tickets in step-major order; ticket
@@ -399,7 +560,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles_multi(const KArgs 
 // reads (and itself) has finished step r-1.  A waited-on ticket is always
 // smaller than the waiter's, and tickets are taken in order by running CTAs,
 // so the wait graph has no cycle and needs no co-residency guarantee.
-template <int NT, int CPT, int AM>
+template <int NT, int CPT, int AM, int ST>
 __global__ void __launch_bounds__(NT, min_blocks(NT)) k_persistent(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int32_t s_ticket;
@@ -443,8 +604,8 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_persistent(const KArgs a
             fence_proxy_async();
         }
         if (!__syncthreads_and(ok)) break;
-        if (!run_tile<NT, CPT, true, AM>(a, tile, step & 1, ring, reinterpret_cast<PushInfo *>(smem + kSmemPush),
-                                         step))
+        if (!run_any_tile<NT, CPT, true, AM, ST>(a, tile, step & 1, ring,
+                                                 reinterpret_cast<PushInfo *>(smem + kSmemPush), step))
             break;
         if (threadIdx.x == 0 && (int64_t)tile != a.stall_tile) {
             __threadfence();

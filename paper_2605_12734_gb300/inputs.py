@@ -18,6 +18,12 @@ Workloads (3D 7-point FP64 Jacobi, the paper's Jacobi proxy of Sec. V in 3D):
                    in [64, 384], blocks per job in {8, 27, 64, 216}, iterations
                    uniform in [10, 200].
 * ``CEILING_1024`` 1024^3 in 4096 blocks of 64^3, 50 iterations.
+
+2D 5-point FP64 Jacobi (the paper's Jacobi2D application, Sec. V):
+
+* ``JACOBI2D_32768`` the paper's per-GPU base domain 32768 x 32768, 100
+                   iterations, every cell U[0,1), split into px x py blocks
+                   with px*py = ODF (px = 2^ceil(log2(ODF)/2), py = ODF/px).
 """
 from __future__ import annotations
 
@@ -66,6 +72,7 @@ class Workload:
     init_mode: int
     split: tuple[int, int, int] | None = None           # uniform px, py, pz
     cuts: tuple[list[int], list[int], list[int]] | None = None  # explicit edges
+    stencil: str = "3d7"                                 # "3d7" or "2d5" (nz = 1)
 
     @property
     def cells(self) -> int:
@@ -108,6 +115,17 @@ def uneven_768(iters: int = 200) -> Workload:
 def ceiling_1024(iters: int = 50) -> Workload:
     return Workload("jacobi3d-1024^3-odf4096", 1024, 1024, 1024, iters, 7, INIT_UNIFORM,
                     split=(16, 16, 16))
+
+
+def jacobi2d_32768(odf: int, iters: int = 100, edge: int = 32768) -> Workload:
+    """The paper's Jacobi2D base domain on one GPU, in ODF blocks."""
+    if odf < 1 or odf & (odf - 1):
+        raise ValueError("ODF must be a power of two")
+    lg = odf.bit_length() - 1
+    px = 1 << ((lg + 1) // 2)
+    py = odf // px
+    return Workload(f"jacobi2d-{edge}^2-odf{odf}", edge, edge, 1, iters, 9, INIT_UNIFORM,
+                    split=(px, py, 1), stencil="2d5")
 
 
 @dataclass(frozen=True)

@@ -147,3 +147,82 @@ def test_tile_counts(od, kw):
         total += -(-by // cap) * -(-bz // min(tz, bz))
     assert info["ntiles"] == total
     assert info["smem_bytes"] <= 232448
+
+
+# ----------------------------------------------------------------- 2D stencil
+
+@pytest.mark.parametrize("nx,ny,px,py", [(1000, 700, 3, 4), (64, 64, 1, 1), (7, 5, 7, 5), (32768, 32768, 64, 64)])
+def test_plan_2d_counts(od, nx, ny, px, py):
+    info = od.plan_2d(nx, ny, split=(px, py))
+    assert info["nchares"] == px * py and info["cells"] == nx * ny
+    # internal faces: each of the px-1 x-cuts feeds ny cells both ways, each
+    # of the py-1 y-cuts nx cells; the shell is 2*(nx+ny) cells
+    assert info["face_cells_internal"] == 2 * (px - 1) * ny + 2 * (py - 1) * nx
+    assert info["face_cells_dirichlet"] == 2 * (nx + ny)
+
+
+def test_decompose_2d_matches_oracle_split(od):
+    nx, ny, px, py = 1001, 333, 5, 7
+    box, nbr = od.decompose_2d(nx, ny, split=(px, py))
+    ex, ey = list(oracle.split(nx, px)), list(oracle.split(ny, py))
+    assert box.shape == (px * py, 4)
+    for c in range(px * py):
+        cx, cy = c % px, c // px
+        assert list(box[c]) == [ex[cx], ex[cx + 1] - ex[cx], ey[cy], ey[cy + 1] - ey[cy]]
+        assert list(nbr[c]) == [c - 1 if cx > 0 else -1, c + 1 if cx < px - 1 else -1,
+                                c - px if cy > 0 else -1, c + px if cy < py - 1 else -1]
+
+
+def test_decompose_2d_uneven_cuts(od):
+    cx, cy = [0, 3, 50, 51, 100], [0, 1, 2, 40]
+    box, nbr = od.decompose_2d(100, 40, cuts=(cx, cy))
+    assert len(box) == 12
+    assert int(np.sum(box[:, 1] * box[:, 3])) == 4000
+    assert list(box[5]) == [3, 47, 1, 1]
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dims=(8, 8, 2)),                                   # nz must be 1
+    dict(dims=(8, 8, 1), split=(1, 1, 2)),                  # no z blocks
+    dict(dims=(8, 8, 1), split=(9, 1, 1)),                  # more blocks than cells
+    dict(dims=(8, 8, 1), stencil=7),                        # unknown stencil
+])
+def test_invalid_2d_configs_rejected(od, bad):
+    dims = bad.pop("dims")
+    bad.setdefault("stencil", "2d5")
+    with pytest.raises(od.ODError) as ei:
+        od.plan(*dims, **bad)
+    assert ei.value.status == od._native.OD_EINVAL
+
+
+@pytest.mark.parametrize("kw", [
+    dict(dims=(1000, 700), split=(3, 4)),
+    dict(dims=(5000, 64), split=(1, 1)),                    # rows wider than a CTA: several segments
+    dict(dims=(301, 77), split=(2, 3), tile_y=64, tile_z=5),
+    dict(dims=(9, 9), split=(9, 9)),                        # 1 x 1 chares
+])
+def test_tile_counts_2d(od, kw):
+    dims = kw.pop("dims")
+    info = od.plan_2d(*dims, **kw)
+    box, _ = od.decompose_2d(*dims, **kw)
+    cap = info["threads"] * info["cells_per_thread"]
+    if kw.get("tile_y"):
+        cap = min(cap, kw["tile_y"])
+    tz = kw.get("tile_z", 0) or 32
+    total = 0
+    for (x0, bx, y0, by) in box:
+        nseg = -(-bx // cap)
+        w = -(-bx // nseg)
+        w += w & 1                       # even segment starts
+        total += -(-bx // w) * -(-by // min(tz, by))
+        assert w <= cap + 1
+    assert info["ntiles"] == total
+    assert info["smem_bytes"] <= 232448
+
+
+def test_auto_cta_shape_2d(od):
+    def shape(*dims, **kw):
+        i = od.plan_2d(*dims, **kw)
+        return i["threads"], i["cells_per_thread"]
+    assert shape(32768, 32768, split=(64, 64)) == (128, 4)
+    assert shape(32768, 32768, split=(128, 128)) == (128, 2)

@@ -183,3 +183,73 @@ def test_update_every_mode_matches_ieee(od, mode):
         want = (((((x[:, 0] + x[:, 1]) + x[:, 2]) + x[:, 3]) + x[:, 4]) + x[:, 5]) / 6.0
     got = od.arith_host(10 + mode, np.ascontiguousarray(x).ravel())[: len(x)]
     same(got, want)
+
+
+def _update2d_inputs(rng, n):
+    """Four operands per cell (the 2D update): the 3D generator's regimes,
+    plus the tie / sticky patterns at each of the three chain positions and
+    sums whose quarter is subnormal (the division by 4 is then not exact)."""
+    x = np.ascontiguousarray(_update_inputs(rng, n)[:, :4])
+    base = 7 * (n // 8)
+    for t in range(1, 4):
+        parts = [0.5 ** (i + 1) for i in range(t - 1)]
+        parts.append(1.0 - sum(parts))
+        rows = slice(base + (t - 1) * 200, base + t * 200)
+        x[rows] = 0.0
+        x[rows, :t] = parts
+        x[rows, t] = 2.0 ** -53 * (1 + 2.0 ** -int(rng.integers(20, 52)))
+    # sums with biased exponent 0..5 (subnormal up to 2^-1018): one normal
+    # operand of exponent 1..4, subnormal or zero partners, either sign; the
+    # quarter is subnormal (and rounds) below exponent 3
+    tail = slice(n - 2000, n)
+    e = rng.integers(1, 5, 2000, dtype=np.uint64)
+    x[tail] = 0.0
+    x[tail, 0] = from_bits((e << np.uint64(52)) | rng.integers(0, 1 << 52, 2000, dtype=np.uint64))
+    sub = from_bits(rng.integers(0, 1 << 52, (2000, 3), dtype=np.uint64))
+    x[tail, 1:] = sub * rng.choice([-1.0, 0.0, 1.0], (2000, 3))
+    # four normal operands of exponent 1..6 and mixed signs: cancellation
+    # leaves sums of every small exponent inside the window chain's domain
+    tail = slice(n - 4000, n - 2000)
+    e = rng.integers(1, 7, (2000, 4), dtype=np.uint64)
+    x[tail] = from_bits((e << np.uint64(52)) | rng.integers(0, 1 << 52, (2000, 4), dtype=np.uint64))
+    x[tail] *= np.array([1.0, -1.0, 1.0, -1.0])
+    # deep cancellation inside the chain's exponent domain (every operand of
+    # biased exponent 4..8): v - v' leaves a few ulps, w - w cancels exactly,
+    # so the sum is subnormal or barely normal
+    tail = slice(n - 6000, n - 4000)
+    e = rng.integers(4, 9, 2000, dtype=np.uint64)
+    mv = rng.integers(1 << 20, 1 << 52, 2000, dtype=np.uint64)
+    v = from_bits((e << np.uint64(52)) | mv)
+    v2 = from_bits((e << np.uint64(52)) | (mv - rng.integers(0, 1 << 19, 2000, dtype=np.uint64)))
+    w = from_bits((rng.integers(4, 9, 2000, dtype=np.uint64) << np.uint64(52)) | rng.integers(0, 1 << 52, 2000, dtype=np.uint64))
+    x[tail] = np.stack([v, -v2, w, -w], axis=1)
+    # a positive in-domain window sum cancelled by the IEEE adds after it
+    # (modes with fewer than three window adds): tiny or subnormal sums
+    tail = slice(n - 8000, n - 6000)
+    a = from_bits((rng.integers(4, 9, 2000, dtype=np.uint64) << np.uint64(52))
+                  | rng.integers(0, 1 << 52, 2000, dtype=np.uint64))
+    b = from_bits((rng.integers(4, 9, 2000, dtype=np.uint64) << np.uint64(52))
+                  | rng.integers(0, 1 << 52, 2000, dtype=np.uint64))
+    ab = a + b
+    c = -from_bits(ab.view(np.uint64) - (rng.integers(0, 1 << 52, 2000, dtype=np.uint64) >> rng.integers(0, 52, 2000, dtype=np.uint64)))
+    d = from_bits(rng.integers(0, 1 << 52, 2000, dtype=np.uint64)) * rng.choice([-1.0, 0.0, 1.0], 2000)
+    x[tail] = np.stack([a, b, c, d], axis=1)
+    # the same with the cancelling operand last (after a third window add)
+    h = slice(n - 7000, n - 6000)
+    w3 = from_bits((rng.integers(4, 9, 1000, dtype=np.uint64) << np.uint64(52))
+                   | rng.integers(0, 1 << 52, 1000, dtype=np.uint64))
+    abw = (x[h, 0] + x[h, 1]) + w3
+    x[h, 2] = w3
+    x[h, 3] = -from_bits(abw.view(np.uint64) - (rng.integers(0, 1 << 52, 1000, dtype=np.uint64)
+                                                >> rng.integers(0, 52, 1000, dtype=np.uint64)))
+    return x
+
+
+@pytest.mark.parametrize("mode", range(5))
+def test_update2d_every_mode_matches_ieee(od, mode):
+    rng = np.random.default_rng(200 + mode)
+    x = _update2d_inputs(rng, 400_000)
+    with np.errstate(all="ignore"):
+        want = (((x[:, 0] + x[:, 1]) + x[:, 2]) + x[:, 3]) / 4.0
+    got = od.arith_host(20 + mode, np.ascontiguousarray(x).ravel())
+    same(got, want)
