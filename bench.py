@@ -36,10 +36,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="odf", choices=["odf", "uneven", "ceiling", "serve", "jacobi2d"],
+    ap.add_argument("--workload", default="odf", choices=["odf", "uneven", "ceiling", "serve", "jacobi2d", "launch"],
                     help="odf: 512^3 at --odf (default); uneven: 768x512x512 in ~300 uneven chares; "
                          "ceiling: 1024^3 in 4096 chares; serve: Poisson stream of jobs into the server; "
-                         "jacobi2d: the 2D 5-point Jacobi on 32768^2 in --odf chares (a power of two)")
+                         "jacobi2d: the 2D 5-point Jacobi on 32768^2 in --odf chares (a power of two); "
+                         "launch: the kernel-launch overhead microbenchmarks")
     ap.add_argument("--jobs", type=int, default=300, help="serve: number of jobs")
     ap.add_argument("--rate", type=float, default=60.0, help="serve: Poisson arrival rate (jobs/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
@@ -310,6 +311,8 @@ def run_ours(args):
     dev = local
     if args.workload == "serve":
         return run_serve(args, pkg, torch, rank, world, dev)
+    if args.workload == "launch":
+        return run_launch(args, pkg, rank, dev)
     edge, odf = args.edge, args.odf
     p = round(odf ** (1 / 3))
     if p ** 3 != odf and args.workload != "jacobi2d":
@@ -502,6 +505,38 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_launch(args, pkg, rank, dev):
+    """The paper's launch-overhead measurements (Sec. III) on this GPU: the
+    round trip of one empty kernel, a fixed amount of work split over 1..1024
+    pre-enqueued kernels released together, and the kernel rate of 1-4 host
+    threads driving 1-8 chares each."""
+    if rank != 0:
+        return 0
+    clocks = ClockSampler(dev)
+    clocks.start()
+    lat = {w: pkg.bench_launch_latency(w, reps=5000, device=dev) for w in ("sync", "event", "callback")}
+    work = 4096
+    release = []
+    for total in (256 * 1024, 4 * 1024 * 1024):
+        for nk in (1, 2, 4, 8, 16, 32, 64, 256, 1024):
+            t = sorted(pkg.bench_release(total, nk, work, device=dev) for _ in range(5))
+            release.append({"total_threads": total, "kernels": nk, "us_median": t[2], "us_min": t[0]})
+    rate = []
+    for ht in (1, 2, 4):
+        for ch in (1, 2, 4, 8):
+            rate.append({"host_threads": ht, "chares_per_thread": ch,
+                         "kernels_per_s": pkg.bench_launch_rate(ht, ch, kernels=max(200, 4000 // (ht * ch)),
+                                                                 device=dev)})
+    clk = clocks.stop()
+    line = {"metric": "kernel launch round trip (empty kernel, cudaStreamSynchronize)", "value": lat["sync"],
+            "unit": "us", "n_gpus": 1, "higher_is_better": False, "dtype": "none", "data": "synthetic",
+            "config": {"workload": "launch-overhead-microbenchmarks", "release_work_lcg_steps": work,
+                       "rate_kernel": "empty, one block of 32 threads per SM"},
+            "latency_us": lat, "release": release, "launch_rate": rate, "clocks": clk}
+    print(json.dumps(line), flush=True)
     return 0
 
 

@@ -256,6 +256,44 @@ OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
 OD_API od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n);
 OD_API od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n);
 
+/* ------------------------------------------------------------------ launch overhead
+ *
+ * Microbenchmarks of what a kernel launch costs an overdecomposed application
+ * (the paper's Sec. III measurements), the context for the per-chare path's
+ * slowdown with ODF.  Each call runs on `device`, creates and frees its own
+ * streams, events and buffers, returns after the GPU has finished, and bounds
+ * every host wait (10 s per wait: OD_ETIMEOUT).  Arguments are checked before
+ * any CUDA call (OD_EINVAL). */
+
+/* One kernel at a time: an empty one-block kernel is launched and waited for,
+ * `reps` times (1..1e6) after 10 untimed ones.  wait: 0 = cudaStreamSynchronize,
+ * 1 = polling an event (cudaEventQuery), 2 = a host function enqueued behind
+ * the kernel (cudaLaunchHostFunc) sets a flag the caller polls -- the
+ * callback style of a task runtime.  *us = mean wall-clock microseconds per
+ * launch-and-wait round trip. */
+OD_API od_status od_bench_launch_latency(int32_t device, int32_t wait, int32_t reps, double *us);
+
+/* Pre-enqueued release: `total_threads` (1..2^30) threads of a fixed-work
+ * kernel are split into `nkernels` (1..1024) contiguous kernels, one
+ * non-blocking stream each; every stream first waits on one host-mapped flag
+ * (cuStreamWaitValue32, resolved from the driver at run time), and the host
+ * releases all of them at once.  Thread g iterates the 32-bit LCG
+ * x <- 1664525 x + 1013904223 `work` times (0..1e6, total_threads*work <= 2^40)
+ * from x = g and stores x in out[g]; `out` is a device buffer of
+ * total_threads uint32 owned by the caller, or NULL for a scratch buffer.
+ * *us = time from the first stream passing the flag until the last kernel
+ * finished (device events). */
+OD_API od_status od_bench_release(int32_t device, int64_t total_threads, int32_t nkernels, int32_t work,
+                                  uint32_t *out, double *us);
+
+/* Launch rate: `host_threads` (1..64) host threads each drive `chares`
+ * (1..64) chares; a chare owns a stream and fires an empty kernel of one
+ * block per SM, then the next once its thread has seen (by polling an
+ * event) that the previous one completed, `kernels` times (at most 1e7
+ * kernels in all).  *per_s = kernels completed per second of wall time. */
+OD_API od_status od_bench_launch_rate(int32_t device, int32_t host_threads, int32_t chares, int32_t kernels,
+                                      double *per_s);
+
 /* ------------------------------------------------------------------ serving
  *
  * A server admits independent solves as they arrive, keeps their state

@@ -24,7 +24,8 @@ from ._native import ODError, PATHS, check, lib, od_config, od_plan_info, od_sta
 STENCILS = {"3d7": 0, "2d5": 1}
 
 __all__ = ["Jacobi3D", "Jacobi2D", "Server", "STENCILS", "ODError", "PATHS", "make_config", "plan", "decompose", "lib", "arith_host",
-           "arith_device", "jacobi_noalloc", "plan_2d", "decompose_2d"]
+           "arith_device", "jacobi_noalloc", "plan_2d", "decompose_2d", "bench_launch_latency", "bench_release",
+           "bench_launch_rate"]
 
 
 def _cuts_array(cuts):
@@ -121,6 +122,35 @@ def jacobi_noalloc(u_in, u_out, nx: int, ny: int, nz: int, iters: int, stream: i
     float64) without any device allocation; see od_jacobi_noalloc in od.h."""
     check(lib().od_jacobi_noalloc(u_in.data_ptr(), u_out.data_ptr(), int(nx), int(ny), int(nz), int(iters),
                                   stream), "od_jacobi_noalloc")
+
+
+def bench_launch_latency(wait: str | int = "sync", reps: int = 2000, device: int = 0) -> float:
+    """Mean microseconds per launch-and-wait round trip of an empty kernel
+    (wait: "sync" | "event" | "callback"); see od_bench_launch_latency."""
+    w = {"sync": 0, "event": 1, "callback": 2}[wait] if isinstance(wait, str) else int(wait)
+    us = ctypes.c_double()
+    check(lib().od_bench_launch_latency(int(device), w, int(reps), ctypes.byref(us)), "od_bench_launch_latency")
+    return us.value
+
+
+def bench_release(total_threads: int, nkernels: int, work: int = 256, out=None, device: int = 0) -> float:
+    """Microseconds from the release of `nkernels` pre-enqueued kernels (one
+    stream each, held by cuStreamWaitValue32 on a host flag) to the end of the
+    last; out: optional CUDA uint32/int32 tensor of total_threads results."""
+    us = ctypes.c_double()
+    ptr = None if out is None else out.data_ptr()
+    check(lib().od_bench_release(int(device), int(total_threads), int(nkernels), int(work), ptr, ctypes.byref(us)),
+          "od_bench_release")
+    return us.value
+
+
+def bench_launch_rate(host_threads: int, chares: int, kernels: int = 2000, device: int = 0) -> float:
+    """Kernels per second fired by `host_threads` threads driving `chares`
+    chares each (next kernel once the previous one completed)."""
+    r = ctypes.c_double()
+    check(lib().od_bench_launch_rate(int(device), int(host_threads), int(chares), int(kernels), ctypes.byref(r)),
+          "od_bench_launch_rate")
+    return r.value
 
 
 class Jacobi3D:

@@ -113,6 +113,9 @@ SIGNATURES = {
     "od_server_stats": (_i32, [_vp, ctypes.POINTER(od_server_stats_t)]),
     "od_server_destroy": (_i32, [_vp]),
     "od_jacobi_noalloc": (_i32, [_vp, _vp, _i64, _i64, _i64, _i32, _vp]),
+    "od_bench_launch_latency": (_i32, [_i32, _i32, _i32, ctypes.POINTER(ctypes.c_double)]),
+    "od_bench_release": (_i32, [_i32, _i64, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "od_bench_launch_rate": (_i32, [_i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_double)]),
     "od_destroy": (_i32, [_vp]),
     "od_last_error": (ctypes.c_char_p, []),
     "od_version": (ctypes.c_char_p, []),

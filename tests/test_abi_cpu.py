@@ -226,3 +226,20 @@ def test_auto_cta_shape_2d(od):
         return i["threads"], i["cells_per_thread"]
     assert shape(32768, 32768, split=(64, 64)) == (128, 4)
     assert shape(32768, 32768, split=(128, 128)) == (128, 2)
+
+
+# ----------------------------------------------------------------- launch benchmarks
+
+@pytest.mark.parametrize("call", [
+    lambda L, d: L.od_bench_launch_latency(0, 3, 10, ctypes.byref(d)),          # no such wait mode
+    lambda L, d: L.od_bench_launch_latency(0, 0, 0, ctypes.byref(d)),           # no repetitions
+    lambda L, d: L.od_bench_launch_latency(0, 0, 10, None),                     # no output
+    lambda L, d: L.od_bench_release(0, 0, 1, 1, None, ctypes.byref(d)),         # no threads
+    lambda L, d: L.od_bench_release(0, 1 << 20, 0, 1, None, ctypes.byref(d)),   # no kernels
+    lambda L, d: L.od_bench_release(0, 1 << 30, 8, 1 << 20, None, ctypes.byref(d)),  # too much work
+    lambda L, d: L.od_bench_launch_rate(0, 0, 1, 10, ctypes.byref(d)),          # no host threads
+    lambda L, d: L.od_bench_launch_rate(0, 64, 64, 10000, ctypes.byref(d)),     # > 1e7 kernels
+])
+def test_launch_benchmarks_check_arguments_first(od, call):
+    d = ctypes.c_double()
+    assert call(od.lib(), d) == od._native.OD_EINVAL
