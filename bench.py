@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
     ap.add_argument("--tile-z", type=int, default=0)
+    ap.add_argument("--order", type=int, default=0,
+                    help="persistent task order (od_config.order: 1 reverse odd steps, 2 Morton chares)")
     ap.add_argument("--arith", type=int, default=-1,
                     help="where the update's operations run (od_config.arith; -1 = library default)")
     return ap.parse_args()
@@ -319,7 +321,7 @@ def run_ours(args):
         raise SystemExit("--odf must be a cube")
     stream = torch.cuda.Stream(device=dev)
     tune_kw = dict(threads=args.threads, cells_per_thread=args.cpt, stages=args.stages,
-                   tile_y=args.tile_y, tile_z=args.tile_z, arith=args.arith,
+                   tile_y=args.tile_y, tile_z=args.tile_z, arith=args.arith, order=args.order,
                    autotune=not args.no_tune and not (args.threads or args.cpt or args.stages or args.arith >= 0),
                    device=dev)
     from paper_2605_12734_gb300 import inputs

@@ -140,8 +140,9 @@ typedef struct od_config {
                                     integer pipes; 7 / 8: modes 2 and 3 mixed
                                     cell by cell (half / a quarter of the cells
                                     in mode 3); -1 = library default (7) */
-    int32_t order;               /* persistent path task order: 0 linear every
-                                    step, 1 reversed on odd steps */
+    int32_t order;               /* persistent path task order, bits: 1 = reversed
+                                    on odd steps, 2 = chares in Morton (Z) order
+                                    instead of x-fastest; 0..3 */
     int32_t stream_pool;         /* per-chare path: streams (0 = min(nchares,32)) */
     int32_t device;              /* CUDA device ordinal */
     void *stream;                /* cudaStream_t to enqueue on; NULL = the

@@ -74,7 +74,7 @@ KArgs base_args_impl(const od_ctx *c) {
     a.dep_idx = c->d_dep_idx;
     a.order = c->d_order;
     a.ntiles = (int32_t)c->plan.tiles.size();
-    a.order_mode = c->cfg.order;
+    a.order_mode = c->cfg.order & 1;
     a.stages = c->plan.stages;
     a.stage_doubles = c->plan.stage_doubles;
     a.stall_tile = c->stall_tile;

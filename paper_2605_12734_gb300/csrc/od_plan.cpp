@@ -121,6 +121,10 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         *err = "unknown path";
         return OD_EINVAL;
     }
+    if (cfg->order < 0 || cfg->order > 3) {
+        *err = "order must be 0..3 (bit 0: reverse on odd steps, bit 1: Morton order of the chares)";
+        return OD_EINVAL;
+    }
     p.threads = cfg->threads ? cfg->threads : 128;
     p.cpt = cfg->cells_per_thread ? cfg->cells_per_thread : 4;
     const bool auto_shape = cfg->threads == 0 && cfg->cells_per_thread == 0;
@@ -354,6 +358,28 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
     }
     p.order.resize(p.tiles.size());
     for (size_t ti = 0; ti < p.tiles.size(); ++ti) p.order[ti] = (int32_t)ti;
+    if (cfg->order & 2) {
+        // Z-order (Morton) over the chare grid: chares that are close in all
+        // three axes run close in time, so a face written by one is more
+        // likely still in L2 when its neighbour reads it; a chare's own tiles
+        // keep their order
+        auto spread = [](uint64_t v) {  // bits of a 21-bit value to every third bit
+            v &= 0x1fffffull;
+            v = (v | v << 32) & 0x1f00000000ffffull;
+            v = (v | v << 16) & 0x1f0000ff0000ffull;
+            v = (v | v << 8) & 0x100f00f00f00f00full;
+            v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+            v = (v | v << 2) & 0x1249249249249249ull;
+            return v;
+        };
+        std::vector<uint64_t> key(p.tiles.size());
+        for (size_t ti = 0; ti < p.tiles.size(); ++ti) {
+            const HostChare &h = p.ch[(size_t)p.tiles[ti].c];
+            key[ti] = spread((uint64_t)h.cx) | spread((uint64_t)h.cy) << 1 | spread((uint64_t)h.cz) << 2;
+        }
+        std::stable_sort(p.order.begin(), p.order.end(),
+                         [&](int32_t a, int32_t b) { return key[(size_t)a] < key[(size_t)b]; });
+    }
 
     // arena layout
     size_t at = 0;

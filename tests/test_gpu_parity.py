@@ -129,12 +129,15 @@ def test_launch_shapes(od, path, shape):
         assert_bitexact(s.read(), want, f"{path} {shape}")
 
 
-def test_persistent_reversed_order(od):
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_persistent_task_orders(od, order):
+    # 1: reversed on odd steps, 2: Morton order of the chares, 3: both
     nx, ny, nz = 64, 64, 64
     want = oracle.solve(nx, ny, nz, 6, 1, 9)
-    with od.Jacobi3D(nx, ny, nz, split=(4, 4, 4), seed=6, init_mode=1, path="persistent", order=1) as s:
+    with od.Jacobi3D(nx, ny, nz, cuts=([0, 10, 30, 33, 64], [0, 20, 40, 64], [0, 31, 64]), seed=6, init_mode=1,
+                     path="persistent", order=order) as s:
         s.step(9)
-        assert_bitexact(s.read(), want, "order=1")
+        assert_bitexact(s.read(), want, f"order={order}")
 
 
 def test_stalled_tile_times_out_without_hanging(od):
