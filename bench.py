@@ -162,7 +162,7 @@ def profiled_traffic(args, plan):
 
 
 # bumped whenever the tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 8
+KERNEL_REV = 9
 
 
 def combine_ranks(ms: float, updates: float, world: int, device: str):

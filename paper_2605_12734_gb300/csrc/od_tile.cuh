@@ -178,8 +178,7 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     // the slot's use count & 1.
     auto slot = [&](int p) -> uint32_t { return (seq0 + (uint32_t)(p - kb)) % (uint32_t)S; };
     auto phase = [&](int p) -> uint32_t { return ((seq0 + (uint32_t)(p - kb)) / (uint32_t)S) & 1u; };
-    auto issue = [&](int p) {
-        const uint32_t s = slot(p);
+    auto issue = [&](int p, uint32_t s) {  // s = slot(p)
         uint64_t *bar = ring.bars + s;
         mbar_expect_tx(bar, run_bytes);
         bulk_g2s(ring.base + (size_t)s * SD, src + (size_t)(p + 1) * plane, run_bytes, bar);
@@ -194,7 +193,7 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
 
     if (tid == 0) {
         const int last = min(ke, kb + S - 1);
-        for (int p = kb; p <= last; ++p) issue(p);
+        for (int p = kb; p <= last; ++p) issue(p, slot(p));
         if (PUSH) {
             PushInfo q;
             q.xlo = q.xhi = q.ylo = q.yhi = q.zlo = q.zhi = nullptr;
@@ -268,11 +267,9 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
 
     // One plane: ZP = the plane is a chare z-face with a neighbour there, so
     // every cell is also stored into that neighbour's ghost plane (zp).
-    auto compute_plane = [&](auto zp_tag, int k, double *zp) {
+    auto compute_plane = [&](auto zp_tag, int k, double *zp, const double *sd, const double *sc,
+                             const double *su) {
         constexpr bool ZP = decltype(zp_tag)::value;
-        const double *sd = ring.base + (size_t)slot(k - 1) * SD;
-        const double *sc = ring.base + (size_t)slot(k) * SD;
-        const double *su = ring.base + (size_t)slot(k + 1) * SD;
         double *dpl = dst + (size_t)(k + 1) * plane;
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
@@ -306,14 +303,20 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
         }
     };
 
+    // ring slots of planes k-1, k, k+1 and the phase of k+1, advanced by one
+    // position per plane (no division by the run-time ring depth in the loop)
+    uint32_t sl_m1 = slot(kb), sl_0 = slot(kb + 1), sl_p1 = slot(kb + 2), ph_p1 = phase(kb + 2);
     for (int k = T.k0; k < ke; ++k) {
-        fail = !mbar_wait_bounded(ring.bars + slot(k + 1), phase(k + 1), a.spin_ns);
+        fail = !mbar_wait_bounded(ring.bars + sl_p1, ph_p1, a.spin_ns);
         if (!fail) {
+            const double *sd = ring.base + (size_t)sl_m1 * SD;
+            const double *sc = ring.base + (size_t)sl_0 * SD;
+            const double *su = ring.base + (size_t)sl_p1 * SD;
             double *z0 = (PUSH && k == 0) ? pi->zlo : nullptr;
             double *z1 = (PUSH && k == bz - 1) ? pi->zhi : nullptr;
-            if (z0) compute_plane(std::true_type(), k, z0);
-            if (z1) compute_plane(std::true_type(), k, z1);  // bz == 1 with both: the plane twice
-            if (!z0 && !z1) compute_plane(std::false_type(), k, nullptr);
+            if (z0) compute_plane(std::true_type(), k, z0, sd, sc, su);
+            if (z1) compute_plane(std::true_type(), k, z1, sd, sc, su);  // bz == 1 with both: the plane twice
+            if (!z0 && !z1) compute_plane(std::false_type(), k, nullptr, sd, sc, su);
         }
         if (__syncthreads_or(fail)) {
             if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
@@ -322,8 +325,14 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
         }
         // plane k-1 is no longer needed: refill its slot
         if (k - 1 + S <= ke) {
-            if (tid == 0) issue(k - 1 + S);
+            if (tid == 0) issue(k - 1 + S, sl_m1);
             issued_hi = k - 1 + S;
+        }
+        sl_m1 = sl_0;
+        sl_0 = sl_p1;
+        if (++sl_p1 == (uint32_t)S) {
+            sl_p1 = 0;
+            ph_p1 ^= 1u;
         }
     }
     ring.seq = seq0 + (uint32_t)(ke - kb + 1);
@@ -363,8 +372,7 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
 
     auto slot = [&](int p) -> uint32_t { return (seq0 + (uint32_t)(p - kb)) % (uint32_t)S; };
     auto phase = [&](int p) -> uint32_t { return ((seq0 + (uint32_t)(p - kb)) / (uint32_t)S) & 1u; };
-    auto issue = [&](int p) {
-        const uint32_t s = slot(p);
+    auto issue = [&](int p, uint32_t s) {  // s = slot(p)
         uint64_t *bar = ring.bars + s;
         mbar_expect_tx(bar, run_bytes);
         bulk_g2s(ring.base + (size_t)s * SD, src + (size_t)(p + 1) * plane, run_bytes, bar);
@@ -378,7 +386,7 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
 
     if (tid == 0) {
         const int last = min(ke, kb + S - 1);
-        for (int p = kb; p <= last; ++p) issue(p);
+        for (int p = kb; p <= last; ++p) issue(p, slot(p));
         if (PUSH) {
             PushInfo q;
             q.xlo = q.xhi = q.ylo = q.yhi = q.zlo = q.zhi = nullptr;
@@ -430,11 +438,9 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
         return false;
     }
 
-    auto compute_plane = [&](auto zp_tag, int k, double *zp) {
+    auto compute_plane = [&](auto zp_tag, int k, double *zp, const double *sd, const double *sc,
+                             const double *su) {
         constexpr bool ZP = decltype(zp_tag)::value;
-        const double *sd = ring.base + (size_t)slot(k - 1) * SD;
-        const double *sc = ring.base + (size_t)slot(k) * SD;
-        const double *su = ring.base + (size_t)slot(k + 1) * SD;
         double *dpl = dst + (size_t)(k + 1) * plane;
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
@@ -459,14 +465,18 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
         }
     };
 
+    uint32_t sl_m1 = slot(kb), sl_0 = slot(kb + 1), sl_p1 = slot(kb + 2), ph_p1 = phase(kb + 2);
     for (int k = T.k0; k < ke; ++k) {
-        fail = !mbar_wait_bounded(ring.bars + slot(k + 1), phase(k + 1), a.spin_ns);
+        fail = !mbar_wait_bounded(ring.bars + sl_p1, ph_p1, a.spin_ns);
         if (!fail) {
+            const double *sd = ring.base + (size_t)sl_m1 * SD;
+            const double *sc = ring.base + (size_t)sl_0 * SD;
+            const double *su = ring.base + (size_t)sl_p1 * SD;
             double *z0 = (PUSH && k == 0) ? pi->zlo : nullptr;
             double *z1 = (PUSH && k == bz - 1) ? pi->zhi : nullptr;
-            if (z0) compute_plane(std::true_type(), k, z0);
-            if (z1) compute_plane(std::true_type(), k, z1);
-            if (!z0 && !z1) compute_plane(std::false_type(), k, nullptr);
+            if (z0) compute_plane(std::true_type(), k, z0, sd, sc, su);
+            if (z1) compute_plane(std::true_type(), k, z1, sd, sc, su);
+            if (!z0 && !z1) compute_plane(std::false_type(), k, nullptr, sd, sc, su);
         }
         if (__syncthreads_or(fail)) {
             if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
@@ -474,8 +484,14 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
             return false;
         }
         if (k - 1 + S <= ke) {
-            if (tid == 0) issue(k - 1 + S);
+            if (tid == 0) issue(k - 1 + S, sl_m1);
             issued_hi = k - 1 + S;
+        }
+        sl_m1 = sl_0;
+        sl_0 = sl_p1;
+        if (++sl_p1 == (uint32_t)S) {
+            sl_p1 = 0;
+            ph_p1 ^= 1u;
         }
     }
     ring.seq = seq0 + (uint32_t)(ke - kb + 1);
