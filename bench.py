@@ -150,7 +150,13 @@ def profiled_traffic(args, plan):
     """DRAM bytes per step of the tile kernel from the committed ncu summary
     (profiles/traffic_*.json) when it was taken on this exact kernel build and
     workload; None otherwise."""
-    p = os.path.join(ROOT, "profiles", f"traffic_{args.path}_{args.edge}cubed_odf{args.odf}.json")
+    if args.workload == "jacobi2d":
+        name = f"traffic_{args.path}2d_{args.edge2d}sq_odf{args.odf}.json"
+    elif args.workload == "odf":
+        name = f"traffic_{args.path}_{args.edge}cubed_odf{args.odf}.json"
+    else:
+        return None
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -190,50 +196,56 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def _time_oracle(sweep, cells: int, target_s: float):
+    """Rate of an oracle sweep function sweep(iters): grow the iteration
+    count until one call lasts about target_s, then take the rate from the
+    difference of the last two calls (their one-off copy and page faults
+    cancel).  Returns (updates/s, iterations of the last call, its seconds)."""
+    def timed(n):
+        t0 = time.perf_counter()
+        sweep(n)
+        return time.perf_counter() - t0
+    n0, t0 = 1, timed(1)
+    n1 = max(2, int(target_s / 2 / max(t0, 1e-3)))
+    t1 = timed(n1)
+    if t1 < target_s / 4:  # the first call was dominated by its one-off cost
+        n1 = max(n1 + 1, int(n1 * target_s / 2 / t1))
+        t1 = timed(n1)
+    n2 = max(n1 + 1, int(n1 * target_s / t1))
+    t2 = timed(n2)
+    rate = (n2 - n1) * cells / max(t2 - t1, 1e-9)
+    return rate, n2, t2
+
+
 def oracle_cpu_baseline(edge: int, target_s: float = 10.0):
     """Time the CPU oracle's monolithic sweep (its OpenMP z-plane split) on a
-    bounded sample of the same workload: the full edge^3 field, as many
-    iterations as fit in about target_s seconds."""
+    bounded sample of the same workload: the full edge^3 field, iterated for
+    about target_s seconds."""
     import oracle
     from paper_2605_12734_gb300 import inputs
     oracle.build()
     threads = oracle.max_threads()
     P = oracle.init_padded(edge, edge, edge, 2, inputs.INIT_UNIFORM)
-    # an upper bound of the per-iteration cost (a 3-iteration call, its
-    # one-off copy and page faults included) so the sample never overruns
-    t1 = time.perf_counter()
-    oracle.sweep(P, 3, threads)
-    t3 = time.perf_counter()
-    per_iter = max(t3 - t1, 1e-3) / 3
-    iters = max(1, min(1000, int(target_s / per_iter)))
-    t0 = time.perf_counter()
-    oracle.sweep(P, iters, threads)
-    dt = time.perf_counter() - t0
-    ups = edge ** 3 * iters / dt
+    ups, iters, dt = _time_oracle(lambda n: oracle.sweep(P, n, threads), edge ** 3, target_s)
     return {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{edge}^3 field (U[0,1), seed 2), {iters} Jacobi iterations of the "
-                      f"undecomposed C oracle sweep on {threads} OpenMP threads ({dt:.1f} s)"}
+            "sample": f"{edge}^3 field (U[0,1), seed 2), undecomposed C oracle sweep on {threads} OpenMP threads; "
+                      f"rate from the difference of calls of increasing length, the last {iters} "
+                      f"iterations in {dt:.1f} s"}
 
 
 def oracle_cpu_baseline_2d(edge: int, target_s: float = 10.0):
     """The same for the 2D workload: the C oracle's 2D sweep of the full
-    edge^2 field, as many iterations as fit in about target_s seconds."""
+    edge^2 field."""
     import oracle
     from paper_2605_12734_gb300 import inputs
     oracle.build()
     threads = oracle.max_threads()
     P = oracle.init_padded_2d(edge, edge, 9, inputs.INIT_UNIFORM)
-    t1 = time.perf_counter()
-    oracle.sweep_2d(P, 3, threads)
-    t3 = time.perf_counter()
-    per_iter = max(t3 - t1, 1e-3) / 3
-    iters = max(1, min(1000, int(target_s / per_iter)))
-    t0 = time.perf_counter()
-    oracle.sweep_2d(P, iters, threads)
-    dt = time.perf_counter() - t0
-    return {"value": edge ** 2 * iters / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{edge}^2 field (U[0,1), seed 9), {iters} iterations of the undecomposed C oracle "
-                      f"2D sweep on {threads} OpenMP threads ({dt:.1f} s)"}
+    ups, iters, dt = _time_oracle(lambda n: oracle.sweep_2d(P, n, threads), edge ** 2, target_s)
+    return {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{edge}^2 field (U[0,1), seed 9), undecomposed C oracle 2D sweep on {threads} OpenMP "
+                      f"threads; rate from the difference of calls of increasing length, the last {iters} "
+                      f"iterations in {dt:.1f} s"}
 
 
 # ----------------------------------------------------------------- reference arm
@@ -408,10 +420,16 @@ def run_ours(args):
                     "alu": {"achieved": fpu * ups / 1e9, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
                             "frac": fpu * ups / 1e9 / FP64_NOMINAL_GFLOPS,
                             "fp64_adds_per_update": fp64_adds}}
-    traffic = profiled_traffic(args, plan) if not two_d else None
+    traffic = profiled_traffic(args, plan)
     if traffic is not None:
-        roofline["traffic"] = traffic
-        roofline["traffic_note"] = "DRAM bytes per iteration (ncu, one persistent launch of this kernel build)"
+        # the timed region is one persistent launch of args.steps iterations
+        per_launch = args.steps if args.path == "persistent" else 1
+        roofline["traffic"] = traffic * per_launch
+        roofline["traffic_per_step"] = traffic
+        roofline["traffic_vs_algorithmic"] = traffic / bytes_step
+        roofline["traffic_note"] = ("DRAM read+write bytes per launch of the timed region, from one ncu "
+                                    "capture of this kernel build (profiles/traffic_*.json), scaled by its "
+                                    "iterations per launch")
 
     # end to end through the public API with pinned host buffers: each e2e
     # step is a whole solve of the config's 100 iterations: write the initial
