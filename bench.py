@@ -36,11 +36,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="odf", choices=["odf", "uneven", "ceiling", "serve", "jacobi2d", "launch"],
+    ap.add_argument("--workload", default="odf", choices=["odf", "uneven", "ceiling", "serve", "jacobi2d", "launch", "shards"],
                     help="odf: 512^3 at --odf (default); uneven: 768x512x512 in ~300 uneven chares; "
                          "ceiling: 1024^3 in 4096 chares; serve: Poisson stream of jobs into the server; "
                          "jacobi2d: the 2D 5-point Jacobi on 32768^2 in --odf chares (a power of two); "
-                         "launch: the kernel-launch overhead microbenchmarks")
+                         "launch: the kernel-launch overhead microbenchmarks; shards: 512^3 at ODF 4096 split "
+                         "over 1-8 contexts (and 2 processes) exchanging faces through communication endpoints")
     ap.add_argument("--jobs", type=int, default=300, help="serve: number of jobs")
     ap.add_argument("--rate", type=float, default=60.0, help="serve: Poisson arrival rate (jobs/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
@@ -327,6 +328,8 @@ def run_ours(args):
         return run_serve(args, pkg, torch, rank, world, dev)
     if args.workload == "launch":
         return run_launch(args, pkg, rank, dev)
+    if args.workload == "shards":
+        return run_shards(args, pkg, torch, rank, dev)
     edge, odf = args.edge, args.odf
     p = round(odf ** (1 / 3))
     if p ** 3 != odf and args.workload != "jacobi2d":
@@ -556,6 +559,94 @@ def run_launch(args, pkg, rank, dev):
             "config": {"workload": "launch-overhead-microbenchmarks", "release_work_lcg_steps": work,
                        "rate_kernel": "empty, one block of 32 threads per SM"},
             "latency_us": lat, "release": release, "launch_rate": rate, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+SHARD_SHAPE = dict(threads=128, cells_per_thread=4, stages=4, arith=7, tile_z=32)
+
+
+def _shard_worker(rank, world, port, edge, steps, warmup, path, out):
+    """One process of the two-process shard measurement (spawned)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2605_12734_gb300 as pkg
+    from paper_2605_12734_gb300.shard import IpcTransport, ProcessShard, ShardPlan, _make_solver
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    plan = ShardPlan((edge, edge, edge), (1, 1, world))
+    stream = torch.cuda.Stream(device=0)
+    p = 16
+    solver = _make_solver(pkg, plan, rank, (p, p, p // world), stream.cuda_stream, seed=2, init_mode=1, path=path,
+                          device=0, **SHARD_SHAPE)
+    tr = IpcTransport(plan, rank, 0, stream.cuda_stream)
+    sh = ProcessShard(plan, rank, solver, tr)
+    sh.step(warmup)
+    stream.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    sh.step(steps)
+    stream.synchronize()
+    dt = time.perf_counter() - t0
+    dist.barrier()
+    sh.drain()
+    out[rank] = dt
+    dist.barrier()
+    solver.close()
+    tr.close()
+    dist.destroy_process_group()
+
+
+def run_shards(args, pkg, torch, rank, dev):
+    """The paper's process-width trade-off (Sec. III "Performance
+    trade-offs") on one GPU: the 512^3 grid at ODF 4096 held by one context,
+    or split along z into 2, 4, 8 shards (contexts on their own streams) whose
+    boundary faces move every iteration through communication endpoints (two
+    device copies and an event per face, the inter-process transport), or
+    held by two processes sharing the GPU through CUDA IPC endpoints."""
+    if rank != 0:
+        return 0
+    import socket
+    import torch.multiprocessing as mp
+    from paper_2605_12734_gb300.shard import ShardedJacobi
+    edge, steps, warmup = args.edge, args.steps, args.warmup
+    rows = []
+    clocks = ClockSampler(dev)
+    clocks.start()
+    for S in (1, 2, 4, 8):
+        sj = ShardedJacobi((edge, edge, edge), (1, 1, S), (16, 16, 16 // S), seed=2, init_mode=1, path=args.path,
+                           device=dev, **SHARD_SHAPE)
+        sj.step(warmup)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        sj.step(steps)
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        sj.close()
+        rows.append({"shards": S, "processes": 1, "ms_per_step": dt * 1e3 / steps,
+                     "updates_per_s": edge ** 3 * steps / dt})
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        out = man.dict()
+        mp.spawn(_shard_worker, args=(2, port, edge, steps, warmup, args.path, out), nprocs=2, join=True)
+        dt = max(dict(out).values())
+    rows.append({"shards": 2, "processes": 2, "ms_per_step": dt * 1e3 / steps,
+                 "updates_per_s": edge ** 3 * steps / dt})
+    clk = clocks.stop()
+    base = rows[0]["ms_per_step"]
+    for r in rows:
+        r["vs_one_context"] = r["ms_per_step"] / base
+    line = {"metric": "grid-pt updates/s of 512^3 at ODF 4096 split over shards exchanging faces",
+            "value": rows[1]["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"jacobi3d-{edge}^3-odf4096-shards", "path": args.path, "shape": SHARD_SHAPE,
+                       "timing": "host wall clock around the steps, device synchronised on both sides"},
+            "shards": rows, "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -154,6 +154,14 @@ typedef struct od_config {
     uint64_t spin_limit_ns;      /* device-side wait limit (0 = 2 000 000 000) */
     int32_t stencil;             /* OD_STENCIL_3D7 (default) or OD_STENCIL_2D5 */
     int32_t reserved;
+    /* A shard: this context holds the sub-box [gx0, gx0+nx) x [gy0, gy0+ny) x
+     * [gz0, gz0+nz) of a global grid gnx x gny x gnz (gnx = 0: the context is
+     * the whole grid).  The initial field, including every ghost layer, is the
+     * global field's; faces inside the global grid are fed by od_face_copy
+     * imports, faces on its boundary hold the Dirichlet shell.  2D: gnz = 1,
+     * gz0 = 0. */
+    int64_t gnx, gny, gnz;
+    int64_t gx0, gy0, gz0;
 } od_config;
 
 /* Host-only summary of a configuration's decomposition and memory. */
@@ -235,6 +243,20 @@ OD_API od_status od_read(od_ctx *ctx, double *dst, int32_t dst_is_device);
  * Enqueued on the stream (host sources are copied before return). */
 OD_API od_status od_write(od_ctx *ctx, const double *src, int32_t src_is_device);
 
+/* Face exchange of a shard (a context holding a sub-box of a global grid,
+ * see od_config.gnx): the data of the paper's transports between chares of
+ * different processes (Sec. IV).  dir 0 (export) copies the current field's
+ * boundary layer on domain face `face` -- the interior cells next to it --
+ * into buf; dir 1 (import) copies buf into the ghost layer on that face,
+ * which the next iteration reads.  face: 0..5 = x-, x+, y-, y+, z-, z+ (2D:
+ * 0..3 = x-, x+, y-, y+ of the 2D grid).  buf holds the whole face, dense:
+ * x faces nz x ny doubles (y fastest), y faces nz x nx, z faces ny x nx (x
+ * fastest); 2D x faces ny, y faces nx.  buf_is_device != 0: device memory of
+ * the context's device, the copy is enqueued on the context's stream;
+ * otherwise host memory, and the call synchronises.  od_write does not touch
+ * the ghost layers of a shard's domain faces: import them after it. */
+OD_API od_status od_face_copy(od_ctx *ctx, int32_t face, int32_t dir, double *buf, int32_t buf_is_device);
+
 /* Counters and the plan; synchronises and reports device-side errors. */
 OD_API od_status od_stats_get(od_ctx *ctx, od_stats *out);
 
@@ -256,6 +278,50 @@ OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
  * of the current device and synchronises.  n >= 0 elements. */
 OD_API od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n);
 OD_API od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n);
+
+/* ------------------------------------------------------------------ inter-process transport
+ *
+ * The paper's intra-node, inter-process path (Sec. IV, transport item 2):
+ * every process allocates one device communication buffer and a pool of
+ * interprocess events once (od_comm_create), and every peer maps them once
+ * through their IPC handles (od_comm_handles in the owner, od_comm_open in
+ * the peer), so no handle is opened per message.  A face of a shard then
+ * moves by two device-to-device copies: the sender exports it into its own
+ * buffer (od_face_copy, dir 0) and records an event (od_comm_record); after a
+ * host control message with the buffer offset and the event index, the
+ * receiver makes its stream wait on that event of the sender's endpoint
+ * (od_comm_wait) and imports from the mapped buffer (od_face_copy, dir 1).
+ * The endpoints work within one process too (no od_comm_open needed). */
+typedef struct od_comm od_comm;
+
+/* Bytes of an endpoint's handle block: a 16-byte header, the buffer's IPC
+ * handle and one IPC handle per event (64 bytes each). */
+#define OD_COMM_HANDLE_BYTES(nevents) (16u + 64u * (1u + (uint64_t)(nevents)))
+
+/* A new endpoint on `device`: `bytes` (1..2^40) of device memory and
+ * `nevents` (1..4096) interprocess events (timing disabled).  Owned by the
+ * caller until od_comm_destroy. */
+OD_API od_status od_comm_create(od_comm **out, int32_t device, uint64_t bytes, int32_t nevents);
+/* Write the endpoint's handle block (OD_COMM_HANDLE_BYTES(nevents) bytes) for
+ * the peers.  OD_ESTATE for an endpoint opened from a peer. */
+OD_API od_status od_comm_handles(const od_comm *c, void *handles, uint64_t capacity);
+/* Map a peer process's endpoint from its handle block (`size` bytes) into
+ * this process on `device` (the same physical GPU or a peer of it).  The
+ * handles of an endpoint of this same process cannot be opened (CUDA
+ * refuses): use that endpoint directly. */
+OD_API od_status od_comm_open(od_comm **out, int32_t device, const void *handles, uint64_t size);
+/* The endpoint's buffer (device pointer, valid in this process), its size
+ * and event count; any output may be NULL. */
+OD_API od_status od_comm_buffer(const od_comm *c, double **buf, uint64_t *bytes, int32_t *nevents);
+/* Record event `event` of the endpoint on `stream` (a cudaStream_t). */
+OD_API od_status od_comm_record(od_comm *c, int32_t event, void *stream);
+/* Make `stream` wait for the last recording of event `event` of the endpoint
+ * that happened before this call (host order: the recorder's control
+ * message must have arrived first). */
+OD_API od_status od_comm_wait(od_comm *c, int32_t event, void *stream);
+/* Free the buffer and events (or unmap a peer's); the caller must have
+ * finished every stream that uses them. */
+OD_API od_status od_comm_destroy(od_comm *c);
 
 /* ------------------------------------------------------------------ launch overhead
  *

@@ -25,7 +25,7 @@ STENCILS = {"3d7": 0, "2d5": 1}
 
 __all__ = ["Jacobi3D", "Jacobi2D", "Server", "STENCILS", "ODError", "PATHS", "make_config", "plan", "decompose", "lib", "arith_host",
            "arith_device", "jacobi_noalloc", "plan_2d", "decompose_2d", "bench_launch_latency", "bench_release",
-           "bench_launch_rate"]
+           "bench_launch_rate", "Comm"]
 
 
 def _cuts_array(cuts):
@@ -40,7 +40,7 @@ def make_config(nx: int, ny: int, nz: int, *, split=(1, 1, 1), cuts=None, seed: 
                 tile_y: int = 0, tile_z: int = 0, threads: int = 0, cells_per_thread: int = 0,
                 stages: int = 0, arith: int = -1, order: int = 0, stream_pool: int = 0, device: int = 0,
                 stream: int | None = None, arena: int | None = None, arena_bytes: int = 0,
-                spin_limit_ns: int = 0, stencil: str | int = "3d7"):
+                spin_limit_ns: int = 0, stencil: str | int = "3d7", gdims=None, goff=None):
     """Build an od_config (returns (config, keepalive) -- keep both alive while
     the config is used, the cut arrays are referenced by pointer).  For the
     2D stencil ("2d5") nz is 1 and split / cuts may give two axes."""
@@ -52,6 +52,11 @@ def make_config(nx: int, ny: int, nz: int, *, split=(1, 1, 1), cuts=None, seed: 
         cuts = tuple(cuts) + (None,) * (3 - len(cuts))
     cfg.px, cfg.py, cfg.pz = (int(v) for v in split)
     cfg.stencil = STENCILS[stencil] if isinstance(stencil, str) else int(stencil)
+    if gdims is not None:  # a shard: this context is a sub-box of the global grid gdims at offset goff
+        g = tuple(int(v) for v in gdims) + (1,) * (3 - len(gdims))
+        o = tuple(int(v) for v in (goff or ())) + (0,) * (3 - len(goff or ()))
+        cfg.gnx, cfg.gny, cfg.gnz = g
+        cfg.gx0, cfg.gy0, cfg.gz0 = o
     keep = []
     if cuts is not None:
         for axis, cl in zip("xyz", cuts):
@@ -217,6 +222,20 @@ class Jacobi3D:
             assert src.is_cuda and src.numel() == self.cells and src.is_contiguous()
             check(lib().od_write(self._h, src.data_ptr(), 1), "od_write")
 
+    def face_copy(self, face: int, direction: int, buf) -> None:
+        """Export (direction 0) the boundary layer on domain face `face` into
+        buf, or import (1) buf into its ghost layer; buf: a device pointer
+        (int), a CUDA float64 tensor, or a numpy float64 array (host)."""
+        if isinstance(buf, np.ndarray):
+            assert buf.dtype == np.float64 and buf.flags["C_CONTIGUOUS"]
+            ptr, dev = buf.ctypes.data, 0
+        elif isinstance(buf, int):
+            ptr, dev = buf, 1
+        else:
+            assert buf.is_cuda and buf.dtype.itemsize == 8 and buf.is_contiguous()
+            ptr, dev = buf.data_ptr(), 1
+        check(lib().od_face_copy(self._h, int(face), int(direction), ptr, dev), "od_face_copy")
+
     def stats(self) -> dict:
         st = od_stats()
         check(lib().od_stats_get(self._h, ctypes.byref(st)), "od_stats_get")
@@ -263,6 +282,54 @@ def decompose_2d(nx, ny, **kw):
     """2D chare boxes (n,4: x0,bx,y0,by) and neighbours (n,4: x-,x+,y-,y+)."""
     box, nbr = decompose(nx, ny, 1, stencil="2d5", **kw)
     return box[:, :4].copy(), nbr[:, :4].copy()
+
+
+class Comm:
+    """A communication endpoint (od_comm_*): a device buffer and a pool of
+    interprocess events, created here or mapped from a peer's handles."""
+
+    def __init__(self, handle):
+        self._h = handle
+        buf, nbytes, nev = ctypes.c_void_p(), ctypes.c_uint64(), ctypes.c_int32()
+        check(lib().od_comm_buffer(self._h, ctypes.byref(buf), ctypes.byref(nbytes), ctypes.byref(nev)),
+              "od_comm_buffer")
+        self.ptr, self.nbytes, self.nevents = buf.value, nbytes.value, nev.value
+
+    @classmethod
+    def create(cls, nbytes: int, nevents: int, device: int = 0) -> "Comm":
+        h = ctypes.c_void_p()
+        check(lib().od_comm_create(ctypes.byref(h), int(device), int(nbytes), int(nevents)), "od_comm_create")
+        return cls(h)
+
+    @classmethod
+    def open(cls, handles: bytes, device: int = 0) -> "Comm":
+        h = ctypes.c_void_p()
+        blob = ctypes.create_string_buffer(bytes(handles), len(handles))
+        check(lib().od_comm_open(ctypes.byref(h), int(device), blob, len(handles)), "od_comm_open")
+        return cls(h)
+
+    def handles(self) -> bytes:
+        n = 16 + 64 * (1 + self.nevents)
+        blob = ctypes.create_string_buffer(n)
+        check(lib().od_comm_handles(self._h, blob, n), "od_comm_handles")
+        return blob.raw
+
+    def record(self, event: int, stream: int) -> None:
+        check(lib().od_comm_record(self._h, int(event), stream), "od_comm_record")
+
+    def wait(self, event: int, stream: int) -> None:
+        check(lib().od_comm_wait(self._h, int(event), stream), "od_comm_wait")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().od_comm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

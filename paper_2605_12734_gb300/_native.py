@@ -35,6 +35,7 @@ class od_config(ctypes.Structure):
         ("stages", _i32), ("arith", _i32), ("order", _i32), ("stream_pool", _i32), ("device", _i32),
         ("stream", _vp), ("arena", _vp), ("arena_bytes", _u64), ("spin_limit_ns", _u64),
         ("stencil", _i32), ("reserved", _i32),
+        ("gnx", _i64), ("gny", _i64), ("gnz", _i64), ("gx0", _i64), ("gy0", _i64), ("gz0", _i64),
     ]
 
 
@@ -116,6 +117,14 @@ SIGNATURES = {
     "od_bench_launch_latency": (_i32, [_i32, _i32, _i32, ctypes.POINTER(ctypes.c_double)]),
     "od_bench_release": (_i32, [_i32, _i64, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_double)]),
     "od_bench_launch_rate": (_i32, [_i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_double)]),
+    "od_face_copy": (_i32, [_vp, _i32, _i32, _vp, _i32]),
+    "od_comm_create": (_i32, [ctypes.POINTER(_vp), _i32, _u64, _i32]),
+    "od_comm_handles": (_i32, [_vp, _vp, _u64]),
+    "od_comm_open": (_i32, [ctypes.POINTER(_vp), _i32, _vp, _u64]),
+    "od_comm_buffer": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_u64), ctypes.POINTER(_i32)]),
+    "od_comm_record": (_i32, [_vp, _i32, _vp]),
+    "od_comm_wait": (_i32, [_vp, _i32, _vp]),
+    "od_comm_destroy": (_i32, [_vp]),
     "od_destroy": (_i32, [_vp]),
     "od_last_error": (ctypes.c_char_p, []),
     "od_version": (ctypes.c_char_p, []),

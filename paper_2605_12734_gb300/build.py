@@ -25,7 +25,8 @@ NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-f
               "-Xcompiler", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
 
-SOURCES = ["od_kernels.cu", "od_api.cu", "od_plan.cpp", "od_noalloc.cu", "od_serve.cu", "od_launch.cu"]
+SOURCES = ["od_kernels.cu", "od_api.cu", "od_plan.cpp", "od_noalloc.cu", "od_serve.cu", "od_launch.cu",
+           "od_comm.cu"]
 # the tile kernels, compiled once per arithmetic mode (-DOD_AMODE=m)
 TILE_SOURCE = "od_tiles.cu"
 AMODES = range(9)

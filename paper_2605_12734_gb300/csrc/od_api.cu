@@ -740,7 +740,8 @@ od_status od_create(od_ctx **out, const od_config *cfg_in) {
     OD_TRY(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming));
     c->ev.resize(2 * p.ch.size(), nullptr);
     for (auto &e : c->ev) OD_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    OD_TRY(od::launch_init(c->d_ch, (int)p.ch.size(), p.nx, p.ny, p.nz, cfg->seed, cfg->init_mode, p.stencil,
+    OD_TRY(od::launch_init(c->d_ch, (int)p.ch.size(), p.gnx, p.gny, p.gnz, p.gx0, p.gy0, p.gz0, cfg->seed,
+                           cfg->init_mode, p.stencil,
                            c->stream));
     OD_TRY(cudaStreamSynchronize(c->stream));
 #undef OD_TRY
@@ -812,6 +813,36 @@ od_status od_write(od_ctx *c, const double *src, int32_t src_is_device) {
     }
     OD_CUDA(od::launch_scatter(c->d_ch, (int)p.ch.size(), par, p.nx, p.ny, p.nz, g, c->stream));
     if (!src_is_device) OD_CUDA(cudaStreamSynchronize(c->stream));
+    return OD_OK;
+}
+
+od_status od_face_copy(od_ctx *c, int32_t face, int32_t dir, double *buf, int32_t buf_is_device) {
+    if (!c || !buf || (dir != 0 && dir != 1)) return fail(OD_EINVAL, "od_face_copy: null argument or dir not 0/1");
+    if (c->failed) return fail(OD_ESTATE, "context failed earlier; destroy it");
+    const od::Plan &p = c->plan;
+    int f = face;
+    if (p.stencil == OD_STENCIL_2D5) {  // the 2D grid's y faces are the internal z faces
+        if (face < 0 || face > 3) return fail(OD_EINVAL, "od_face_copy: a 2D face is 0..3");
+        f = face < 2 ? face : face + 2;
+    } else if (face < 0 || face > 5) {
+        return fail(OD_EINVAL, "od_face_copy: face must be 0..5");
+    }
+    const int64_t n = f < 2 ? p.ny * p.nz : f < 4 ? p.nx * p.nz : p.nx * p.ny;
+    DeviceGuard dg(c->device);
+    const int par = (int)(c->steps & 1);
+    const int nch = (int)p.ch.size();
+    if (buf_is_device) {
+        OD_CUDA(od::launch_face_copy(c->d_ch, nch, par, f, dir, buf, p.nx, p.ny, p.nz, c->stream));
+        return OD_OK;
+    }
+    od_status s = ensure_stage(c);
+    if (s != OD_OK) return s;
+    if (dir == 1)
+        OD_CUDA(cudaMemcpyAsync(c->d_stage, buf, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    OD_CUDA(od::launch_face_copy(c->d_ch, nch, par, f, dir, c->d_stage, p.nx, p.ny, p.nz, c->stream));
+    if (dir == 0)
+        OD_CUDA(cudaMemcpyAsync(buf, c->d_stage, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    OD_CUDA(cudaStreamSynchronize(c->stream));
     return OD_OK;
 }
 

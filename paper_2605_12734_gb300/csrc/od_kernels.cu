@@ -99,8 +99,8 @@ __device__ __forceinline__ bool padded_cell(const ChareDev &C, int64_t e, int64_
 // A2: the initial field in both parities, interior and every ghost cell.
 // For the 2D stencil (internal grid (nx, 1, ny)) a cell takes its 2D padded
 // index gx + (nx+2)*gz.
-__global__ void k_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
-                       int mode, int stencil) {
+__global__ void k_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, int64_t ox, int64_t oy,
+                       int64_t oz, uint64_t seed, int mode, int stencil) {
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
         const int64_t na = (int64_t)(C.bz + 2) * C.rows * C.pitch;
@@ -109,6 +109,9 @@ __global__ void k_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int6
             int64_t gx, gy, gz;
             double v = 0.0;
             if (padded_cell(C, e, &gx, &gy, &gz)) {
+                gx += ox;  // shard offset: padded global coordinates of the whole grid
+                gy += oy;
+                gz += oz;
                 if (stencil == OD_STENCIL_2D5) {
                     const bool shell = gx == 0 || gz == 0 || gx == nx + 1 || gz == nz + 1;
                     if (shell || mode != 0) v = field_uniform(seed, (uint64_t)(gx + (nx + 2) * gz));
@@ -165,6 +168,34 @@ __global__ void k_unpack(const ChareDev *ch, int c, int p, int slot) {
         while (e >= C.foff[f + 1]) ++f;
         if (C.nbr[f] < 0) continue;
         A[face_offset(C, f, e - C.foff[f], true)] = R[e];
+    }
+}
+
+// Domain-face exchange of a shard: the chares on domain face f (no neighbour
+// there) copy, cell by cell, their boundary layer of parity p into buf
+// (dir 0) or buf into their ghost layer (dir 1).  buf is the whole face,
+// dense: x faces nz x ny (y fastest), y faces nz x nx, z faces ny x nx (x
+// fastest).
+__global__ void k_face_copy(const ChareDev *ch, int nch, int p, int f, int dir, double *buf, int64_t nx, int64_t ny,
+                            int64_t nz) {
+    for (int c = blockIdx.y; c < nch; c += gridDim.y) {
+        const ChareDev &C = ch[c];
+        const bool on_face = f == OD_FACE_XLO ? C.x0 == 0 : f == OD_FACE_XHI ? C.x0 + C.bx == nx
+                           : f == OD_FACE_YLO ? C.y0 == 0 : f == OD_FACE_YHI ? C.y0 + C.by == ny
+                           : f == OD_FACE_ZLO ? C.z0 == 0 : C.z0 + C.bz == nz;
+        if (!on_face) continue;
+        const int n = f < 2 ? C.by * C.bz : f < 4 ? C.bx * C.bz : C.bx * C.by;
+        const int w = f < 2 ? C.by : C.bx;  // fastest extent of the chare's face
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+            const int a = q % w, b = q / w;
+            int64_t g;  // position in buf
+            if (f < 2) g = (C.z0 + b) * ny + C.y0 + a;
+            else if (f < 4) g = (C.z0 + b) * nx + C.x0 + a;
+            else g = (C.y0 + b) * nx + C.x0 + a;
+            const int64_t o = face_offset(C, f, q, dir != 0);
+            if (dir == 0) buf[g] = C.A[p][o];
+            else C.A[p][o] = buf[g];
+        }
     }
 }
 
@@ -291,9 +322,16 @@ cudaError_t persistent_occupancy(int threads, int cpt, int amode, int smem_bytes
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, (size_t)smem_bytes);
 }
 
-cudaError_t launch_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
-                        int mode, int stencil, cudaStream_t s) {
-    k_init<<<dim3(io_grid_x(nch), io_grid_y(nch)), 256, 0, s>>>(ch, nch, nx, ny, nz, seed, mode, stencil);
+cudaError_t launch_init(const ChareDev *ch, int nch, int64_t gnx, int64_t gny, int64_t gnz, int64_t gx0,
+                        int64_t gy0, int64_t gz0, uint64_t seed, int mode, int stencil, cudaStream_t s) {
+    k_init<<<dim3(io_grid_x(nch), io_grid_y(nch)), 256, 0, s>>>(ch, nch, gnx, gny, gnz, gx0, gy0, gz0, seed, mode,
+                                                                stencil);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_copy(const ChareDev *ch, int nch, int parity, int face, int dir, double *buf, int64_t nx,
+                             int64_t ny, int64_t nz, cudaStream_t s) {
+    k_face_copy<<<dim3(io_grid_x(nch), io_grid_y(nch)), 256, 0, s>>>(ch, nch, parity, face, dir, buf, nx, ny, nz);
     return cudaGetLastError();
 }
 

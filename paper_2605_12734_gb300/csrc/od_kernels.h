@@ -33,8 +33,14 @@ cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, in
 cudaError_t persistent_occupancy(int threads, int cpt, int amode, int smem_bytes, int stencil,
                                  int *blocks_per_sm);
 
-cudaError_t launch_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, uint64_t seed,
-                        int mode, int stencil, cudaStream_t s);
+// The initial field of a shard at offset (gx0, gy0, gz0) of a global grid
+// gnx x gny x gnz (the whole grid: offsets 0, global = local extents).
+cudaError_t launch_init(const ChareDev *ch, int nch, int64_t gnx, int64_t gny, int64_t gnz, int64_t gx0,
+                        int64_t gy0, int64_t gz0, uint64_t seed, int mode, int stencil, cudaStream_t s);
+// Domain-face exchange of a shard (od_face_copy): dir 0 copies the boundary
+// layer of parity p on face f into buf, dir 1 buf into the ghost layer.
+cudaError_t launch_face_copy(const ChareDev *ch, int nch, int parity, int face, int dir, double *buf, int64_t nx,
+                             int64_t ny, int64_t nz, cudaStream_t s);
 cudaError_t launch_pack(const ChareDev *ch, int c, int parity, int elems, cudaStream_t s);
 cudaError_t launch_unpack(const ChareDev *ch, int c, int parity, int slot, int elems, cudaStream_t s);
 cudaError_t launch_gather(const ChareDev *ch, int nch, int parity, int64_t nx, int64_t ny, double *g,

@@ -179,6 +179,26 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
             !edges_from(cfg->nz, cfg->pz, cfg->cuts_z, cfg->ncuts_z, "z", &p.ez, err))
             return OD_EINVAL;
     }
+    // shard of a global grid (all zero: the context is the whole grid)
+    const bool shard = cfg->gnx || cfg->gny || cfg->gnz || cfg->gx0 || cfg->gy0 || cfg->gz0;
+    if (!shard) {
+        p.gnx = p.nx; p.gny = p.ny; p.gnz = p.nz;
+    } else if (p.stencil == OD_STENCIL_2D5) {
+        if ((cfg->gnz != 0 && cfg->gnz != 1) || cfg->gz0 != 0) {
+            *err = "2D shard: gnz must be 1 (or 0) and gz0 0";
+            return OD_EINVAL;
+        }
+        p.gnx = cfg->gnx; p.gny = 1; p.gnz = cfg->gny;
+        p.gx0 = cfg->gx0; p.gy0 = 0; p.gz0 = cfg->gy0;
+    } else {
+        p.gnx = cfg->gnx; p.gny = cfg->gny; p.gnz = cfg->gnz;
+        p.gx0 = cfg->gx0; p.gy0 = cfg->gy0; p.gz0 = cfg->gz0;
+    }
+    if (p.gx0 < 0 || p.gy0 < 0 || p.gz0 < 0 || p.gx0 + p.nx > p.gnx || p.gy0 + p.ny > p.gny ||
+        p.gz0 + p.nz > p.gnz) {
+        *err = "shard box must lie inside the global grid (gx0 + nx <= gnx, ...)";
+        return OD_EINVAL;
+    }
     p.px = (int32_t)p.ex.size() - 1;
     p.py = (int32_t)p.ey.size() - 1;
     p.pz = (int32_t)p.ez.size() - 1;

@@ -27,6 +27,8 @@ struct HostChare {
 struct Plan {
     int32_t stencil = 0;                      // OD_STENCIL_*; 2D runs as (nx, 1, ny)
     int64_t nx = 0, ny = 0, nz = 0;           // internal (3D) extents
+    int64_t gnx = 0, gny = 0, gnz = 0;        // global grid (internal axes) this context is a shard of
+    int64_t gx0 = 0, gy0 = 0, gz0 = 0;        // offset of this context's interior in it
     int32_t px = 0, py = 0, pz = 0;
     std::vector<int64_t> ex, ey, ez;          // block edges per axis
     std::vector<HostChare> ch;
