@@ -162,14 +162,16 @@ def profiled_traffic(args, plan):
         return None
     with open(p) as f:
         d = json.load(f)
+    rev = KERNEL_REV_2D if args.workload == "jacobi2d" else KERNEL_REV
     if d.get("arith") != plan["arith"] or d.get("threads") != plan["threads"] or \
-            d.get("cells_per_thread") != plan["cells_per_thread"] or d.get("kernel_rev") != KERNEL_REV:
+            d.get("cells_per_thread") != plan["cells_per_thread"] or d.get("kernel_rev") != rev:
         return None
     return d["dram_bytes_per_step"]
 
 
-# bumped whenever the tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 9
+# bumped whenever a tile kernel changes, so stale profiler counters are not reused
+KERNEL_REV = 9      # 3D 7-point
+KERNEL_REV_2D = 10  # 2D 5-point
 
 
 def combine_ranks(ms: float, updates: float, world: int, device: str):

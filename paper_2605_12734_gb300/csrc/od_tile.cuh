@@ -527,10 +527,17 @@ __device__ __forceinline__ Ring ring_setup(const KArgs &a, unsigned char *smem) 
 #ifndef OD_MIN_THREADS_PER_SM
 #define OD_MIN_THREADS_PER_SM 1280
 #endif
-constexpr int min_blocks(int nt) { return OD_MIN_THREADS_PER_SM / nt; }
+// The 2D sweep needs fewer registers and gains from more resident warps
+// (measured: 1536 threads per SM, 38 registers, 2.9 % faster than 1280).
+#ifndef OD_MIN_THREADS_PER_SM_2D
+#define OD_MIN_THREADS_PER_SM_2D 1536
+#endif
+constexpr int min_blocks(int nt, int st) {
+    return (st == OD_STENCIL_2D5 ? OD_MIN_THREADS_PER_SM_2D : OD_MIN_THREADS_PER_SM) / nt;
+}
 
 template <int NT, int CPT, bool PUSH, int AM, int ST>
-__global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles(const KArgs a) {
+__global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_tiles(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (blockDim.x != NT) {
         if (threadIdx.x == 0) record_err(a.err, OD_ERR_BAD_LAUNCH, -1, -1);
@@ -546,7 +553,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles(const KArgs a) {
 // [first[j], first[j+1]); every block runs one tile of its job.  All jobs
 // share the launch's CTA shape, ring depth and slot size.
 template <int NT, int CPT, int AM, int ST>
-__global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles_multi(const KArgs *jobs, const int32_t *first,
+__global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_tiles_multi(const KArgs *jobs, const int32_t *first,
                                                                    int32_t njobs) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int32_t s_job;
@@ -577,7 +584,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT)) k_tiles_multi(const KArgs 
 // smaller than the waiter's, and tickets are taken in order by running CTAs,
 // so the wait graph has no cycle and needs no co-residency guarantee.
 template <int NT, int CPT, int AM, int ST>
-__global__ void __launch_bounds__(NT, min_blocks(NT)) k_persistent(const KArgs a) {
+__global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_persistent(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int32_t s_ticket;
     if (blockDim.x != NT) {
