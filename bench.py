@@ -706,6 +706,7 @@ def run_serve(args, pkg, torch, rank, world, dev):
             "latency_p50_s": pct(0.50), "latency_p99_s": pct(0.99), "latency_mean_s": sum(lat) / len(lat),
             "latency_max_s": lat_sorted[-1], "wall_s": wall, "launches": st["launches"],
             "pool_peak_gb": st["pool_peak"] / (1 << 30), "offered_updates_per_s": upd / jobs[-1].arrival_s,
+            "admit_seconds": st["admit_seconds"],
             "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -406,6 +406,8 @@ typedef struct od_server_stats_t {
     double updates_done;         /* cell updates of completed jobs */
     uint64_t pool_used, pool_peak;
     double seconds;              /* since the server was created */
+    double admit_seconds;        /* spent creating job contexts (on the
+                                    admission thread, beside the launches) */
 } od_server_stats_t;
 
 OD_API void od_server_config_default(od_server_config *cfg);

@@ -126,9 +126,9 @@ struct od_server {
     std::vector<cudaEvent_t> free_events;
     std::deque<Batch> inflight;
     int64_t next_batch = 0;
-    std::thread worker;
+    std::thread worker, admitter;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work, cv_done, cv_admit;
     std::deque<Job *> queue;
     std::vector<Job *> running;
     std::unordered_map<uint64_t, Job *> jobs;
@@ -138,6 +138,7 @@ struct od_server {
     // statistics
     int64_t launches = 0, done = 0, failed = 0;
     double updates_done = 0;
+    double admit_seconds = 0;  // spent creating job contexts (admission thread)
     std::string worker_error;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -166,22 +167,27 @@ od_config job_config(od_server *s, Job *j) {
 }
 
 // Admit queued jobs (called with the lock held; drops it around od_create).
-void admit(od_server *s, std::unique_lock<std::mutex> &lk) {
+// Returns whether any job left the queue.
+bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
+    bool progress = false;
     while (!s->queue.empty() && (s->cfg.max_active <= 0 || (int)s->running.size() < s->cfg.max_active) &&
            (int)s->running.size() < s->max_jobs) {
         Job *j = s->queue.front();
         size_t off = 0;
-        if (!s->pool.alloc(j->bytes, &off)) return;  // wait for memory
+        if (!s->pool.alloc(j->bytes, &off)) return progress;  // wait for memory
         s->queue.pop_front();
         j->off = off;
         od_config c = job_config(s, j);
         c.arena = s->pool_base + off;
         c.arena_bytes = j->bytes;
         lk.unlock();
+        const double t_create = s->now();
         od_ctx *ctx = nullptr;
         od_status st = od_create(&ctx, &c);
         std::string msg = st == OD_OK ? "" : od_last_error();
         lk.lock();
+        s->admit_seconds += s->now() - t_create;
+        progress = true;
         if (st != OD_OK || ctx->plan.stage_doubles * s->stages * 8 + 256 > s->smem_cap) {
             if (ctx) od_destroy(ctx);
             s->pool.release(j->off, j->bytes);
@@ -202,7 +208,9 @@ void admit(od_server *s, std::unique_lock<std::mutex> &lk) {
         }
         j->state = OD_JOB_RUNNING;
         s->running.push_back(j);
+        s->cv_work.notify_all();
     }
+    return progress;
 }
 
 // Retire launches that completed (lock held).
@@ -274,18 +282,30 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
     return true;
 }
 
+// Admission thread: creates the contexts of queued jobs (tables, initial
+// field) while the worker keeps the GPU busy with the running ones.
+void admitter_main(od_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        if (admit(s, lk)) continue;
+        s->cv_admit.wait_for(lk, std::chrono::milliseconds(2));
+    }
+}
+
 void worker_main(od_server *s) {
     cudaSetDevice(s->device);
     std::vector<KArgs> hk;
     std::vector<int32_t> hf;
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
-        admit(s, lk);
         retire(s);
         // drop finished jobs from the running set (their memory stays until release)
+        const size_t before = s->running.size();
         s->running.erase(std::remove_if(s->running.begin(), s->running.end(),
                                         [](Job *j) { return j->state != OD_JOB_RUNNING; }),
                          s->running.end());
+        if (s->running.size() != before) s->cv_admit.notify_all();  // an active slot is free
         bool launched = false;
         if (s->inflight.size() < 2 && s->worker_error.empty()) launched = launch_batch(s, hk, hf);
         if (launched) continue;
@@ -361,6 +381,7 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
     if (od::prepare_tile_kernels(s->threads, s->cpt, s->arith, s->smem_cap, OD_STENCIL_3D7) != cudaSuccess)
         return bail(OD_ECUDA, "cannot configure the tile kernels");
     s->worker = std::thread(worker_main, s);
+    s->admitter = std::thread(admitter_main, s);
     *out = s;
     return OD_OK;
 }
@@ -396,7 +417,7 @@ od_status od_server_submit(od_server *s, const od_config *job, int32_t iters, ui
     s->jobs[j->id] = j;
     s->queue.push_back(j);
     *job_id = j->id;
-    s->cv_work.notify_all();
+    s->cv_admit.notify_all();
     return OD_OK;
 }
 
@@ -456,7 +477,7 @@ od_status od_server_release(od_server *s, uint64_t id) {
     lk.lock();
     if (had_memory) s->pool.release(j->off, j->bytes);
     delete j;
-    s->cv_work.notify_all();
+    s->cv_admit.notify_all();  // memory is free for queued jobs
     return OD_OK;
 }
 
@@ -473,6 +494,7 @@ od_status od_server_stats(od_server *s, od_server_stats_t *out) {
     out->pool_used = s->pool.used();
     out->pool_peak = s->pool.peak();
     out->seconds = s->now();
+    out->admit_seconds = s->admit_seconds;
     if (!s->worker_error.empty()) return fail(OD_ECUDA, s->worker_error);
     return OD_OK;
 }
@@ -483,8 +505,10 @@ od_status od_server_destroy(od_server *s) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
         s->cv_work.notify_all();
+        s->cv_admit.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
+    if (s->admitter.joinable()) s->admitter.join();
     cudaSetDevice(s->device);
     if (s->compute) cudaStreamSynchronize(s->compute);
     for (auto &kv : s->jobs) {
