@@ -447,7 +447,7 @@ def run_ours(args):
         host_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
         solver.read(host_in.numpy())       # a valid field to feed back in
         iters_job = 100
-        reps = 2
+        reps = 5
         solver.write(host_in.numpy())
         solver.step(iters_job)
         solver.read(host_out.numpy())      # warm-up job

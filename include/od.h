@@ -232,13 +232,15 @@ OD_API od_status od_sync(od_ctx *ctx);
 
 /* Copy the current field u^{steps_done} (interior only, x fastest,
  * nx*ny*nz doubles) to dst.  dst_is_device != 0: dst is device memory of the
- * context's device; otherwise host memory (a device staging buffer of
- * nx*ny*nz doubles is allocated on the first host read or write and kept).
- * Synchronises the stream. */
+ * context's device; otherwise host memory: pinned (page-locked) host memory
+ * is written in place by the gather kernel over the host link, pageable
+ * memory through a device staging buffer of nx*ny*nz doubles allocated on
+ * the first such read or write and kept.  Synchronises the stream. */
 OD_API od_status od_read(od_ctx *ctx, double *dst, int32_t dst_is_device);
 
 /* Replace the current field's interior with src (nx*ny*nz doubles, x fastest;
- * device or host as for od_read) and refresh every internal ghost layer; the
+ * device memory, or host memory copied through the staging buffer) and
+ * refresh every internal ghost layer; the
  * Dirichlet shell is kept.  Used to import a checkpoint or a user field.
  * Enqueued on the stream (host sources are copied before return). */
 OD_API od_status od_write(od_ctx *ctx, const double *src, int32_t src_is_device);

@@ -78,49 +78,37 @@ __device__ __forceinline__ double field_init(int64_t gx, int64_t gy, int64_t gz,
     return field_uniform(seed, (uint64_t)(gx + (nx + 2) * (gy + (ny + 2) * gz)));
 }
 
-// Classify element e of a chare's padded array: returns false for padding
-// and for edge/corner ghosts (never read), else the padded global
-// coordinates of the cell it holds (a 2D chare has no y-ghost rows: its
-// cells all get padded y index 1).
-__device__ __forceinline__ bool padded_cell(const ChareDev &C, int64_t e, int64_t *gx, int64_t *gy,
-                                            int64_t *gz) {
-    const int col = (int)(e % C.pitch);
-    const int64_t row = e / C.pitch;
-    const int jp = (int)(row % C.rows) + 1 - C.row0, kp = (int)(row / C.rows);
-    if (col > C.bx + 1) return false;
-    const int ghosts = (col == 0 || col == C.bx + 1) + (jp == 0 || jp == C.by + 1) + (kp == 0 || kp == C.bz + 1);
-    if (ghosts > 1) return false;
-    *gx = C.x0 + col;
-    *gy = C.y0 + jp;
-    *gz = C.z0 + kp;
-    return true;
-}
-
-// A2: the initial field in both parities, interior and every ghost cell.
-// For the 2D stencil (internal grid (nx, 1, ny)) a cell takes its 2D padded
-// index gx + (nx+2)*gz.
+// A2: the initial field in both parities, interior and every ghost cell
+// (edge/corner ghosts and row padding, never read, get 0).  One warp per
+// padded row.  A 2D chare's rows are single-row planes whose cells take the
+// 2D padded index gx + (nx+2)*gz; (ox, oy, oz) is a shard's offset in the
+// global grid nx x ny x nz.
 __global__ void k_init(const ChareDev *ch, int nch, int64_t nx, int64_t ny, int64_t nz, int64_t ox, int64_t oy,
                        int64_t oz, uint64_t seed, int mode, int stencil) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
-        const int64_t na = (int64_t)(C.bz + 2) * C.rows * C.pitch;
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na;
-             e += (int64_t)gridDim.x * blockDim.x) {
-            int64_t gx, gy, gz;
-            double v = 0.0;
-            if (padded_cell(C, e, &gx, &gy, &gz)) {
-                gx += ox;  // shard offset: padded global coordinates of the whole grid
-                gy += oy;
-                gz += oz;
-                if (stencil == OD_STENCIL_2D5) {
-                    const bool shell = gx == 0 || gz == 0 || gx == nx + 1 || gz == nz + 1;
-                    if (shell || mode != 0) v = field_uniform(seed, (uint64_t)(gx + (nx + 2) * gz));
-                } else {
-                    v = field_init(gx, gy, gz, nx, ny, nz, seed, mode);
+        const int nrow = C.rows * (C.bz + 2);
+        for (int rr = blockIdx.x * nwarps + warp; rr < nrow; rr += gridDim.x * nwarps) {
+            const int kp = rr / C.rows, rp = rr - kp * C.rows;
+            const int jp = rp + 1 - C.row0;  // padded y index (a 2D chare's single row is row 1)
+            const int ghosts_yz = (jp == 0 || jp == C.by + 1) + (kp == 0 || kp == C.bz + 1);
+            const int64_t gy = C.y0 + jp + oy, gz = C.z0 + kp + oz;
+            double *a0 = C.A[0] + (int64_t)rr * C.pitch, *a1 = C.A[1] + (int64_t)rr * C.pitch;
+            for (int cp = lane; cp < C.pitch; cp += 32) {
+                double v = 0.0;
+                if (cp <= C.bx + 1 && ghosts_yz + (cp == 0 || cp == C.bx + 1) <= 1) {
+                    const int64_t gx = C.x0 + cp + ox;
+                    if (stencil == OD_STENCIL_2D5) {
+                        const bool shell = gx == 0 || gz == 0 || gx == nx + 1 || gz == nz + 1;
+                        if (shell || mode != 0) v = field_uniform(seed, (uint64_t)(gx + (nx + 2) * gz));
+                    } else {
+                        v = field_init(gx, gy, gz, nx, ny, nz, seed, mode);
+                    }
                 }
+                a0[cp] = v;
+                a1[cp] = v;
             }
-            C.A[0][e] = v;
-            C.A[1][e] = v;
         }
     }
 }
@@ -199,36 +187,48 @@ __global__ void k_face_copy(const ChareDev *ch, int nch, int p, int f, int dir, 
     }
 }
 
-// A11: interiors of parity p -> global x-fastest array.
+// A11: interiors of parity p -> global x-fastest array.  One warp per
+// interior row (coalesced on both sides), one 32-bit division per row.
 __global__ void k_gather(const ChareDev *ch, int nch, int p, int64_t nx, int64_t ny, double *g) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
-        const int64_t n = (int64_t)C.bx * C.by * C.bz;
+        const int nrow = C.by * C.bz;
         const int64_t plane = (int64_t)C.rows * C.pitch;
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-             e += (int64_t)gridDim.x * blockDim.x) {
-            const int i = (int)(e % C.bx);
-            const int64_t r = e / C.bx;
-            const int j = (int)(r % C.by), k = (int)(r / C.by);
-            g[(C.z0 + k) * ny * nx + (C.y0 + j) * nx + C.x0 + i] =
-                C.A[p][(k + 1) * plane + (int64_t)(j + C.row0) * C.pitch + i + 1];
+        for (int rr = blockIdx.x * nwarps + warp; rr < nrow; rr += gridDim.x * nwarps) {
+            const int k = rr / C.by, j = rr - k * C.by;
+            const double *src = C.A[p] + (k + 1) * plane + (int64_t)(j + C.row0) * C.pitch + 1;
+            double *dst = g + ((C.z0 + k) * ny + C.y0 + j) * nx + C.x0;
+            for (int i = lane; i < C.bx; i += 32) dst[i] = src[i];
         }
     }
 }
 
 // Import: global x-fastest interior -> interiors and internal ghost cells of
-// parity p (Dirichlet ghosts keep the shell).
+// parity p (ghosts on the context's own boundary keep their values: the
+// Dirichlet shell, or a shard's imported faces).  One warp per padded row;
+// edge and corner ghosts (never read) are skipped.
 __global__ void k_scatter(const ChareDev *ch, int nch, int p, int64_t nx, int64_t ny, int64_t nz,
                           const double *g) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
-        const int64_t na = (int64_t)(C.bz + 2) * C.rows * C.pitch;
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < na;
-             e += (int64_t)gridDim.x * blockDim.x) {
-            int64_t gx, gy, gz;
-            if (!padded_cell(C, e, &gx, &gy, &gz)) continue;
-            if (gx == 0 || gy == 0 || gz == 0 || gx == nx + 1 || gy == ny + 1 || gz == nz + 1) continue;
-            C.A[p][e] = g[(gz - 1) * ny * nx + (gy - 1) * nx + (gx - 1)];
+        const int nrow = C.rows * (C.bz + 2);
+        for (int rr = blockIdx.x * nwarps + warp; rr < nrow; rr += gridDim.x * nwarps) {
+            const int kp = rr / C.rows, rp = rr - kp * C.rows;
+            const int jp = rp + 1 - C.row0;  // padded y index (a 2D chare's single row is row 1)
+            const bool gy_ghost = jp == 0 || jp == C.by + 1, gz_ghost = kp == 0 || kp == C.bz + 1;
+            if (gy_ghost && gz_ghost) continue;
+            const int64_t gy = C.y0 + jp, gz = C.z0 + kp;
+            if (gy == 0 || gy == ny + 1 || gz == 0 || gz == nz + 1) continue;
+            double *dst = C.A[p] + (int64_t)rr * C.pitch;
+            const double *src = g + ((gz - 1) * ny + (gy - 1)) * nx - 1;
+            for (int cp = lane; cp < C.bx + 2; cp += 32) {
+                if ((gy_ghost || gz_ghost) && (cp == 0 || cp == C.bx + 1)) continue;
+                const int64_t gx = C.x0 + cp;
+                if (gx == 0 || gx == nx + 1) continue;
+                dst[cp] = src[gx];
+            }
         }
     }
 }

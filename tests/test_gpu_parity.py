@@ -113,6 +113,24 @@ def test_device_read_and_write(od):
         assert_bitexact(s.read(), want, "device write")
 
 
+def test_pinned_host_read_and_write(od):
+    # pinned host buffers are read and written in place by the I/O kernels
+    import torch
+    nx, ny, nz = 40, 33, 29
+    want = oracle.solve(nx, ny, nz, 3, 1, 6)
+    with od.Jacobi3D(nx, ny, nz, split=(2, 3, 1), seed=3, init_mode=1, path="fused") as s:
+        s.step(6)
+        h = torch.zeros(nx * ny * nz, dtype=torch.float64, pin_memory=True)
+        s.read(h.numpy())
+        assert_bitexact(h.numpy(), want, "pinned read")
+        s.write(h.numpy())
+        s.step(2)
+        assert_bitexact(s.read(), oracle.solve(nx, ny, nz, 3, 1, 8), "pinned write, then two steps")
+        view = torch.zeros(nx * ny * nz + 5, dtype=torch.float64, pin_memory=True)[3:3 + nx * ny * nz]
+        s.read(view.numpy())  # a pointer inside a pinned allocation
+        assert_bitexact(view.numpy(), oracle.solve(nx, ny, nz, 3, 1, 8), "pinned read at an offset")
+
+
 @pytest.mark.parametrize("shape", [
     dict(threads=128, cells_per_thread=2), dict(threads=128, cells_per_thread=8),
     dict(threads=256, cells_per_thread=1), dict(threads=256, cells_per_thread=8),
