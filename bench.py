@@ -170,8 +170,8 @@ def profiled_traffic(args, plan):
 
 
 # bumped whenever a tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 9      # 3D 7-point
-KERNEL_REV_2D = 10  # 2D 5-point
+KERNEL_REV = 10     # 3D 7-point
+KERNEL_REV_2D = 11  # 2D 5-point
 
 
 def combine_ranks(ms: float, updates: float, world: int, device: str):

@@ -226,15 +226,16 @@ OD_HD uint32_t clz32(uint32_t x) {
 }
 
 // Round W (whose top set bit is at 52 + p, p in [0, 11]) to 53 significant
-// bits, nearest even; returns p.
+// bits, nearest even; returns p.  With the p dropped bits r, half = 2^(p-1)
+// and the kept lowest bit l, adding half - 1 + l and truncating rounds up
+// exactly when r > half, or r == half and l == 1 (ties to even); for p = 0
+// nothing is dropped and the added amount, masked to p bits, is 0.
 OD_HD uint32_t round_window(uint64_t &W) {
     const uint32_t hi = (uint32_t)(W >> 32), lo = (uint32_t)W;
     const uint32_t p = 11u - clz32(hi);           // hi >= 2^20
-    const uint32_t unit = 1u << p;
-    const uint32_t rem = lo & (unit - 1u);
-    const uint32_t half = unit >> 1;
-    const uint32_t up = (uint32_t)(rem > half) | ((uint32_t)(rem == half) & (uint32_t)(p != 0u) & (lo >> p));
-    W = (W - rem) + ((uint64_t)(up & 1u) << p);
+    const uint32_t mask = (1u << p) - 1u;
+    const uint32_t bias = ((mask >> 1) + ((lo >> p) & 1u)) & mask;  // half - 1 + l (0 when p = 0)
+    W = (W + bias) & ~(uint64_t)mask;
     return p;
 }
 
