@@ -1,21 +1,22 @@
 // od_tile.cuh -- the tile sweep of libod (sm_103a), shared by the per-chare
 // compute kernel, the fused step kernel and the persistent kernel.
 //
-// A task is nj full rows x nk planes of one chare.  One elected thread issues,
-// per z-plane, a 1D bulk copy (cp.async.bulk, the TMA's untiled form) of the
-// tile's nj rows plus its two y-halo rows -- one contiguous run of the chare's
-// padded array -- and two small copies of that plane's x-ghost spans into a
-// ring slot whose mbarrier counts the transaction bytes; `stages` planes are
-// in flight.  Every thread owns the same cells of every plane and keeps the
-// z-1 value in registers, so a cell reads x-1, x+1, y-1, y+1, z+1 from shared
-// memory.  The new value is stored once to HBM, coalesced, and, on a chare
-// boundary, once more straight into the neighbour's ghost layer (the fused
-// paths' pack + delivery + unpack).
+// A 3D task is nj full rows x nk planes of one chare.  One elected thread
+// issues, per z-plane, a 1D bulk copy (cp.async.bulk, the TMA's untiled form)
+// of the tile's nj rows plus its two y-halo rows -- one contiguous run of the
+// chare's padded array that already holds the x-ghosts -- into a ring slot
+// whose mbarrier counts the transaction bytes.  The ring keeps planes k-1, k
+// and k+1 resident while plane k is computed, with the other `stages` - 3
+// slots in flight.  Every thread owns the same cells of every plane and reads
+// all six neighbours from shared memory.  The new value is stored once to
+// HBM, coalesced, and, on a chare boundary, once more straight into the
+// neighbour's ghost layer (the fused paths' pack + delivery + unpack).  The
+// 2D task (run_tile_2d) is a row segment over a run of rows, the same way.
 //
 // The arithmetic is the Jacobi update of the paper's stencil proxy (Sec. V,
-// "jacobi2d", here 3D 7-point) with round-to-nearest binary64 adds and
-// division and no contraction, which is what makes every path bit-identical
-// to an undecomposed sweep.
+// "jacobi2d"; 3D 7-point, or the paper's own 2D 5-point) with round-to-
+// nearest binary64 adds and division and no contraction, which is what makes
+// every path bit-identical to an undecomposed sweep.
 //
 // Every wait is bounded by KArgs::spin_ns (wall clock, %globaltimer): a wait
 // that runs out records an error and the CTA leaves after draining its own
