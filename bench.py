@@ -55,7 +55,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sweep", action="store_true",
-                    help="also time every path at ODF 1, 8, 64, 512, 4096 (adds a 'sweep' key)")
+                    help="also time every path at every ODF (adds a 'sweep' key; on by default for the odf "
+                         "workload at N=1)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the default ODF sweep")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default: od_create times candidate execution shapes first)")
     ap.add_argument("--threads", type=int, default=0)
@@ -478,6 +480,8 @@ def run_ours(args):
                     "kernels_per_step": (b1["kernel_launches"] - b0["kernel_launches"]) / args.baseline_steps}
 
     sweep = None
+    if args.workload == "odf" and world == 1 and not args.no_sweep:
+        args.sweep = True  # the metric is throughput vs ODF: sweep every path at every ODF
     if args.sweep and rank == 0 and two_d:
         sweep = []
         for o in (1, 4, 16, 64, 256, 1024, 4096):
