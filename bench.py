@@ -478,6 +478,11 @@ def run_ours(args):
                     "steps": args.baseline_steps,
                     "api_calls_per_step": (b1["api_calls"] - b0["api_calls"]) / args.baseline_steps,
                     "kernels_per_step": (b1["kernel_launches"] - b0["kernel_launches"]) / args.baseline_steps}
+        # the paper's runtime remedy: several host threads (PEs) submit the chares' work
+        for pe in (2, 4, 8):
+            ms_pe, _, _ = time_path(pkg, edge, odf, "per_chare", args.baseline_steps, 1, stream,
+                                    dict(device=dev, pe_threads=pe), make=make if two_d else None)
+            baseline[f"ms_per_step_pe{pe}"] = ms_pe
 
     sweep = None
     if args.workload == "odf" and world == 1 and not args.no_sweep:

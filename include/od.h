@@ -153,7 +153,10 @@ typedef struct od_config {
     uint64_t arena_bytes;        /* size of `arena` in bytes */
     uint64_t spin_limit_ns;      /* device-side wait limit (0 = 2 000 000 000) */
     int32_t stencil;             /* OD_STENCIL_3D7 (default) or OD_STENCIL_2D5 */
-    int32_t reserved;
+    int32_t pe_threads;          /* per-chare path: host threads that submit the
+                                    chares' work in parallel, each with its own
+                                    slice of the stream pool (the paper's several
+                                    PEs per GPU); 0 or 1 = the calling thread */
     /* A shard: this context holds the sub-box [gx0, gx0+nx) x [gy0, gy0+ny) x
      * [gz0, gz0+nz) of a global grid gnx x gny x gnz (gnx = 0: the context is
      * the whole grid).  The initial field, including every ghost layer, is the

@@ -40,7 +40,8 @@ def make_config(nx: int, ny: int, nz: int, *, split=(1, 1, 1), cuts=None, seed: 
                 tile_y: int = 0, tile_z: int = 0, threads: int = 0, cells_per_thread: int = 0,
                 stages: int = 0, arith: int = -1, order: int = 0, stream_pool: int = 0, device: int = 0,
                 stream: int | None = None, arena: int | None = None, arena_bytes: int = 0,
-                spin_limit_ns: int = 0, stencil: str | int = "3d7", gdims=None, goff=None):
+                spin_limit_ns: int = 0, stencil: str | int = "3d7", gdims=None, goff=None,
+                pe_threads: int = 0):
     """Build an od_config (returns (config, keepalive) -- keep both alive while
     the config is used, the cut arrays are referenced by pointer).  For the
     2D stencil ("2d5") nz is 1 and split / cuts may give two axes."""
@@ -52,6 +53,7 @@ def make_config(nx: int, ny: int, nz: int, *, split=(1, 1, 1), cuts=None, seed: 
         cuts = tuple(cuts) + (None,) * (3 - len(cuts))
     cfg.px, cfg.py, cfg.pz = (int(v) for v in split)
     cfg.stencil = STENCILS[stencil] if isinstance(stencil, str) else int(stencil)
+    cfg.pe_threads = int(pe_threads)
     if gdims is not None:  # a shard: this context is a sub-box of the global grid gdims at offset goff
         g = tuple(int(v) for v in gdims) + (1,) * (3 - len(gdims))
         o = tuple(int(v) for v in (goff or ())) + (0,) * (3 - len(goff or ()))

@@ -34,7 +34,7 @@ class od_config(ctypes.Structure):
         ("tile_y", _i32), ("tile_z", _i32), ("threads", _i32), ("cells_per_thread", _i32),
         ("stages", _i32), ("arith", _i32), ("order", _i32), ("stream_pool", _i32), ("device", _i32),
         ("stream", _vp), ("arena", _vp), ("arena_bytes", _u64), ("spin_limit_ns", _u64),
-        ("stencil", _i32), ("reserved", _i32),
+        ("stencil", _i32), ("pe_threads", _i32),
         ("gnx", _i64), ("gny", _i64), ("gnz", _i64), ("gx0", _i64), ("gy0", _i64), ("gz0", _i64),
     ]
 

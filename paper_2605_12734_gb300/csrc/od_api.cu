@@ -10,10 +10,12 @@
 #include <sys/stat.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "od.h"
@@ -135,11 +137,58 @@ od_status enqueue_persistent(od_ctx *c, int32_t iters) {
 // t&1 only after its own stream has waited (in phase B of step t+1) for the
 // receiver's step t+1 delivery, which its stream issued after the receiver's
 // step-t unpack.
+// Phase A of chare ci at step t on stream st (see above).
+cudaError_t per_chare_phase_a(od_ctx *c, int ci, int64_t t, cudaStream_t st, int64_t *kernels, int64_t *calls) {
+    const od::Plan &p = c->plan;
+    const int sp = (int)(t & 1), dp = sp ^ 1, slot = (int)(t & 1);
+    const od::HostChare &h = p.ch[(size_t)ci];
+    KArgs a = base_args_impl(c);
+    a.tile_begin = h.tile_begin;
+    a.parity = sp;
+    cudaError_t e = od::launch_tiles(a, h.tile_end - h.tile_begin, p.threads, p.cpt, p.amode, false, p.smem_bytes, st);
+    if (e == cudaSuccess) e = od::launch_pack(c->d_ch, ci, dp, h.foff[6], st);
+    if (e != cudaSuccess) return e;
+    (*kernels) += 2;
+    (*calls) += 2;
+    for (int f = 0; f < 6; ++f) {
+        const int n = h.nbr[f];
+        if (n < 0) continue;
+        const int opp = f ^ 1;
+        const ChareDev &dn = c->h_ch[(size_t)n];
+        const ChareDev &me = c->h_ch[(size_t)ci];
+        const size_t bytes = (size_t)(h.foff[f + 1] - h.foff[f]) * sizeof(double);
+        if (bytes == 0) continue;
+        e = cudaMemcpyAsync(dn.recv[slot] + dn.foff[opp], me.send + me.foff[f], bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return e;
+        (*calls)++;
+    }
+    (*calls)++;
+    return cudaEventRecord(c->ev[2 * (size_t)ci + slot], st);
+}
+
+// Phase B of chare ci at step t: wait for the neighbours' deliveries, unpack.
+cudaError_t per_chare_phase_b(od_ctx *c, int ci, int64_t t, cudaStream_t st, int64_t *kernels, int64_t *calls) {
+    const od::HostChare &h = c->plan.ch[(size_t)ci];
+    const int dp = (int)(t & 1) ^ 1, slot = (int)(t & 1);
+    bool any = false;
+    for (int f = 0; f < 6; ++f) {
+        const int n = h.nbr[f];
+        if (n < 0) continue;
+        any = true;
+        const cudaError_t e = cudaStreamWaitEvent(st, c->ev[2 * (size_t)n + slot], 0);
+        if (e != cudaSuccess) return e;
+        (*calls)++;
+    }
+    if (!any) return cudaSuccess;
+    (*kernels)++;
+    (*calls)++;
+    return od::launch_unpack(c->d_ch, ci, dp, slot, h.foff[6], st);
+}
+
 od_status enqueue_per_chare_steps(od_ctx *c, int64_t t_first, int32_t iters, int64_t *kernels,
                                   int64_t *calls) {
-    const od::Plan &p = c->plan;
     const int P = (int)c->pool.size();
-    const int nch = (int)p.ch.size();
+    const int nch = (int)c->plan.ch.size();
     OD_CUDA(cudaEventRecord(c->fork, c->stream));
     (*calls)++;
     for (int i = 0; i < P; ++i) {
@@ -148,48 +197,8 @@ od_status enqueue_per_chare_steps(od_ctx *c, int64_t t_first, int32_t iters, int
     }
     for (int32_t s = 0; s < iters; ++s) {
         const int64_t t = t_first + s;
-        const int sp = (int)(t & 1), dp = sp ^ 1, slot = (int)(t & 1);
-        for (int ci = 0; ci < nch; ++ci) {
-            const od::HostChare &h = p.ch[(size_t)ci];
-            cudaStream_t st = c->pool[ci % P];
-            KArgs a = base_args_impl(c);
-            a.tile_begin = h.tile_begin;
-            a.parity = sp;
-            OD_CUDA(od::launch_tiles(a, h.tile_end - h.tile_begin, p.threads, p.cpt, p.amode, false, p.smem_bytes, st));
-            OD_CUDA(od::launch_pack(c->d_ch, ci, dp, h.foff[6], st));
-            (*kernels) += 2;
-            (*calls) += 2;
-            for (int f = 0; f < 6; ++f) {
-                const int n = h.nbr[f];
-                if (n < 0) continue;
-                const int opp = f ^ 1;
-                const ChareDev &dn = c->h_ch[(size_t)n];
-                const ChareDev &me = c->h_ch[(size_t)ci];
-                size_t bytes = (size_t)(h.foff[f + 1] - h.foff[f]) * sizeof(double);
-                OD_CUDA(cudaMemcpyAsync(dn.recv[slot] + dn.foff[opp], me.send + me.foff[f], bytes,
-                                        cudaMemcpyDeviceToDevice, st));
-                (*calls)++;
-            }
-            OD_CUDA(cudaEventRecord(c->ev[2 * (size_t)ci + slot], st));
-            (*calls)++;
-        }
-        for (int ci = 0; ci < nch; ++ci) {
-            const od::HostChare &h = p.ch[(size_t)ci];
-            cudaStream_t st = c->pool[ci % P];
-            bool any = false;
-            for (int f = 0; f < 6; ++f) {
-                const int n = h.nbr[f];
-                if (n < 0) continue;
-                any = true;
-                OD_CUDA(cudaStreamWaitEvent(st, c->ev[2 * (size_t)n + slot], 0));
-                (*calls)++;
-            }
-            if (any) {
-                OD_CUDA(od::launch_unpack(c->d_ch, ci, dp, slot, h.foff[6], st));
-                (*kernels)++;
-                (*calls)++;
-            }
-        }
+        for (int ci = 0; ci < nch; ++ci) OD_CUDA(per_chare_phase_a(c, ci, t, c->pool[ci % P], kernels, calls));
+        for (int ci = 0; ci < nch; ++ci) OD_CUDA(per_chare_phase_b(c, ci, t, c->pool[ci % P], kernels, calls));
     }
     for (int i = 0; i < P; ++i) {
         OD_CUDA(cudaEventRecord(c->join[i], c->pool[i]));
@@ -199,7 +208,83 @@ od_status enqueue_per_chare_steps(od_ctx *c, int64_t t_first, int32_t iters, int
     return OD_OK;
 }
 
+// A reusable barrier for the submitting host threads (spin, then yield).
+class HostBarrier {
+  public:
+    explicit HostBarrier(int n) : n_(n) {}
+    void wait() {
+        const int64_t g = gen_.load(std::memory_order_acquire);
+        if (count_.fetch_add(1, std::memory_order_acq_rel) + 1 == n_) {
+            count_.store(0, std::memory_order_relaxed);
+            gen_.store(g + 1, std::memory_order_release);
+            return;
+        }
+        for (int spin = 0; gen_.load(std::memory_order_acquire) == g; ++spin)
+            if (spin > 256) std::this_thread::yield();
+    }
+
+  private:
+    const int n_;
+    std::atomic<int> count_{0};
+    std::atomic<int64_t> gen_{0};
+};
+
+// The per-chare path submitted by T host threads (the paper's several PEs
+// per GPU, Sec. III): thread k owns a contiguous block of chares and its own
+// slice of the stream pool.  Phase A of a step (every chare's records) must
+// be issued before any phase-B wait on those events, so the threads meet at
+// a barrier between the phases and after each step.
+od_status enqueue_per_chare_mt(od_ctx *c, int32_t iters, int T) {
+    const int P = (int)c->pool.size();
+    const int nch = (int)c->plan.ch.size();
+    T = std::max(1, std::min({T, P, nch}));
+    OD_CUDA(cudaEventRecord(c->fork, c->stream));
+    for (int i = 0; i < P; ++i) OD_CUDA(cudaStreamWaitEvent(c->pool[i], c->fork, 0));
+    int64_t calls_all = 1 + P;
+    HostBarrier bar(T);
+    std::atomic<int> failed{0};
+    std::vector<cudaError_t> err((size_t)T, cudaSuccess);
+    std::vector<int64_t> kern((size_t)T, 0), calls((size_t)T, 0);
+    const int64_t t_first = c->steps;
+    auto work = [&](int k) {
+        const int c0 = (int)((int64_t)nch * k / T), c1 = (int)((int64_t)nch * (k + 1) / T);
+        const int s0 = P * k / T, ns = std::max(1, P * (k + 1) / T - s0);
+        cudaError_t e = cudaSetDevice(c->device);
+        for (int32_t s = 0; s < iters; ++s) {
+            const int64_t t = t_first + s;
+            for (int ci = c0; ci < c1 && e == cudaSuccess && !failed.load(); ++ci)
+                e = per_chare_phase_a(c, ci, t, c->pool[s0 + (ci - c0) % ns], &kern[k], &calls[k]);
+            if (e != cudaSuccess) failed.store(1);
+            bar.wait();  // every record of this step is issued before any wait on it
+            for (int ci = c0; ci < c1 && e == cudaSuccess && !failed.load(); ++ci)
+                e = per_chare_phase_b(c, ci, t, c->pool[s0 + (ci - c0) % ns], &kern[k], &calls[k]);
+            if (e != cudaSuccess) failed.store(1);
+            bar.wait();
+        }
+        err[(size_t)k] = e;
+    };
+    std::vector<std::thread> th;
+    for (int k = 1; k < T; ++k) th.emplace_back(work, k);
+    work(0);
+    for (auto &x : th) x.join();
+    for (int k = 0; k < T; ++k)
+        if (err[(size_t)k] != cudaSuccess) return cuda_fail(err[(size_t)k], "per-chare submission");
+    for (int i = 0; i < P; ++i) {
+        OD_CUDA(cudaEventRecord(c->join[i], c->pool[i]));
+        OD_CUDA(cudaStreamWaitEvent(c->stream, c->join[i], 0));
+    }
+    calls_all += 2 * P;
+    for (int k = 0; k < T; ++k) {
+        c->launches += kern[(size_t)k];
+        calls_all += calls[(size_t)k];
+    }
+    c->api_calls += calls_all;
+    c->steps += iters;
+    return OD_OK;
+}
+
 od_status enqueue_per_chare(od_ctx *c, int32_t iters) {
+    if (c->cfg.pe_threads > 1) return enqueue_per_chare_mt(c, iters, c->cfg.pe_threads);
     int64_t k = 0, calls = 0;
     od_status s = enqueue_per_chare_steps(c, c->steps, iters, &k, &calls);
     c->launches += k;

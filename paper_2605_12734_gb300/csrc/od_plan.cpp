@@ -121,6 +121,10 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         *err = "unknown path";
         return OD_EINVAL;
     }
+    if (cfg->pe_threads < 0 || cfg->pe_threads > 64) {
+        *err = "pe_threads must be in [0, 64]";
+        return OD_EINVAL;
+    }
     if (cfg->order < 0 || cfg->order > 3) {
         *err = "order must be 0..3 (bit 0: reverse on odd steps, bit 1: Morton order of the chares)";
         return OD_EINVAL;

@@ -111,6 +111,7 @@ def test_plan_model_bytes(od, odf):
     dict(split=(1, 1, 1), dims=(4, 4, 4), stages=9),
     dict(split=(1, 1, 1), dims=(4, 4, 4), stages=2),
     dict(split=(1, 1, 1), dims=(4, 4, 4), order=4),
+    dict(split=(1, 1, 1), dims=(4, 4, 4), pe_threads=65),
     dict(split=(1, 1, 1), dims=(8192, 4, 4)),       # row wider than any CTA can hold
     dict(split=(1, 1, 1), dims=(600, 4, 4), threads=128, cells_per_thread=4),  # 600 > 512
     dict(cuts=([0, 3, 2, 8], None, None), dims=(8, 4, 4)),  # not ascending

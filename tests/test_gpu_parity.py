@@ -113,6 +113,20 @@ def test_device_read_and_write(od):
         assert_bitexact(s.read(), want, "device write")
 
 
+@pytest.mark.parametrize("pe", [2, 3, 8])
+def test_per_chare_with_several_submitting_threads(od, pe):
+    # the per-chare path submitted by several host threads (the paper's PEs)
+    nx, ny, nz = 70, 45, 38
+    cuts = ([0, 13, 40, 70], [0, 24, 45], [0, 5, 6, 38])
+    want = oracle.solve(nx, ny, nz, 8, 1, 9)
+    with od.Jacobi3D(nx, ny, nz, cuts=cuts, seed=8, init_mode=1, path="per_chare", pe_threads=pe,
+                     stream_pool=6) as s:
+        s.step(4)
+        s.step(5)
+        assert_bitexact(s.read(), want, f"pe_threads={pe}")
+        assert s.stats()["steps_done"] == 9
+
+
 def test_pinned_host_read_and_write(od):
     # pinned host buffers are read and written in place by the I/O kernels
     import torch
