@@ -429,7 +429,9 @@ OD_API od_status od_server_wait(od_server *s, uint64_t job_id, double timeout_s,
 OD_API od_status od_server_job_info(od_server *s, uint64_t job_id, od_job_info *out);
 /* Copy a done job's field (nx*ny*nz doubles, x fastest) to dst (device or host). */
 OD_API od_status od_server_fetch(od_server *s, uint64_t job_id, double *dst, int32_t dst_is_device);
-/* Forget a job that is done, failed or still queued, returning its memory to the pool. */
+/* Forget a job that is done, failed or still queued, returning its memory to
+ * the pool.  OD_ESTATE while it runs, and in the short window in which the
+ * admission thread is creating its context (release it after it has run). */
 OD_API od_status od_server_release(od_server *s, uint64_t job_id);
 OD_API od_status od_server_stats(od_server *s, od_server_stats_t *out);
 /* Stop the worker (after the launches in flight) and free everything. */

@@ -97,6 +97,7 @@ struct Job {
     int32_t iters = 0;
     int64_t steps_enq = 0;      // steps enqueued on the device
     int state = OD_JOB_QUEUED;
+    bool admitting = false;     // out of the queue, its context being created (lock released)
     double t_submit = 0, t_admit = 0, t_done = 0;
     size_t off = 0, bytes = 0;
     od_ctx *ctx = nullptr;
@@ -176,6 +177,7 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
         size_t off = 0;
         if (!s->pool.alloc(j->bytes, &off)) return progress;  // wait for memory
         s->queue.pop_front();
+        j->admitting = true;
         j->off = off;
         od_config c = job_config(s, j);
         c.arena = s->pool_base + off;
@@ -186,6 +188,7 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
         od_status st = od_create(&ctx, &c);
         std::string msg = st == OD_OK ? "" : od_last_error();
         lk.lock();
+        j->admitting = false;
         s->admit_seconds += s->now() - t_create;
         progress = true;
         if (st != OD_OK || ctx->plan.stage_doubles * s->stages * 8 + 256 > s->smem_cap) {
@@ -468,7 +471,11 @@ od_status od_server_release(od_server *s, uint64_t id) {
     Job *j = find(s, id);
     if (!j) return fail(OD_ENOTFOUND, "unknown job");
     if (j->state == OD_JOB_RUNNING) return fail(OD_ESTATE, "job still running");
-    if (j->state == OD_JOB_QUEUED) s->queue.erase(std::find(s->queue.begin(), s->queue.end(), j));
+    if (j->admitting) return fail(OD_ESTATE, "job is being admitted; release it once it has run");
+    if (j->state == OD_JOB_QUEUED) {
+        auto it = std::find(s->queue.begin(), s->queue.end(), j);
+        if (it != s->queue.end()) s->queue.erase(it);
+    }
     od_ctx *ctx = j->ctx;
     const bool had_memory = ctx != nullptr;
     s->jobs.erase(id);
