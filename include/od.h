@@ -1,6 +1,6 @@
 /*
- * od.h -- C ABI of libod: an overdecomposed 3D 7-point FP64 Jacobi solver on
- * one GPU (sm_103a).
+ * od.h -- C ABI of libod: an overdecomposed FP64 Jacobi solver (3D 7-point,
+ * and the paper's own 2D 5-point) on one GPU (sm_103a).
  *
  * The method (the paper's Sec. III "Managing Overdecomposition" and Sec. V
  * "jacobi2d"): the grid is cut into many more blocks ("chares") than there are
@@ -46,7 +46,10 @@
  *     allocates and frees it in od_destroy;
  *   - work is enqueued on the context's stream; od_read, od_sync and od_stats
  *     synchronise that stream and report device-side errors (OD_ETIMEOUT for a
- *     bounded wait that ran out, OD_ECUDA for a CUDA error).
+ *     bounded wait that ran out, OD_ECUDA for a CUDA error);
+ *   - one context is used by one host thread at a time (calls on the same
+ *     od_ctx must not overlap); different contexts, and every od_server_*
+ *     call, may be used from any threads concurrently.
  */
 #ifndef OD_H
 #define OD_H
