@@ -330,7 +330,12 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
+    # one rank per node compiles (if anything is stale); the others wait for it
+    if world > 1 and local != 0:
+        dist.barrier()
     od_build.build()
+    if world > 1 and local == 0:
+        dist.barrier()
     dev = local
     if args.workload == "serve":
         return run_serve(args, pkg, torch, rank, world, dev)
