@@ -432,6 +432,12 @@ OD_API od_status od_server_wait(od_server *s, uint64_t job_id, double timeout_s,
 OD_API od_status od_server_job_info(od_server *s, uint64_t job_id, od_job_info *out);
 /* Copy a done job's field (nx*ny*nz doubles, x fastest) to dst (device or host). */
 OD_API od_status od_server_fetch(od_server *s, uint64_t job_id, double *dst, int32_t dst_is_device);
+/* Short names of the serving loop: od_submit = od_server_submit, od_fetch =
+ * od_server_fetch; od_poll sets *done = 1 once the job is done or failed (0
+ * while it is queued or running) without waiting. */
+OD_API od_status od_submit(od_server *s, const od_config *job, int32_t iters, uint64_t *job_id);
+OD_API od_status od_poll(od_server *s, uint64_t job_id, int32_t *done);
+OD_API od_status od_fetch(od_server *s, uint64_t job_id, double *dst, int32_t dst_is_device);
 /* Forget a job that is done, failed or still queued, returning its memory to
  * the pool.  OD_ESTATE while it runs, and in the short window in which the
  * admission thread is creating its context (release it after it has run). */

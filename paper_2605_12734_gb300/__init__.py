@@ -360,6 +360,12 @@ class Server:
         self._sizes[jid.value] = int(nx) * int(ny) * int(nz)
         return jid.value
 
+    def poll(self, job: int) -> bool:
+        """True once the job is done or failed (od_poll, no waiting)."""
+        done = ctypes.c_int32()
+        check(lib().od_poll(self._h, int(job), ctypes.byref(done)), "od_poll")
+        return bool(done.value)
+
     def wait(self, job: int, timeout_s: float = 60.0) -> int:
         st = ctypes.c_int32()
         check(lib().od_server_wait(self._h, job, float(timeout_s), ctypes.byref(st)), "od_server_wait")

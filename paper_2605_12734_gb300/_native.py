@@ -114,6 +114,9 @@ SIGNATURES = {
     "od_server_release": (_i32, [_vp, _u64]),
     "od_server_stats": (_i32, [_vp, ctypes.POINTER(od_server_stats_t)]),
     "od_server_destroy": (_i32, [_vp]),
+    "od_submit": (_i32, [_vp, ctypes.POINTER(od_config), _i32, ctypes.POINTER(_u64)]),
+    "od_poll": (_i32, [_vp, _u64, ctypes.POINTER(_i32)]),
+    "od_fetch": (_i32, [_vp, _u64, _vp, _i32]),
     "od_jacobi_noalloc": (_i32, [_vp, _vp, _i64, _i64, _i64, _i32, _vp]),
     "od_bench_launch_latency": (_i32, [_i32, _i32, _i32, ctypes.POINTER(ctypes.c_double)]),
     "od_bench_release": (_i32, [_i32, _i64, _i32, _i32, _vp, ctypes.POINTER(ctypes.c_double)]),

@@ -427,13 +427,35 @@ od_status od_server_submit(od_server *s, const od_config *job, int32_t iters, ui
 od_status od_server_wait(od_server *s, uint64_t id, double timeout_s, int32_t *state) {
     if (!s) return fail(OD_EINVAL, "null server");
     std::unique_lock<std::mutex> lk(s->mu);
+    const auto until = Clock::now() + std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s);
+    for (;;) {
+        Job *j = find(s, id);  // looked up again after every wake: another thread may release it
+        if (!j) return fail(OD_ENOTFOUND, "unknown job");
+        if ((j->state != OD_JOB_QUEUED && j->state != OD_JOB_RUNNING) ||
+            s->cv_done.wait_until(lk, until) == std::cv_status::timeout) {
+            j = find(s, id);
+            if (!j) return fail(OD_ENOTFOUND, "unknown job");
+            if (state) *state = j->state;
+            return OD_OK;
+        }
+    }
+}
+
+od_status od_submit(od_server *s, const od_config *job, int32_t iters, uint64_t *job_id) {
+    return od_server_submit(s, job, iters, job_id);
+}
+
+od_status od_poll(od_server *s, uint64_t id, int32_t *done) {
+    if (!s || !done) return fail(OD_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
     Job *j = find(s, id);
     if (!j) return fail(OD_ENOTFOUND, "unknown job");
-    const auto until = Clock::now() + std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s);
-    while (j->state == OD_JOB_QUEUED || j->state == OD_JOB_RUNNING)
-        if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout) break;
-    if (state) *state = j->state;
+    *done = j->state == OD_JOB_DONE || j->state == OD_JOB_FAILED;
     return OD_OK;
+}
+
+od_status od_fetch(od_server *s, uint64_t id, double *dst, int32_t dst_is_device) {
+    return od_server_fetch(s, id, dst, dst_is_device);
 }
 
 od_status od_server_job_info(od_server *s, uint64_t id, od_job_info *out) {

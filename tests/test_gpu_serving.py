@@ -112,3 +112,24 @@ def test_autotune_same_bits_and_cache(od, tmp_path, monkeypatch):
         assert abs(s2.stats()["tune_ms_per_step"] - st["tune_ms_per_step"]) < 1e-9  # from the cache
         assert s2.stats()["plan"]["threads"] == st["plan"]["threads"]
     assert len((tmp_path / "tune.txt").read_text().splitlines()) == 1
+
+
+def test_short_serving_names(od):
+    # od_submit / od_poll / od_fetch: the serving loop's short entry points
+    import ctypes
+    import time
+    from paper_2605_12734_gb300 import _native
+    e, it = 40, 7
+    want = oracle.solve(e, e, e, 9, 1, it)
+    with od.Server(256 << 20) as srv:
+        cfg, keep = od.make_config(e, e, e, split=(2, 2, 2), seed=9, init_mode=1)
+        jid = ctypes.c_uint64()
+        assert od.lib().od_submit(srv._h, ctypes.byref(cfg), it, ctypes.byref(jid)) == _native.OD_OK
+        t0 = time.time()
+        while not srv.poll(jid.value):
+            assert time.time() - t0 < 60
+            time.sleep(0.001)
+        got = np.empty(e ** 3)
+        assert od.lib().od_fetch(srv._h, jid.value, got.ctypes.data, 0) == _native.OD_OK
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+        srv.release(jid.value)
