@@ -218,6 +218,17 @@ OD_API od_status od_plan(const od_config *cfg, od_plan_info *out);
  * arrays hold. */
 OD_API od_status od_decompose(const od_config *cfg, int64_t *box, int32_t *nbr, int64_t capacity);
 
+/* The persistent path's schedule, host-only: the tiles of a configuration
+ * and, per tile, the tiles it waits for (CSR).  *ntiles and *ndeps are always
+ * set; tiles[8t..8t+7] = chare, x0, nx, y0, ny, z0, nz, 0 (the tile's box in
+ * the context's interior coordinates; a 2D grid appears as (nx, 1, ny)) is
+ * written when tiles_cap >= *ntiles, and dep_ptr (ntiles+1 entries) and
+ * dep_idx when, in addition, deps_cap >= *ndeps.  Tile b is in tile a's list
+ * iff a 7-point update of a's cells reads b's cells or the other way round:
+ * the boxes overlap, or touch across a face. */
+OD_API od_status od_plan_tiles(const od_config *cfg, int64_t *tiles, int64_t tiles_cap, int32_t *dep_ptr,
+                               int32_t *dep_idx, int64_t deps_cap, int64_t *ntiles, int64_t *ndeps);
+
 /* Allocate device state on cfg->device, build the chare/tile tables, tune if
  * asked, and write the initial field (u^0) including every ghost layer.
  * Synchronous.  *out is NULL on error. */

@@ -101,6 +101,21 @@ def decompose(nx, ny, nz, **kw):
     return box, nbr
 
 
+def plan_tiles(nx, ny, nz, **kw):
+    """The persistent schedule, host-only: tiles (n, 7: chare, x0, nx, y0, ny,
+    z0, nz) and the dependency CSR (dep_ptr, dep_idx)."""
+    cfg, keep = make_config(nx, ny, nz, **kw)
+    nt, nd = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().od_plan_tiles(ctypes.byref(cfg), None, 0, None, None, 0, ctypes.byref(nt), ctypes.byref(nd)),
+          "od_plan_tiles")
+    tiles = np.zeros((nt.value, 8), dtype=np.int64)
+    ptr = np.zeros(nt.value + 1, dtype=np.int32)
+    idx = np.zeros(max(nd.value, 1), dtype=np.int32)
+    check(lib().od_plan_tiles(ctypes.byref(cfg), tiles.ctypes.data, nt.value, ptr.ctypes.data, idx.ctypes.data,
+                              nd.value, ctypes.byref(nt), ctypes.byref(nd)), "od_plan_tiles")
+    return tiles[:, :7], ptr, idx[:nd.value]
+
+
 def arith_host(op: int, a: np.ndarray, b: np.ndarray | None = None) -> np.ndarray:
     """Run the kernels' exact integer-pipe arithmetic on the host: op 0
     a/6, op 1 a+b, op 10+m the 3D Jacobi update in arithmetic mode m over six

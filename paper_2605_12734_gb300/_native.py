@@ -95,6 +95,8 @@ SIGNATURES = {
     "od_config_default": (None, [ctypes.POINTER(od_config)]),
     "od_plan": (_i32, [ctypes.POINTER(od_config), ctypes.POINTER(od_plan_info)]),
     "od_decompose": (_i32, [ctypes.POINTER(od_config), ctypes.POINTER(_i64), ctypes.POINTER(_i32), _i64]),
+    "od_plan_tiles": (_i32, [ctypes.POINTER(od_config), _vp, _i64, _vp, _vp, _i64, ctypes.POINTER(_i64),
+                             ctypes.POINTER(_i64)]),
     "od_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(od_config)]),
     "od_step": (_i32, [_vp, _i32]),
     "od_set_path": (_i32, [_vp, _i32]),

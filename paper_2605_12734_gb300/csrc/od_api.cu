@@ -694,6 +694,34 @@ od_status od_plan(const od_config *cfg, od_plan_info *out) {
     return OD_OK;
 }
 
+od_status od_plan_tiles(const od_config *cfg, int64_t *tiles, int64_t tiles_cap, int32_t *dep_ptr,
+                        int32_t *dep_idx, int64_t deps_cap, int64_t *ntiles, int64_t *ndeps) {
+    if (!cfg || !ntiles || !ndeps) return fail(OD_EINVAL, "null argument");
+    od::Plan p;
+    std::string err;
+    od_status s = od::build_plan(cfg, &p, &err);
+    if (s != OD_OK) return fail(s, err);
+    *ntiles = (int64_t)p.tiles.size();
+    *ndeps = (int64_t)p.dep_idx.size();
+    if (tiles && tiles_cap >= *ntiles) {
+        for (size_t t = 0; t < p.tiles.size(); ++t) {
+            const TileDev &T = p.tiles[t];
+            const od::HostChare &h = p.ch[(size_t)T.c];
+            int64_t *o = tiles + 8 * t;
+            o[0] = T.c;
+            o[1] = h.x0 + T.i0; o[2] = T.ni;
+            o[3] = h.y0 + T.j0; o[4] = T.nj;
+            o[5] = h.z0 + T.k0; o[6] = T.nk;
+            o[7] = 0;
+        }
+    }
+    if (dep_ptr && dep_idx && tiles_cap >= *ntiles && deps_cap >= *ndeps) {
+        std::copy(p.dep_ptr.begin(), p.dep_ptr.end(), dep_ptr);
+        std::copy(p.dep_idx.begin(), p.dep_idx.end(), dep_idx);
+    }
+    return OD_OK;
+}
+
 od_status od_decompose(const od_config *cfg, int64_t *box, int32_t *nbr, int64_t capacity) {
     if (!cfg || !box || !nbr) return fail(OD_EINVAL, "null argument");
     od::Plan p;
