@@ -406,9 +406,10 @@ def run_ours(args):
     # the adds on the FP64 pipe and the rest, with the division, exactly on
     # the integer pipes.
     if two_d:  # 3 adds; modes 4..6 all run the three adds in the window
-        fp64_adds = {0: 3, 1: 3, 2: 2, 3: 1, 4: 0, 5: 0, 6: 0, 7: 1.5, 8: 1.75}[plan["arith"]]
+        fp64_adds = {0: 3, 1: 3, 2: 2, 3: 1, 4: 0, 5: 0, 6: 0, 7: 1.5, 8: 1.75, 9: 2, 10: 1, 11: 1.5}[plan["arith"]]
     else:
-        fp64_adds = {0: 5, 1: 5, 2: 4, 3: 3, 4: 2, 5: 1, 6: 0, 7: 3.5, 8: 3.75}[plan["arith"]]
+        fp64_adds = {0: 5, 1: 5, 2: 4, 3: 3, 4: 2, 5: 1, 6: 0, 7: 3.5, 8: 3.75, 9: 4, 10: 3,
+                     11: 3.5}[plan["arith"]]
     fpu = FLOPS_PER_UPDATE_2D if two_d else FLOPS_PER_UPDATE
     fp64_pipe = FP64_LANES_PER_SM * SMS * SM_MAX_GHZ  # G FP64 instructions/s
     hbm_peak, peak_kind = measured_peaks()

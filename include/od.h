@@ -142,7 +142,11 @@ typedef struct od_config {
                                     1+k (k = 1..5) also the first k adds on the
                                     integer pipes; 7 / 8: modes 2 and 3 mixed
                                     cell by cell (half / a quarter of the cells
-                                    in mode 3); -1 = library default (7) */
+                                    in mode 3); 9 / 10: the last one / two adds
+                                    on the integer pipes and the division taken
+                                    from their result; 11: 9 and 10 mixed cell
+                                    by cell; -1 = library default (7; 2 for the
+                                    2D stencil) */
     int32_t order;               /* persistent path task order, bits: 1 = reversed
                                     on odd steps, 2 = chares in Morton (Z) order
                                     instead of x-fastest; 0..3 */
@@ -290,9 +294,10 @@ OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
  * op 1: out[i] = a[i] + b[i] (b unused for op 0); op 2 / 3: the same on the
  * FP64 pipe (device only); op 10+m (m = 0..6): the whole Jacobi update
  * (((((a0+a1)+a2)+a3)+a4)+a5)/6 of the six operands a[6i..6i+5] in
- * arithmetic mode m (see od_config.arith), b unused; op 20+m (m = 0..4): the
- * 2D update (((a0+a1)+a2)+a3)/4 of a[4i..4i+3] in mode m (m = 4: three window
- * adds).  od_arith_host runs the routines on the host CPU
+ * arithmetic mode m (see od_config.arith), b unused; op 17 / 18: the same
+ * update in the tail form with one / two window adds (modes 9 and 10); op
+ * 20+m (m = 0..4): the 2D update (((a0+a1)+a2)+a3)/4 of a[4i..4i+3] in mode m
+ * (m = 4: three window adds); op 25 / 26: its tail form.  od_arith_host runs the routines on the host CPU
  * over host arrays; od_arith_device runs them in a kernel over device arrays
  * of the current device and synchronises.  n >= 0 elements. */
 OD_API od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n);

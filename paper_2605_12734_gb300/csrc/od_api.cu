@@ -514,7 +514,7 @@ od_status run_tuning(const od_config *cfg, TuneChoice *best) {
     if (tune_cache_lookup(key, best)) return OD_OK;
 
     const int shapes[6][2] = {{128, 4}, {128, 8}, {256, 4}, {256, 8}, {128, 2}, {256, 2}};
-    const int ariths[4] = {2, 3, 7, 8};
+    const int ariths[5] = {2, 7, 8, 10, 11};
     std::vector<TuneChoice> round1;
     for (auto &sh : shapes)
         for (int am : ariths) {
@@ -664,8 +664,8 @@ void od_config_default(od_config *cfg) {
 
 od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n) {
     if (n < 0 || (n > 0 && (!a || !out || (op == 1 && !b)))) return fail(OD_EINVAL, "bad arguments");
-    if (op != 0 && op != 1 && !(op >= 10 && op <= 16) && !(op >= 20 && op <= 24))
-        return fail(OD_EINVAL, "host op must be 0 (div6), 1 (add), 10..16 (3D update) or 20..24 (2D update)");
+    if (op != 0 && op != 1 && !(op >= 10 && op <= 18) && !(op >= 20 && op <= 26))
+        return fail(OD_EINVAL, "host op must be 0 (div6), 1 (add), 10..18 (3D update) or 20..26 (2D update)");
     for (int64_t i = 0; i < n; ++i)
         out[i] = op == 0   ? od::div6(a[i])
                  : op == 1 ? od::add(a[i], b[i])
@@ -676,8 +676,8 @@ od_status od_arith_host(int32_t op, const double *a, const double *b, double *ou
 
 od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n) {
     if (n < 0 || (n > 0 && (!a || !out || ((op == 1 || op == 3) && !b)))) return fail(OD_EINVAL, "bad arguments");
-    if (!((op >= 0 && op <= 3) || (op >= 10 && op <= 16) || (op >= 20 && op <= 24)))
-        return fail(OD_EINVAL, "op must be 0..3, 10..16 or 20..24");
+    if (!((op >= 0 && op <= 3) || (op >= 10 && op <= 18) || (op >= 20 && op <= 26)))
+        return fail(OD_EINVAL, "op must be 0..3, 10..18 or 20..26");
     if (n == 0) return OD_OK;
     OD_CUDA(od::launch_arith(op, a, b, out, n, 0));
     OD_CUDA(cudaStreamSynchronize(0));

@@ -366,6 +366,38 @@ OD_HD double jacobi_update(double W, double E, double S, double N, double D, dou
     return ok ? v : jacobi_update_ieee<false>(W, E, S, N, D, U);
 }
 
+// The update with its LAST KT adds (KT = 1 or 2) in the window chain and the
+// division by 6 taken straight from the window word: the first 5-KT adds are
+// IEEE operations (FP64 pipe), their sum s joins the remaining operands in the
+// window, and the rounded window value is divided without being packed into
+// a double and unpacked again.  ok = false when the window's domain is left.
+template <int KT>
+OD_HD double jacobi_update_tail(double W, double E, double S, double N, double D, double U, bool &ok) {
+    static_assert(KT == 1 || KT == 2, "one or two adds in the tail");
+    double s = ieee_add(W, E);
+    s = ieee_add(s, S);
+    s = ieee_add(s, N);
+    bool good;
+    uint32_t emax, p;
+    uint64_t Wd;
+    if constexpr (KT == 1) {
+        const double x[2] = {ieee_add(s, D), U};
+        Wd = window_chain<1>(x, good, emax, p);
+    } else {
+        const double x[3] = {s, D, U};
+        Wd = window_chain<2>(x, good, emax, p);
+    }
+    ok = good;
+    return div6_window(Wd, emax, p);
+}
+
+template <int KT>
+OD_HD double jacobi_update_tail_checked(double W, double E, double S, double N, double D, double U) {
+    bool ok;
+    const double v = jacobi_update_tail<KT>(W, E, S, N, D, U, ok);
+    return ok ? v : jacobi_update_ieee<false>(W, E, S, N, D, U);
+}
+
 // ---------------------------------------------------------------- 2D update
 //
 // The paper's own application: the 5-point update (((W+E)+S)+N)/4.  Division
@@ -430,19 +462,54 @@ OD_HD double jacobi2d_update(double W, double E, double S, double N) {
     return ok ? v : jacobi2d_update_ieee<false>(W, E, S, N);
 }
 
+// The 2D update with its last KT adds (1 or 2) in the window; the division
+// by 4 lowers the window value's exponent by two as it is packed (the window
+// domain keeps the quotient normal).
+template <int KT>
+OD_HD double jacobi2d_update_tail(double W, double E, double S, double N, bool &ok) {
+    static_assert(KT == 1 || KT == 2, "one or two adds in the tail");
+    const double s = ieee_add(W, E);
+    bool good;
+    uint32_t emax, p;
+    uint64_t Wd;
+    if constexpr (KT == 1) {
+        const double x[2] = {ieee_add(s, S), N};
+        Wd = window_chain<1>(x, good, emax, p);
+    } else {
+        const double x[3] = {s, S, N};
+        Wd = window_chain<2>(x, good, emax, p);
+    }
+    ok = good;
+    return pack_window(Wd, emax - 2u, p);
+}
+
+template <int KT>
+OD_HD double jacobi2d_update_tail_checked(double W, double E, double S, double N) {
+    bool ok;
+    const double v = jacobi2d_update_tail<KT>(W, E, S, N, ok);
+    return ok ? v : jacobi2d_update_ieee<false>(W, E, S, N);
+}
+
+// Run-time dispatch of the 2D update (tests): 0..4 head modes, 5 / 6 the
+// tail form with one / two window adds.
 OD_HD double jacobi2d_update_mode(int am, const double *x) {
     switch (am) {
         case 0: return jacobi2d_update<0>(x[0], x[1], x[2], x[3]);
         case 1: return jacobi2d_update<1>(x[0], x[1], x[2], x[3]);
         case 2: return jacobi2d_update<2>(x[0], x[1], x[2], x[3]);
         case 3: return jacobi2d_update<3>(x[0], x[1], x[2], x[3]);
+        case 5: return jacobi2d_update_tail_checked<1>(x[0], x[1], x[2], x[3]);
+        case 6: return jacobi2d_update_tail_checked<2>(x[0], x[1], x[2], x[3]);
         default: return jacobi2d_update<4>(x[0], x[1], x[2], x[3]);
     }
 }
 
-// Run-time dispatch of jacobi_update (tests).
+// Run-time dispatch of jacobi_update (tests): 0..6 head modes, 7 / 8 the
+// tail form with one / two window adds.
 OD_HD double jacobi_update_mode(int am, const double *x) {
     switch (am) {
+        case 7: return jacobi_update_tail_checked<1>(x[0], x[1], x[2], x[3], x[4], x[5]);
+        case 8: return jacobi_update_tail_checked<2>(x[0], x[1], x[2], x[3], x[4], x[5]);
         case 0: return jacobi_update<0>(x[0], x[1], x[2], x[3], x[4], x[5]);
         case 1: return jacobi_update<1>(x[0], x[1], x[2], x[3], x[4], x[5]);
         case 2: return jacobi_update<2>(x[0], x[1], x[2], x[3], x[4], x[5]);

@@ -20,6 +20,9 @@ void *tile_kernel_am5(int threads, int cpt, int kind);
 void *tile_kernel_am6(int threads, int cpt, int kind);
 void *tile_kernel_am7(int threads, int cpt, int kind);
 void *tile_kernel_am8(int threads, int cpt, int kind);
+void *tile_kernel_am9(int threads, int cpt, int kind);
+void *tile_kernel_am10(int threads, int cpt, int kind);
+void *tile_kernel_am11(int threads, int cpt, int kind);
 void *tile_kernel2d_am0(int threads, int cpt, int kind);
 void *tile_kernel2d_am1(int threads, int cpt, int kind);
 void *tile_kernel2d_am2(int threads, int cpt, int kind);
@@ -27,6 +30,9 @@ void *tile_kernel2d_am3(int threads, int cpt, int kind);
 void *tile_kernel2d_am4(int threads, int cpt, int kind);
 void *tile_kernel2d_am7(int threads, int cpt, int kind);
 void *tile_kernel2d_am8(int threads, int cpt, int kind);
+void *tile_kernel2d_am9(int threads, int cpt, int kind);
+void *tile_kernel2d_am10(int threads, int cpt, int kind);
+void *tile_kernel2d_am11(int threads, int cpt, int kind);
 
 namespace {
 
@@ -41,6 +47,9 @@ void *tile_kernel(int stencil, int amode, int threads, int cpt, int kind) {
         case 4: case 5: case 6: return tile_kernel2d_am4(threads, cpt, kind);
         case 7: return tile_kernel2d_am7(threads, cpt, kind);
         case 8: return tile_kernel2d_am8(threads, cpt, kind);
+        case 9: return tile_kernel2d_am9(threads, cpt, kind);
+        case 10: return tile_kernel2d_am10(threads, cpt, kind);
+        case 11: return tile_kernel2d_am11(threads, cpt, kind);
         default: return nullptr;
     }
     if (stencil != OD_STENCIL_3D7) return nullptr;
@@ -54,6 +63,9 @@ void *tile_kernel(int stencil, int amode, int threads, int cpt, int kind) {
         case 6: return tile_kernel_am6(threads, cpt, kind);
         case 7: return tile_kernel_am7(threads, cpt, kind);
         case 8: return tile_kernel_am8(threads, cpt, kind);
+        case 9: return tile_kernel_am9(threads, cpt, kind);
+        case 10: return tile_kernel_am10(threads, cpt, kind);
+        case 11: return tile_kernel_am11(threads, cpt, kind);
         default: return nullptr;
     }
 }

@@ -280,12 +280,20 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
             // modes 7 and 8 mix the per-cell placement to balance the FP64 and
             // integer pipes: 7 = every other cell with two window adds, 8 =
             // one cell in four (m is a compile-time constant after unrolling)
+            // modes 9-11: the tail form (the last one or two adds in the window,
+            // the division from the window word); 11 mixes them like 7
             constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
             double v;
-            if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0))
+            if constexpr (AM == 9 || AM == 10 || AM == 11) {
+                if ((AM == 11 && (m & 1)) || AM == 10)
+                    v = jacobi_update_tail<2>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
+                else
+                    v = jacobi_update_tail<1>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
+            } else if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0)) {
                 v = jacobi_update_fast<3>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
-            else
+            } else {
                 v = jacobi_update_fast<AMa>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
+            }
             if (!ok)  // rare: an operand left the integer routines' domain
                 v = update_slow(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r]);
             if (w & kValid) {
@@ -450,10 +458,16 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
             bool ok;
             constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
             double v;
-            if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0))
+            if constexpr (AM == 9 || AM == 10 || AM == 11) {
+                if ((AM == 11 && (m & 1)) || AM == 10)
+                    v = jacobi2d_update_tail<2>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
+                else
+                    v = jacobi2d_update_tail<1>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
+            } else if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0)) {
                 v = jacobi2d_update_fast<3>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
-            else
+            } else {
                 v = jacobi2d_update_fast<AMa>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
+            }
             if (!ok) v = update2d_slow(sc[r - 1], sc[r + 1], sd[r], su[r]);
             if (w & kValid) {
                 dpl[r] = v;

@@ -175,7 +175,7 @@ def _update_inputs(rng, n):
     return x
 
 
-@pytest.mark.parametrize("mode", range(7))
+@pytest.mark.parametrize("mode", range(9))  # 7 / 8: the tail form (op 17 / 18)
 def test_update_every_mode_matches_ieee(od, mode):
     rng = np.random.default_rng(100 + mode)
     x = _update_inputs(rng, 400_000)
@@ -245,7 +245,7 @@ def _update2d_inputs(rng, n):
     return x
 
 
-@pytest.mark.parametrize("mode", range(5))
+@pytest.mark.parametrize("mode", range(7))  # 5 / 6: the tail form (op 25 / 26)
 def test_update2d_every_mode_matches_ieee(od, mode):
     rng = np.random.default_rng(200 + mode)
     x = _update2d_inputs(rng, 400_000)
@@ -253,3 +253,18 @@ def test_update2d_every_mode_matches_ieee(od, mode):
         want = (((x[:, 0] + x[:, 1]) + x[:, 2]) + x[:, 3]) / 4.0
     got = od.arith_host(20 + mode, np.ascontiguousarray(x).ravel())
     same(got, want)
+
+
+@pytest.mark.parametrize("op,n_ops", [(17, 6), (18, 6), (25, 4), (26, 4)])
+def test_tail_forms_in_the_solver_regime(od, op, n_ops):
+    # operands like a Jacobi field after some iterations: similar magnitudes,
+    # so the tail window takes (nearly) every cell, with every rounding case
+    rng = np.random.default_rng(op)
+    x = 0.25 + 0.5 * rng.random((500_000, n_ops))
+    x[::3] *= 2.0 ** rng.integers(-8, 1, (x[::3].shape[0], n_ops))
+    with np.errstate(all="ignore"):
+        want = x[:, 0] + x[:, 1]
+        for k in range(2, n_ops):
+            want = want + x[:, k]
+        want = want / (6.0 if n_ops == 6 else 4.0)
+    same(od.arith_host(op, np.ascontiguousarray(x).ravel()), want)

@@ -60,7 +60,7 @@ def test_add_device(env):
                                            x[1, :2_000_000].contiguous()).cpu().numpy().view(np.uint64), want)
 
 
-@pytest.mark.parametrize("mode", range(7))
+@pytest.mark.parametrize("mode", range(9))  # 7 / 8: the tail form (op 17 / 18)
 def test_update_every_mode_device(env, mode):
     # the full update on the GPU in every arithmetic mode equals the host IEEE
     # chain, on the same mix of inputs as the host test

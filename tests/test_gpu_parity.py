@@ -151,7 +151,7 @@ def test_pinned_host_read_and_write(od):
     dict(threads=512, cells_per_thread=1), dict(threads=512, cells_per_thread=2, stages=3),
     dict(threads=256, cells_per_thread=4, stages=8),
     dict(threads=256, cells_per_thread=4, tile_y=3, tile_z=1),
- ] + [dict(arith=m) for m in range(9)])
+ ] + [dict(arith=m) for m in range(12)])
 @pytest.mark.parametrize("path", ["fused", "persistent"])
 def test_launch_shapes(od, path, shape):
     nx, ny, nz = 96, 40, 44
