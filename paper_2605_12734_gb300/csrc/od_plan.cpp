@@ -234,6 +234,16 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
                 if ((int64_t)shapes[i][0] * shapes[i][1] >= wmax) pick = i;
         p.threads = shapes[pick][0];
         p.cpt = shapes[pick][1];
+        // chares whose whole plane fits in 256 cells (16^2 and smaller) would
+        // leave half of a 128 x 4 CTA idle: use 128 x 2
+        int64_t plane_max = 0;
+        for (int64_t a = 1; a < (int64_t)p.ex.size(); ++a)
+            for (int64_t b = 1; b < (int64_t)p.ey.size(); ++b)
+                plane_max = std::max(plane_max, (p.ex[a] - p.ex[a - 1]) * (p.ey[b] - p.ey[b - 1]));
+        if (plane_max <= 256) {
+            p.threads = 128;
+            p.cpt = 2;
+        }
     }
     for (int64_t e = 1; e < (int64_t)p.ex.size() && p.stencil == OD_STENCIL_3D7; ++e)
         if (p.ex[e] - p.ex[e - 1] > (int64_t)p.threads * p.cpt) {

@@ -84,6 +84,8 @@ def test_auto_cta_shape(od):
     assert shape(512, 512, 512, split=(1, 1, 1)) == (256, 4)
     assert shape(1024, 8, 8, split=(1, 1, 1)) == (256, 8)
     assert shape(2048, 8, 8, split=(1, 1, 1)) == (256, 8)
+    assert shape(512, 512, 512, split=(32, 32, 32)) == (128, 2)   # 16^3 chares: a plane is 256 cells
+    assert shape(64, 64, 64, split=(8, 8, 8)) == (128, 2)
 
 
 @pytest.mark.parametrize("odf", [1, 8, 64, 512, 4096])
