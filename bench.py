@@ -372,7 +372,14 @@ def run_ours(args):
             return pkg.Jacobi2D(dims[0], dims[1], seed=seed, init_mode=1, path=path, **dec, **kw)
         return pkg.Jacobi3D(*dims, seed=seed, init_mode=1, path=path, **dec, **kw)
 
+    # under torchrun rank 0 tunes first and writes the tuning cache; the other
+    # ranks (identical GPUs) then find their shape there instead of all tuning
+    # at once and appending to the same file
+    if world > 1 and rank != 0:
+        dist.barrier()
     solver = make(args.path, stream=stream.cuda_stream, **tune_kw)
+    if world > 1 and rank == 0:
+        dist.barrier()
     plan = solver.stats()["plan"]
     solver.step(args.warmup)
     solver.sync()
