@@ -259,6 +259,13 @@ OD_API od_status od_sync(od_ctx *ctx);
  * the first such read or write and kept.  Synchronises the stream. */
 OD_API od_status od_read(od_ctx *ctx, double *dst, int32_t dst_is_device);
 
+/* Read n (0..2^24) cells of the current field into out (host), without
+ * reading the whole grid: cells[i] is a global interior index, x fastest
+ * (x + nx*(y + ny*z); 2D: x + nx*y).  Allocates two small device buffers for
+ * the call; synchronises the stream.  OD_EINVAL for an index outside the
+ * grid. */
+OD_API od_status od_read_cells(od_ctx *ctx, const int64_t *cells, int64_t n, double *out);
+
 /* Replace the current field's interior with src (nx*ny*nz doubles, x fastest;
  * device memory, or host memory copied through the staging buffer) and
  * refresh every internal ghost layer; the

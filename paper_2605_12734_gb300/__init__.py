@@ -230,6 +230,14 @@ class Jacobi3D:
         check(lib().od_read(self._h, out.data_ptr(), 1), "od_read")
         return out
 
+    def read_cells(self, cells) -> np.ndarray:
+        """Values of the current field at the given global interior indices
+        (x fastest), without reading the whole grid."""
+        idx = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.empty(idx.size, dtype=np.float64)
+        check(lib().od_read_cells(self._h, idx.ctypes.data, idx.size, out.ctypes.data), "od_read_cells")
+        return out
+
     def write(self, src) -> None:
         if isinstance(src, np.ndarray):
             src = np.ascontiguousarray(src, dtype=np.float64)

@@ -908,6 +908,45 @@ od_status od_sync(od_ctx *c) {
     return check_device_error_impl(c);
 }
 
+od_status od_read_cells(od_ctx *c, const int64_t *cells, int64_t n, double *out) {
+    if (!c || (n > 0 && (!cells || !out)) || n < 0 || n > (1 << 24))
+        return fail(OD_EINVAL, "od_read_cells: null argument or n outside [0, 2^24]");
+    if (n == 0) return OD_OK;
+    DeviceGuard dg(c->device);
+    od_status s = check_device_error_impl(c);
+    if (s != OD_OK) return s;
+    const od::Plan &p = c->plan;
+    const int par = (int)(c->steps & 1);
+    // global index -> (x, y, z) of the internal grid -> chare -> address
+    std::vector<const double *> addr((size_t)n);
+    for (int64_t q = 0; q < n; ++q) {
+        const int64_t g = cells[q];
+        if (g < 0 || g >= p.cells) return fail(OD_EINVAL, "od_read_cells: cell index outside the grid");
+        const int64_t x = g % p.nx, yz = g / p.nx, y = yz % p.ny, z = yz / p.ny;
+        const int cx = (int)(std::upper_bound(p.ex.begin(), p.ex.end(), x) - p.ex.begin()) - 1;
+        const int cy = (int)(std::upper_bound(p.ey.begin(), p.ey.end(), y) - p.ey.begin()) - 1;
+        const int cz = (int)(std::upper_bound(p.ez.begin(), p.ez.end(), z) - p.ez.begin()) - 1;
+        const size_t ci = (size_t)cx + (size_t)p.px * ((size_t)cy + (size_t)p.py * (size_t)cz);
+        const ChareDev &C = c->h_ch[ci];
+        const int64_t i = x - C.x0, j = y - C.y0, k = z - C.z0;
+        addr[(size_t)q] = C.A[par] + ((k + 1) * C.rows + j + C.row0) * (int64_t)C.pitch + i + 1;
+    }
+    void *d_addr = nullptr, *d_out = nullptr;
+    cudaError_t e = cudaMalloc(&d_addr, (size_t)n * sizeof(void *));
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)n * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_addr, addr.data(), (size_t)n * sizeof(void *), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = od::launch_read_cells(static_cast<const double *const *>(d_addr), n, static_cast<double *>(d_out),
+                                  c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, d_out, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (d_addr) cudaFree(d_addr);
+    if (d_out) cudaFree(d_out);
+    return e == cudaSuccess ? OD_OK : cuda_fail(e, "od_read_cells");
+}
+
 od_status od_read(od_ctx *c, double *dst, int32_t dst_is_device) {
     if (!c || !dst) return fail(OD_EINVAL, "null argument");
     DeviceGuard dg(c->device);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "od.h"
 #include "od_arith.cuh"
 #include "od_internal.h"
@@ -199,6 +201,12 @@ __global__ void k_face_copy(const ChareDev *ch, int nch, int p, int f, int dir, 
     }
 }
 
+// Selected cells: out[i] = *addr[i] (addresses inside the chares' arrays).
+__global__ void k_read_cells(const double *const *addr, int64_t n, double *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = *addr[i];
+}
+
 // A11: interiors of parity p -> global x-fastest array.  One warp per
 // interior row (coalesced on both sides), one 32-bit division per row.
 __global__ void k_gather(const ChareDev *ch, int nch, int p, int64_t nx, int64_t ny, double *g) {
@@ -360,6 +368,13 @@ cudaError_t launch_unpack(const ChareDev *ch, int c, int parity, int slot, int e
     if (grid < 1) grid = 1;
     if (grid > 1024) grid = 1024;
     k_unpack<<<grid, 256, 0, s>>>(ch, c, parity, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_cells(const double *const *addr, int64_t n, double *out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 1024);
+    k_read_cells<<<grid, 256, 0, s>>>(addr, n, out);
     return cudaGetLastError();
 }
 

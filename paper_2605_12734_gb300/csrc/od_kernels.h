@@ -43,6 +43,8 @@ cudaError_t launch_face_copy(const ChareDev *ch, int nch, int parity, int face, 
                              int64_t ny, int64_t nz, cudaStream_t s);
 cudaError_t launch_pack(const ChareDev *ch, int c, int parity, int elems, cudaStream_t s);
 cudaError_t launch_unpack(const ChareDev *ch, int c, int parity, int slot, int elems, cudaStream_t s);
+// out[i] = *addr[i] for n device addresses (od_read_cells).
+cudaError_t launch_read_cells(const double *const *addr, int64_t n, double *out, cudaStream_t s);
 cudaError_t launch_gather(const ChareDev *ch, int nch, int parity, int64_t nx, int64_t ny, double *g,
                           cudaStream_t s);
 // Arithmetic self-test over device arrays (op: 0 div6, 1 add on the integer

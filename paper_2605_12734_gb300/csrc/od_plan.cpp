@@ -309,6 +309,10 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         tz = std::min(tz, h.bz);
         balanced_parts(h.bz, tz, &ks, &kl);
         h.tile_begin = (int32_t)p.tiles.size();
+        h.ti.clear();
+        for (int32_t i0 = 0; i0 < h.bx; i0 += w) h.ti.push_back(i0);
+        h.tj.assign(1, 0);
+        h.tk = ks;
         for (size_t a = 0; a < ks.size(); ++a)
             for (int32_t i0 = 0; i0 < h.bx; i0 += w) {
                 TileDev t;
@@ -338,6 +342,9 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         balanced_parts(h.by, nj_cap, &js, &jl);
         balanced_parts(h.bz, tz, &ks, &kl);
         h.tile_begin = (int32_t)p.tiles.size();
+        h.ti.assign(1, 0);
+        h.tj = js;
+        h.tk = ks;
         for (size_t a = 0; a < ks.size(); ++a)
             for (size_t b = 0; b < js.size(); ++b) {
                 TileDev t;
@@ -376,7 +383,9 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
     }
     p.smem_bytes = (int32_t)smem;
 
-    // dependency lists (tiles of the chare itself and its six neighbours)
+    // dependency lists (tiles of the chare itself and its six neighbours):
+    // per axis only the candidate's tiles within one cell of the tile's range
+    // can touch it, found by bisection over the chare's tile starts
     p.dep_ptr.assign(p.tiles.size() + 1, 0);
     p.dep_idx.clear();
     for (size_t ti = 0; ti < p.tiles.size(); ++ti) {
@@ -387,8 +396,23 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         for (int q = 0; q < 7; ++q) {
             if (cand[q] < 0) continue;
             const HostChare &g = p.ch[(size_t)cand[q]];
-            for (int32_t u = g.tile_begin; u < g.tile_end; ++u)
-                if (adjacent_or_same(a, tile_box(g, p.tiles[(size_t)u]))) p.dep_idx.push_back(u);
+            const std::vector<int32_t> *st[3] = {&g.ti, &g.tj, &g.tk};
+            const int64_t org[3] = {g.x0, g.y0, g.z0};
+            size_t lo[3], hi[3];
+            for (int d = 0; d < 3; ++d) {
+                // tiles whose start is <= a.hi (chare-local), from the last one starting <= a.lo - 1
+                const std::vector<int32_t> &v = *st[d];
+                const int64_t l = a.lo[d] - 1 - org[d], r = a.hi[d] - org[d];
+                size_t first = (size_t)(std::upper_bound(v.begin(), v.end(), l) - v.begin());
+                lo[d] = first > 0 ? first - 1 : 0;
+                hi[d] = (size_t)(std::upper_bound(v.begin(), v.end(), r) - v.begin());
+            }
+            for (size_t e = lo[2]; e < hi[2]; ++e)
+                for (size_t b = lo[1]; b < hi[1]; ++b)
+                    for (size_t i = lo[0]; i < hi[0]; ++i) {
+                        const int32_t u = g.tile_begin + (int32_t)((e * g.tj.size() + b) * g.ti.size() + i);
+                        if (adjacent_or_same(a, tile_box(g, p.tiles[(size_t)u]))) p.dep_idx.push_back(u);
+                    }
         }
         p.dep_ptr[ti + 1] = (int32_t)p.dep_idx.size();
     }

@@ -22,6 +22,9 @@ struct HostChare {
     size_t offA[2];
     size_t offSend, offRecv[2];
     int32_t tile_begin, tile_end;   // tiles [begin,end) belong to this chare
+    // the chare's tiles form a grid: per axis the tile starts (chare-local),
+    // tile (a, b, e) = tile_begin + (e * tj.size() + b) * ti.size() + a
+    std::vector<int32_t> ti, tj, tk;
 };
 
 struct Plan {

@@ -282,7 +282,7 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
             // one cell in four (m is a compile-time constant after unrolling)
             // modes 9-11: the tail form (the last one or two adds in the window,
             // the division from the window word); 11 mixes them like 7
-            constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
+            [[maybe_unused]] constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
             double v;
             if constexpr (AM == 9 || AM == 10 || AM == 11) {
                 if ((AM == 11 && (m & 1)) || AM == 10)
@@ -456,7 +456,7 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
             const uint32_t w = rf[m];
             const int r = (int)(w & 0xFFFFu);
             bool ok;
-            constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
+            [[maybe_unused]] constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
             double v;
             if constexpr (AM == 9 || AM == 10 || AM == 11) {
                 if ((AM == 11 && (m & 1)) || AM == 10)

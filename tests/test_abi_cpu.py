@@ -247,3 +247,10 @@ def test_auto_cta_shape_2d(od):
 def test_launch_benchmarks_check_arguments_first(od, call):
     d = ctypes.c_double()
     assert call(od.lib(), d) == od._native.OD_EINVAL
+
+
+def test_read_cells_checks_arguments_first(od):
+    L, d = od.lib(), ctypes.c_double()
+    cells = (ctypes.c_int64 * 1)(0)
+    assert L.od_read_cells(None, cells, 1, ctypes.byref(d)) == od._native.OD_EINVAL  # no context
+    assert L.od_read_cells(None, None, 0, None) == od._native.OD_EINVAL
