@@ -273,6 +273,23 @@ OD_API od_status od_read_cells(od_ctx *ctx, const int64_t *cells, int64_t n, dou
  * Enqueued on the stream (host sources are copied before return). */
 OD_API od_status od_write(od_ctx *ctx, const double *src, int32_t src_is_device);
 
+/* Asynchronous forms of od_write / od_read for pinned (page-locked) host
+ * memory: the transfer is enqueued and the call returns at once; the caller
+ * leaves the buffer alone until od_sync (or any call that synchronises the
+ * context) returns.  Host data moves by the copy engine through the staging
+ * buffer (allocated on first use, nx*ny*nz doubles), with the scatter /
+ * gather kernel on the device side, so a transfer overlaps other contexts'
+ * work and holds SMs only for the short kernel.  od_write_async enqueues the
+ * copy and the scatter on the context's stream.  od_read_async enqueues the
+ * gather on the context's stream and the device-to-host copy on a copy
+ * stream of the context that waits for the gather: work enqueued on the
+ * context's stream afterwards (an event that another context's stream waits
+ * on, say) follows the gather but not the copy, which lets a caller run two
+ * contexts as a pipeline, one job's copies under the other's iterations.
+ * OD_EINVAL when the buffer is not pinned host memory. */
+OD_API od_status od_write_async(od_ctx *ctx, const double *src);
+OD_API od_status od_read_async(od_ctx *ctx, double *dst);
+
 /* Face exchange of a shard (a context holding a sub-box of a global grid,
  * see od_config.gnx): the data of the paper's transports between chares of
  * different processes (Sec. IV).  dir 0 (export) copies the current field's

@@ -247,6 +247,24 @@ class Jacobi3D:
             assert src.is_cuda and src.numel() == self.cells and src.is_contiguous()
             check(lib().od_write(self._h, src.data_ptr(), 1), "od_write")
 
+    @staticmethod
+    def _host_ptr(buf, n):
+        if isinstance(buf, np.ndarray):
+            assert buf.dtype == np.float64 and buf.size == n and buf.flags["C_CONTIGUOUS"]
+            return buf.ctypes.data
+        assert not buf.is_cuda and buf.is_pinned() and buf.numel() == n and buf.is_contiguous()
+        return buf.data_ptr()
+
+    def write_async(self, src) -> None:
+        """Enqueue the import of a pinned host field (a pinned torch tensor or
+        a numpy view of one); src must stay untouched until sync()."""
+        check(lib().od_write_async(self._h, self._host_ptr(src, self.cells)), "od_write_async")
+
+    def read_async(self, out) -> None:
+        """Enqueue the export of the current field into pinned host memory;
+        out is valid after sync()."""
+        check(lib().od_read_async(self._h, self._host_ptr(out, self.cells)), "od_read_async")
+
     def face_copy(self, face: int, direction: int, buf) -> None:
         """Export (direction 0) the boundary layer on domain face `face` into
         buf, or import (1) buf into its ghost layer; buf: a device pointer

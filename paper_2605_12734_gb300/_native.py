@@ -125,6 +125,8 @@ SIGNATURES = {
     "od_bench_launch_rate": (_i32, [_i32, _i32, _i32, _i32, ctypes.POINTER(ctypes.c_double)]),
     "od_face_copy": (_i32, [_vp, _i32, _i32, _vp, _i32]),
     "od_read_cells": (_i32, [_vp, _vp, _i64, _vp]),
+    "od_write_async": (_i32, [_vp, _vp]),
+    "od_read_async": (_i32, [_vp, _vp]),
     "od_comm_create": (_i32, [ctypes.POINTER(_vp), _i32, _u64, _i32]),
     "od_comm_handles": (_i32, [_vp, _vp, _u64]),
     "od_comm_open": (_i32, [ctypes.POINTER(_vp), _i32, _vp, _u64]),

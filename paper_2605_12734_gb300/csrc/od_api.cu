@@ -348,6 +348,10 @@ od_status enqueue_graph(od_ctx *c, int32_t iters) {
 
 od_status check_device_error_impl(od_ctx *c) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && c->copy_pending) {
+        e = cudaStreamSynchronize(c->copy_stream);
+        c->copy_pending = false;
+    }
     if (e != cudaSuccess) {
         c->failed = true;
         return cuda_fail(e, "cudaStreamSynchronize");
@@ -391,6 +395,10 @@ T *device_view(T *host) {
 }
 
 od_status ensure_stage(od_ctx *c) {
+    if (c->copy_pending) {  // an asynchronous export may still be reading the staging buffer
+        cudaError_t e = cudaStreamWaitEvent(c->stream, c->ev_copied, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    }
     if (c->d_stage) return OD_OK;
     size_t bytes = (size_t)c->plan.cells * sizeof(double);
     cudaError_t e = cudaMalloc(&c->d_stage, bytes);
@@ -411,6 +419,12 @@ void release(od_ctx *c) {
     for (auto e : c->join) cudaEventDestroy(e);
     if (c->fork) cudaEventDestroy(c->fork);
     for (auto s : c->pool) cudaStreamDestroy(s);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->ev_gathered) cudaEventDestroy(c->ev_gathered);
+    if (c->ev_copied) cudaEventDestroy(c->ev_copied);
     if (c->d_stage) cudaFree(c->d_stage);
     if (c->own_arena && c->arena) cudaFree(c->arena);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -988,6 +1002,43 @@ od_status od_write(od_ctx *c, const double *src, int32_t src_is_device) {
     }
     OD_CUDA(od::launch_scatter(c->d_ch, (int)p.ch.size(), par, p.nx, p.ny, p.nz, g, c->stream));
     if (!src_is_device) OD_CUDA(cudaStreamSynchronize(c->stream));
+    return OD_OK;
+}
+
+od_status od_write_async(od_ctx *c, const double *src) {
+    if (!c || !src) return fail(OD_EINVAL, "null argument");
+    if (c->failed) return fail(OD_ESTATE, "context failed earlier; destroy it");
+    DeviceGuard dg(c->device);
+    if (!device_view(src)) return fail(OD_EINVAL, "od_write_async: src is not pinned host memory");
+    od_status s = ensure_stage(c);
+    if (s != OD_OK) return s;
+    const od::Plan &p = c->plan;
+    OD_CUDA(cudaMemcpyAsync(c->d_stage, src, (size_t)p.cells * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    OD_CUDA(od::launch_scatter(c->d_ch, (int)p.ch.size(), (int)(c->steps & 1), p.nx, p.ny, p.nz, c->d_stage,
+                               c->stream));
+    return OD_OK;
+}
+
+od_status od_read_async(od_ctx *c, double *dst) {
+    if (!c || !dst) return fail(OD_EINVAL, "null argument");
+    if (c->failed) return fail(OD_ESTATE, "context failed earlier; destroy it");
+    DeviceGuard dg(c->device);
+    if (!device_view(dst)) return fail(OD_EINVAL, "od_read_async: dst is not pinned host memory");
+    od_status s = ensure_stage(c);
+    if (s != OD_OK) return s;
+    if (!c->copy_stream) {
+        OD_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        OD_CUDA(cudaEventCreateWithFlags(&c->ev_gathered, cudaEventDisableTiming));
+        OD_CUDA(cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming));
+    }
+    const od::Plan &p = c->plan;
+    OD_CUDA(od::launch_gather(c->d_ch, (int)p.ch.size(), (int)(c->steps & 1), p.nx, p.ny, c->d_stage, c->stream));
+    OD_CUDA(cudaEventRecord(c->ev_gathered, c->stream));
+    OD_CUDA(cudaStreamWaitEvent(c->copy_stream, c->ev_gathered, 0));
+    OD_CUDA(cudaMemcpyAsync(dst, c->d_stage, (size_t)p.cells * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->copy_stream));
+    OD_CUDA(cudaEventRecord(c->ev_copied, c->copy_stream));
+    c->copy_pending = true;
     return OD_OK;
 }
 

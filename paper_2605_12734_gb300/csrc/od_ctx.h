@@ -27,6 +27,11 @@ struct od_ctx {
             *d_order = nullptr;
     std::vector<ChareDev> h_ch;       // host copy (device pointers)
     double *d_stage = nullptr;        // lazily allocated host-transfer staging
+    // od_read_async: the device-to-host copy of the staging buffer runs on
+    // copy_stream after ev_gathered; ev_copied marks the staging buffer free
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_gathered = nullptr, ev_copied = nullptr;
+    bool copy_pending = false;
     int path = OD_PATH_FUSED;
     int64_t steps = 0;
     int64_t launches = 0, api_calls = 0, graph_launches = 0;

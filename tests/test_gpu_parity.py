@@ -145,6 +145,68 @@ def test_pinned_host_read_and_write(od):
         assert_bitexact(view.numpy(), oracle.solve(nx, ny, nz, 3, 1, 8), "pinned read at an offset")
 
 
+def test_async_host_transfers_pipelined(od):
+    # two contexts as a pipeline: job j's import and iterations are enqueued
+    # before job j-1's export, so copies of one overlap the other's steps
+    import torch
+    nx, ny, nz = 50, 41, 37
+    n = nx * ny * nz
+    fields = [oracle.solve(nx, ny, nz, 7, 1, t) for t in (0, 3)]
+    want = [oracle.solve(nx, ny, nz, 7, 1, t + 5) for t in (0, 3)]
+    hin = [torch.from_numpy(f.copy()).pin_memory() for f in fields]
+    hout = torch.zeros(n, dtype=torch.float64, pin_memory=True)
+    strm = (torch.cuda.Stream(), torch.cuda.Stream())
+    # the Dirichlet shell comes from the seed; the interior from each import
+    with od.Jacobi3D(nx, ny, nz, split=(2, 2, 2), seed=7, init_mode=1, path="persistent",
+                     stream=strm[0].cuda_stream) as a, \
+            od.Jacobi3D(nx, ny, nz, split=(3, 1, 2), seed=7, init_mode=1, path="fused",
+                        stream=strm[1].cuda_stream) as b:
+        ctx = (a, b)
+        ctx[0].write_async(hin[0])
+        ctx[0].step(5)
+        for j in range(1, 6):
+            cur, prev = ctx[j % 2], ctx[(j - 1) % 2]
+            cur.write_async(hin[j % 2])
+            prev.read_async(hout)
+            ev = torch.cuda.Event()
+            ev.record(strm[(j - 1) % 2])  # after prev's gather, before its copy
+            strm[j % 2].wait_event(ev)
+            cur.step(5)
+            prev.sync()
+            assert_bitexact(hout.numpy(), want[(j - 1) % 2], f"job {j - 1}")
+        ctx[1].read_async(hout.numpy())  # a numpy view of pinned memory works too
+        ctx[1].sync()
+        assert_bitexact(hout.numpy(), want[1], "job 5")
+
+
+def test_async_export_then_import_share_the_staging_buffer(od):
+    # the import's copy into the staging buffer waits for the export's copy out
+    import torch
+    nx, ny, nz = 33, 30, 28
+    n = nx * ny * nz
+    out = torch.zeros(n, dtype=torch.float64, pin_memory=True)
+    new = torch.from_numpy(oracle.solve(nx, ny, nz, 5, 1, 2)).pin_memory()
+    with od.Jacobi3D(nx, ny, nz, split=(2, 2, 1), seed=5, init_mode=1, path="fused") as s:
+        s.step(4)
+        s.read_async(out)
+        s.write_async(new)
+        s.step(3)
+        s.sync()
+        assert_bitexact(out.numpy(), oracle.solve(nx, ny, nz, 5, 1, 4), "export before the import")
+        assert_bitexact(s.read(), oracle.solve(nx, ny, nz, 5, 1, 5), "import, then three steps")
+
+
+def test_async_host_transfers_need_pinned_memory(od):
+    with od.Jacobi3D(16, 16, 16, split=(2, 2, 2), seed=1, init_mode=1, path="fused") as s:
+        pageable = np.zeros(16 ** 3)
+        for call in (s.write_async, s.read_async):
+            with pytest.raises(od.ODError) as ei:
+                call(pageable)
+            assert ei.value.status == od._native.OD_EINVAL
+        s.step(1)
+        s.sync()
+
+
 @pytest.mark.parametrize("shape", [
     dict(threads=128, cells_per_thread=2), dict(threads=128, cells_per_thread=8),
     dict(threads=256, cells_per_thread=1), dict(threads=256, cells_per_thread=8),
