@@ -172,8 +172,8 @@ def profiled_traffic(args, plan):
 
 
 # bumped whenever a tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 10     # 3D 7-point
-KERNEL_REV_2D = 11  # 2D 5-point
+KERNEL_REV = 11     # 3D 7-point
+KERNEL_REV_2D = 12  # 2D 5-point
 
 
 def combine_ranks(ms: float, updates: float, world: int, device: str):
@@ -470,10 +470,23 @@ def run_ours(args):
         host_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
         solver.read(host_in.numpy())       # a valid field to feed back in
         iters_job = 100
-        reps = 8
+        reps = 16                          # the pipeline's fill and drain amortised over 16 jobs
         stream2 = torch.cuda.Stream(dev)
         twin = make(args.path, stream=stream2.cuda_stream, **tune_kw)
         ctx, strm = (solver, twin), (stream, stream2)
+        # the host link's bandwidth right now (the host is shared): one copy each way
+        probe = torch.empty(min(n, 1 << 27), dtype=torch.float64, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        with torch.cuda.stream(stream):
+            ev[0].record(stream)
+            probe.copy_(host_in[:probe.numel()], non_blocking=True)
+            ev[1].record(stream)
+            host_out[:probe.numel()].copy_(probe, non_blocking=True)
+            ev[2].record(stream)
+        ev[2].synchronize()
+        link = (probe.numel() * 8 / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9,
+                probe.numel() * 8 / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9)
+        del probe
         first = None
         for c in ctx:                      # warm-up job on each context
             c.write_async(host_in)
@@ -486,6 +499,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         ctx[0].write_async(host_in)
         ctx[0].step(iters_job)
+        spans = []                         # each job's iterations, as the device ran them
         for j in range(1, reps):
             cur, prev = ctx[j % 2], ctx[(j - 1) % 2]
             cur.write_async(host_in)
@@ -493,7 +507,11 @@ def run_ours(args):
             gathered = torch.cuda.Event()
             gathered.record(strm[(j - 1) % 2])
             strm[j % 2].wait_event(gathered)
+            k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k0.record(strm[j % 2])
             cur.step(iters_job)
+            k1.record(strm[j % 2])
+            spans.append((k0, k1))
             prev.sync()
         ctx[(reps - 1) % 2].read_async(host_out)
         ctx[(reps - 1) % 2].sync()
@@ -503,6 +521,9 @@ def run_ours(args):
         e2e = {"value": n * iters_job * reps * world / dt, "unit": UNIT,
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
                "iters_per_step": iters_job, "jobs": reps, "results_identical": same,
+               "host_link_GBps": {"h2d": round(link[0], 1), "d2h": round(link[1], 1)},
+               "iterations_ms_per_job": round(sum(a.elapsed_time(b) for a, b in spans) / len(spans), 3),
+               "wall_ms_per_job": round(dt / reps * 1e3, 3),
                "note": "e2e step = od_write_async(pinned host field) + od_step(100) + od_read_async(pinned host); "
                        "two contexts pipelined, so one job's host copies overlap the other's iterations"}
     solver.close()

@@ -232,8 +232,9 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     issued_hi = min(ke, kb + S - 1);
 
     // this thread's cells: q = tid + m*NT in the tile plane, row-major.  A slot
-    // past the end of the tile repeats the tile's first cell and stores
-    // nothing, so the cell loop needs no validity branch.
+    // past the end of the tile repeats the tile's first cell (it stores the
+    // same value to the same place, and pushes nothing), so the cell loop
+    // needs no validity branch.
     const int ncell = T.nj * bx;
     uint32_t rf[CPT];
 #pragma unroll
@@ -272,6 +273,22 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
                              const double *su) {
         constexpr bool ZP = decltype(zp_tag)::value;
         double *dpl = dst + (size_t)(k + 1) * plane;
+        // no validity branch: a slot past the tile's end repeats the tile's
+        // first cell, so it stores the same value to the same place
+        auto store = [&](uint32_t w, int r, double v) {
+            dpl[r] = v;
+            if (PUSH) {
+                if (w >> 28) {
+                    const int j1 = (int)((w >> 16) & 0x7FFu) + 1;
+                    if (w & kXlo) pi->xlo[(size_t)(k + 1) * pi->xlo_plane + (size_t)j1 * pi->xlo_pitch] = v;
+                    if (w & kXhi) pi->xhi[(size_t)(k + 1) * pi->xhi_plane + (size_t)j1 * pi->xhi_pitch] = v;
+                    if (w & kYlo) pi->ylo[(size_t)(k + 1) * pi->ylo_plane + r] = v;
+                    if (w & kYhi) pi->yhi[(size_t)(k + 1) * pi->yhi_plane + r] = v;
+                }
+                if (ZP) zp[r] = v;
+            }
+        };
+        uint32_t bad = 0;  // bit m: cell m left the integer routines' domain
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
             const uint32_t w = rf[m];
@@ -294,20 +311,16 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
             } else {
                 v = jacobi_update_fast<AMa>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
             }
-            if (!ok)  // rare: an operand left the integer routines' domain
-                v = update_slow(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r]);
-            if (w & kValid) {
-                dpl[r] = v;
-                if (PUSH) {
-                    if (w >> 28) {
-                        const int j1 = (int)((w >> 16) & 0x7FFu) + 1;
-                        if (w & kXlo) pi->xlo[(size_t)(k + 1) * pi->xlo_plane + (size_t)j1 * pi->xlo_pitch] = v;
-                        if (w & kXhi) pi->xhi[(size_t)(k + 1) * pi->xhi_plane + (size_t)j1 * pi->xhi_pitch] = v;
-                        if (w & kYlo) pi->ylo[(size_t)(k + 1) * pi->ylo_plane + r] = v;
-                        if (w & kYhi) pi->yhi[(size_t)(k + 1) * pi->yhi_plane + r] = v;
-                    }
-                    if (ZP) zp[r] = v;
-                }
+            bad |= (ok ? 0u : 1u) << m;
+            store(w, r, v);
+        }
+        if (bad) {  // rare: recompute those cells with IEEE operations and store them again
+#pragma unroll
+            for (int m = 0; m < CPT; ++m) {
+                const uint32_t w = rf[m];
+                const int r = (int)(w & 0xFFFFu);
+                if (bad & (1u << m))
+                    store(w, r, update_slow(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r]));
             }
         }
     };
@@ -421,7 +434,7 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
     issued_hi = min(ke, kb + S - 1);
 
     // this thread's cells q = tid + m*NT of the segment; a slot past its end
-    // repeats cell 0 and stores nothing
+    // repeats cell 0 (same value, same place, no flags)
     uint32_t rf[CPT];
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
@@ -451,6 +464,16 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
                              const double *su) {
         constexpr bool ZP = decltype(zp_tag)::value;
         double *dpl = dst + (size_t)(k + 1) * plane;
+        // no validity branch: a slot past the segment's end repeats its cell
+        // 0, so it stores the same value to the same place
+        auto store = [&](uint32_t w, int r, double v) {
+            dpl[r] = v;
+            if (PUSH) {
+                if (w & kXlo) pi->xlo[(size_t)(k + 1) * pi->xlo_plane] = v;
+                if (w & kXhi) pi->xhi[(size_t)(k + 1) * pi->xhi_plane] = v;
+                if (ZP) zp[r] = v;
+            }
+        };
 #pragma unroll
         for (int m = 0; m < CPT; ++m) {
             const uint32_t w = rf[m];
@@ -469,14 +492,7 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
                 v = jacobi2d_update_fast<AMa>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
             }
             if (!ok) v = update2d_slow(sc[r - 1], sc[r + 1], sd[r], su[r]);
-            if (w & kValid) {
-                dpl[r] = v;
-                if (PUSH) {
-                    if (w & kXlo) pi->xlo[(size_t)(k + 1) * pi->xlo_plane] = v;
-                    if (w & kXhi) pi->xhi[(size_t)(k + 1) * pi->xhi_plane] = v;
-                    if (ZP) zp[r] = v;
-                }
-            }
+            store(w, r, v);
         }
     };
 
