@@ -743,7 +743,7 @@ def run_serve(args, pkg, torch, rank, world, dev):
     clocks = ClockSampler(dev)
     clocks.start()
     t0 = time.perf_counter()
-    base = srv.stats()["seconds"]
+    busy0 = srv.stats()["busy_seconds"]
     for j in jobs:
         delay = t0 + j.arrival_s - time.perf_counter()
         if delay > 0:
@@ -778,6 +778,7 @@ def run_serve(args, pkg, torch, rank, world, dev):
             "latency_max_s": lat_sorted[-1], "wall_s": wall, "launches": st["launches"],
             "pool_peak_gb": st["pool_peak"] / (1 << 30), "offered_updates_per_s": upd / jobs[-1].arrival_s,
             "admit_seconds": st["admit_seconds"],
+            "device_busy_frac": (st["busy_seconds"] - busy0) / wall,
             "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)

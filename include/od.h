@@ -456,6 +456,8 @@ typedef struct od_server_stats_t {
     double seconds;              /* since the server was created */
     double admit_seconds;        /* spent creating job contexts (on the
                                     admission thread, beside the launches) */
+    double busy_seconds;         /* device time of the completed batched
+                                    launches (events around each kernel) */
 } od_server_stats_t;
 
 OD_API void od_server_config_default(od_server_config *cfg);

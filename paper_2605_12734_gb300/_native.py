@@ -75,7 +75,7 @@ class od_server_stats_t(ctypes.Structure):
     _fields_ = [
         ("queued", _i64), ("running", _i64), ("done", _i64), ("failed", _i64), ("launches", _i64),
         ("updates_done", ctypes.c_double), ("pool_used", _u64), ("pool_peak", _u64), ("seconds", ctypes.c_double),
-        ("admit_seconds", ctypes.c_double),
+        ("admit_seconds", ctypes.c_double), ("busy_seconds", ctypes.c_double),
     ]
 
 

@@ -108,7 +108,7 @@ struct Job {
 
 struct Batch {
     int64_t index;
-    cudaEvent_t ev;
+    cudaEvent_t ev0, ev;  // before the kernel, after it (timed: the device's busy time)
 };
 
 }  // namespace
@@ -140,6 +140,7 @@ struct od_server {
     int64_t launches = 0, done = 0, failed = 0;
     double updates_done = 0;
     double admit_seconds = 0;  // spent creating job contexts (admission thread)
+    double busy_seconds = 0;   // device time of the retired batched launches
     std::string worker_error;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -221,6 +222,9 @@ void retire(od_server *s) {
     while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().ev) == cudaSuccess) {
         const Batch b = s->inflight.front();
         s->inflight.pop_front();
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b.ev0, b.ev) == cudaSuccess) s->busy_seconds += ms * 1e-3;
+        s->free_events.push_back(b.ev0);
         s->free_events.push_back(b.ev);
         const double t = s->now();
         for (auto &kv : s->jobs) {
@@ -236,6 +240,17 @@ void retire(od_server *s) {
         s->cv_done.notify_all();
     }
     cudaGetLastError();  // cudaErrorNotReady is not an error here
+}
+
+cudaEvent_t take_event(od_server *s) {
+    cudaEvent_t ev;
+    if (s->free_events.empty()) {
+        cudaEventCreate(&ev);
+    } else {
+        ev = s->free_events.back();
+        s->free_events.pop_back();
+    }
+    return ev;
 }
 
 // One fused step of every running job that still has steps (lock held).
@@ -262,9 +277,12 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
     cudaMemcpyAsync(s->d_jobs[slot], hk.data(), hk.size() * sizeof(KArgs), cudaMemcpyHostToDevice, s->compute);
     cudaMemcpyAsync(s->d_first[slot], hf.data(), hf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s->compute);
     const int smem = 256 + s->stages * max_sd * 8;
+    cudaEvent_t ev0 = take_event(s);
+    cudaEventRecord(ev0, s->compute);
     cudaError_t e = od::launch_tiles_multi(s->d_jobs[slot], s->d_first[slot], (int32_t)in.size(), grid, s->threads,
                                            s->cpt, s->arith, smem, OD_STENCIL_3D7, s->compute);
     if (e != cudaSuccess) {
+        s->free_events.push_back(ev0);
         s->worker_error = std::string("k_tiles_multi: ") + cudaGetErrorString(e);
         return false;
     }
@@ -274,14 +292,9 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
         j->steps_enq++;
         if (j->steps_enq == j->iters) j->done_batch = idx;
     }
-    cudaEvent_t ev;
-    if (s->free_events.empty()) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    else {
-        ev = s->free_events.back();
-        s->free_events.pop_back();
-    }
+    cudaEvent_t ev = take_event(s);
     cudaEventRecord(ev, s->compute);
-    s->inflight.push_back({idx, ev});
+    s->inflight.push_back({idx, ev0, ev});
     return true;
 }
 
@@ -524,6 +537,7 @@ od_status od_server_stats(od_server *s, od_server_stats_t *out) {
     out->pool_peak = s->pool.peak();
     out->seconds = s->now();
     out->admit_seconds = s->admit_seconds;
+    out->busy_seconds = s->busy_seconds;
     if (!s->worker_error.empty()) return fail(OD_ECUDA, s->worker_error);
     return OD_OK;
 }
@@ -544,7 +558,10 @@ od_status od_server_destroy(od_server *s) {
         if (kv.second->ctx) od_destroy(kv.second->ctx);
         delete kv.second;
     }
-    for (auto &b : s->inflight) cudaEventDestroy(b.ev);
+    for (auto &b : s->inflight) {
+        cudaEventDestroy(b.ev0);
+        cudaEventDestroy(b.ev);
+    }
     for (auto e : s->free_events) cudaEventDestroy(e);
     for (int k = 0; k < 2; ++k) {
         if (s->d_jobs[k]) cudaFree(s->d_jobs[k]);

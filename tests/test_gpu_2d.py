@@ -123,6 +123,20 @@ def test_2d_device_read_and_write(od):
         assert_bitexact(s.read(), want, "device write")
 
 
+def test_2d_async_host_transfers(od):
+    import torch
+    nx, ny = 300, 170
+    u3 = torch.from_numpy(oracle.solve_2d(nx, ny, 8, 1, 3)).pin_memory()
+    out = torch.zeros(nx * ny, dtype=torch.float64, pin_memory=True)
+    with od.Jacobi2D(nx, ny, split=(3, 2), seed=8, init_mode=1, path="persistent") as s:
+        s.write_async(u3)
+        s.step(4)
+        s.read_async(out)
+        s.sync()
+        assert_bitexact(out.numpy(), oracle.solve_2d(nx, ny, 8, 1, 7), "import u^3, four steps, export")
+        assert bits(s.read_cells([0, nx * ny - 1]))[1] == bits(out.numpy()[-1:])[0]
+
+
 def test_2d_autotune(od, tmp_path, monkeypatch):
     monkeypatch.setenv("OD_TUNE_CACHE", str(tmp_path / "tune.txt"))
     nx, ny = 1024, 512
