@@ -435,7 +435,7 @@ typedef struct od_server_config {
     int32_t max_jobs_per_launch; /* batch table size (0 = 256) */
     int32_t device;
     int32_t threads, cells_per_thread, stages; /* tile shape for every job (0 = 128, 4, 4) */
-    int32_t arith;               /* as od_config.arith (-1 = 7) */
+    int32_t arith;               /* as od_config.arith (-1 = 11) */
     void *pool;                  /* caller device memory of hbm_budget_bytes, 256-byte
                                     aligned, or NULL: the server allocates it once */
 } od_server_config;
