@@ -221,29 +221,54 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         p.threads = 128;
         p.cpt = wmax <= 256 ? 2 : 4;
     } else if (auto_shape) {
-        // smallest CTA shape that holds two rows of the widest chare (one if
-        // none does): 128 x 4, 256 x 4, 256 x 8 cells
+        // Score each CTA shape that holds a row of the widest chare by
+        //   lanes used (tile cells / CTA cells, over the whole grid)
+        //   x (1 - 0.2 / rows per tile)       (the two y-halo rows loaded per plane)
+        //   x min(1, tiles / half the resident CTAs)   (too few tiles leave SMs
+        //        idle; a GB300 holds about 1280 threads per SM of these
+        //        kernels, 152 SMs, and runs well from half of that)
+        // and keep 128 x 4 unless another shape scores 10 % higher (measured,
+        // fused path: 384^3 in 8 chares 256 x 4 120 vs 103 G updates/s; 150^3
+        // in 27 and 200^3 in 64 128 x 2, 70 vs 52 and 97 vs 85; 32^3 and 64^3
+        // chares of large grids 128 x 4).
         int64_t wmax = 0;
         for (int64_t e = 1; e < (int64_t)p.ex.size(); ++e) wmax = std::max(wmax, p.ex[e] - p.ex[e - 1]);
-        const int32_t shapes[3][2] = {{128, 4}, {256, 4}, {256, 8}};
-        int pick = 2;
-        for (int i = 2; i >= 0; --i)
-            if ((int64_t)shapes[i][0] * shapes[i][1] >= 2 * wmax) pick = i;
-        if ((int64_t)shapes[pick][0] * shapes[pick][1] < 2 * wmax)
-            for (int i = 2; i >= 0; --i)
-                if ((int64_t)shapes[i][0] * shapes[i][1] >= wmax) pick = i;
+        const int32_t shapes[4][2] = {{128, 4}, {128, 2}, {256, 4}, {256, 8}};
+        const int32_t tz = p.tile_z > 0 ? p.tile_z : 32;
+        double best = -1.0, base = -1.0;
+        int pick = -1;
+        for (int i = 0; i < 4; ++i) {
+            const int64_t cap = (int64_t)shapes[i][0] * shapes[i][1];
+            if (cap < wmax || (i == 3 && wmax <= 1024)) continue;  // 256 x 8 only for rows past 1024
+            double used = 0.0, cells = 0.0, rows = 0.0, tiles = 0.0;
+            for (int64_t a = 1; a < (int64_t)p.ex.size(); ++a)
+                for (int64_t b = 1; b < (int64_t)p.ey.size(); ++b)
+                    for (int64_t c = 1; c < (int64_t)p.ez.size(); ++c) {
+                        const int64_t bx = p.ex[a] - p.ex[a - 1], by = p.ey[b] - p.ey[b - 1],
+                                      bz = p.ez[c] - p.ez[c - 1];
+                        int64_t nj = std::min<int64_t>(by, cap / bx);
+                        if (p.tile_y > 0) nj = std::min<int64_t>(nj, p.tile_y);
+                        nj = std::max<int64_t>(nj, 1);
+                        const int64_t slabs = (by + nj - 1) / nj, chunks = (bz + std::min<int64_t>(tz, bz) - 1) /
+                                                                               std::min<int64_t>(tz, bz);
+                        const double v = (double)bx * by * bz;
+                        used += v;
+                        cells += (double)cap * slabs * bz;  // lanes offered: one CTA plane per slab and plane
+                        rows += v * ((double)by / slabs);
+                        tiles += (double)slabs * chunks;
+                    }
+            const double resident = 0.5 * 152.0 * (1280 / shapes[i][0]);
+            const double score = used / cells * (1.0 - 0.2 / (rows / used)) * std::min(1.0, tiles / resident);
+            if (i == 0) base = score;
+            if (score > best) {
+                best = score;
+                pick = i;
+            }
+        }
+        if (pick < 0) pick = 3;  // rows past 1024 cells: only 256 x 8 holds them (checked below)
+        if (pick != 0 && base >= 0.0 && best < 1.1 * base) pick = 0;
         p.threads = shapes[pick][0];
         p.cpt = shapes[pick][1];
-        // chares whose whole plane fits in 256 cells (16^2 and smaller) would
-        // leave half of a 128 x 4 CTA idle: use 128 x 2
-        int64_t plane_max = 0;
-        for (int64_t a = 1; a < (int64_t)p.ex.size(); ++a)
-            for (int64_t b = 1; b < (int64_t)p.ey.size(); ++b)
-                plane_max = std::max(plane_max, (p.ex[a] - p.ex[a - 1]) * (p.ey[b] - p.ey[b - 1]));
-        if (plane_max <= 256) {
-            p.threads = 128;
-            p.cpt = 2;
-        }
     }
     for (int64_t e = 1; e < (int64_t)p.ex.size() && p.stencil == OD_STENCIL_3D7; ++e)
         if (p.ex[e] - p.ex[e - 1] > (int64_t)p.threads * p.cpt) {

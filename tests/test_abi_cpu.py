@@ -81,11 +81,18 @@ def test_auto_cta_shape(od):
         i = od.plan(*dims, **kw)
         return i["threads"], i["cells_per_thread"]
     assert shape(512, 512, 512, split=(16, 16, 16)) == (128, 4)
-    assert shape(512, 512, 512, split=(1, 1, 1)) == (256, 4)
-    assert shape(1024, 8, 8, split=(1, 1, 1)) == (256, 8)
-    assert shape(2048, 8, 8, split=(1, 1, 1)) == (256, 8)
+    assert shape(1024, 1024, 1024, split=(16, 16, 16)) == (128, 4)
+    assert shape(512, 512, 512, split=(1, 1, 1)) == (256, 4)      # one 512-cell row per 128 x 4 tile
+    assert shape(1024, 8, 8, split=(1, 1, 1)) == (256, 4)         # more tiles than 256 x 8 gives
+    assert shape(2048, 8, 8, split=(1, 1, 1)) == (256, 8)         # only 256 x 8 holds the row
     assert shape(512, 512, 512, split=(32, 32, 32)) == (128, 2)   # 16^3 chares: a plane is 256 cells
     assert shape(64, 64, 64, split=(8, 8, 8)) == (128, 2)
+    # the fused path's best shape measured on a GB300 for these grids
+    assert shape(384, 384, 384, split=(2, 2, 2)) == (256, 4)      # 192-cell rows: 2 per 512, 5 per 1024
+    assert shape(300, 300, 300, split=(2, 2, 2)) == (128, 4)
+    assert shape(192, 192, 192, split=(2, 2, 2)) == (128, 2)      # 128 x 4 would give 480 tiles
+    assert shape(150, 150, 150, split=(3, 3, 3)) == (128, 2)
+    assert shape(384, 384, 384, split=(4, 4, 4)) == (128, 4)
 
 
 @pytest.mark.parametrize("odf", [1, 8, 64, 512, 4096])
