@@ -278,12 +278,23 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
         auto store = [&](uint32_t w, int r, double v) {
             dpl[r] = v;
             if (PUSH) {
-                if (w >> 28) {
+                const uint32_t xf = w & (kXlo | kXhi);
+                if (xf) {  // a row's first and last lanes take one path together
                     const int j1 = (int)((w >> 16) & 0x7FFu) + 1;
-                    if (w & kXlo) pi->xlo[(size_t)(k + 1) * pi->xlo_plane + (size_t)j1 * pi->xlo_pitch] = v;
-                    if (w & kXhi) pi->xhi[(size_t)(k + 1) * pi->xhi_plane + (size_t)j1 * pi->xhi_pitch] = v;
-                    if (w & kYlo) pi->ylo[(size_t)(k + 1) * pi->ylo_plane + r] = v;
-                    if (w & kYhi) pi->yhi[(size_t)(k + 1) * pi->yhi_plane + r] = v;
+                    const bool lo = (w & kXlo) != 0;
+                    double *base = lo ? pi->xlo : pi->xhi;
+                    const int pl = lo ? pi->xlo_plane : pi->xhi_plane, pt = lo ? pi->xlo_pitch : pi->xhi_pitch;
+                    base[(size_t)(k + 1) * pl + (size_t)j1 * pt] = v;
+                    if (xf == (kXlo | kXhi))  // bx == 1: the cell is on both x faces
+                        pi->xhi[(size_t)(k + 1) * pi->xhi_plane + (size_t)j1 * pi->xhi_pitch] = v;
+                }
+                const uint32_t yf = w & (kYlo | kYhi);
+                if (yf) {  // whole rows: the branch is uniform across a row's lanes
+                    const bool lo = (w & kYlo) != 0;
+                    double *base = lo ? pi->ylo : pi->yhi;
+                    base[(size_t)(k + 1) * (lo ? pi->ylo_plane : pi->yhi_plane) + r] = v;
+                    if (yf == (kYlo | kYhi))  // by == 1: the row is on both y faces
+                        pi->yhi[(size_t)(k + 1) * pi->yhi_plane + r] = v;
                 }
                 if (ZP) zp[r] = v;
             }
