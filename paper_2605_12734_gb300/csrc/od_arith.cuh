@@ -68,6 +68,31 @@ OD_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
 #endif
 }
 
+// x << s and x >> s for a shift of at most 31: on the device two 32-bit
+// funnel shifts instead of a general 64-bit shift.  The shift counts below
+// are at most 11 whenever their result is used (the domain checks send every
+// other case to the IEEE fallback); a larger count only yields a discarded
+// value, the same on host and device.
+OD_HD uint64_t shl31(uint64_t x, uint32_t s) {
+    s &= 31u;
+#if defined(__CUDA_ARCH__)
+    const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    return ((uint64_t)__funnelshift_l(lo, hi, s) << 32) | (uint64_t)(lo << s);
+#else
+    return x << s;
+#endif
+}
+
+OD_HD uint64_t shr31(uint64_t x, uint32_t s) {
+    s &= 31u;
+#if defined(__CUDA_ARCH__)
+    const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    return ((uint64_t)(hi >> s) << 32) | (uint64_t)__funnelshift_r(lo, hi, s);
+#else
+    return x >> s;
+#endif
+}
+
 // IEEE operations (the fallback and the reference)
 OD_HD double ieee_add(double a, double b) {
 #if defined(__CUDA_ARCH__)
@@ -197,7 +222,7 @@ OD_HD Unpacked add_chain(const Unpacked &a, const Unpacked &b) {
 // s / 6 for s in the chain's range (exponent >= 4): see div6.
 OD_HD double div6_chain(const Unpacked &s) {
     const uint32_t big = (uint32_t)(s.m >= (3ull << 51));
-    const uint64_t N = s.m << (2u - big);
+    const uint64_t N = shl31(s.m, 2u - big);
     const uint64_t Q0 = mulhi64(N, 0xAAAAAAAAAAAAAAABull) >> 1;
     const uint32_t r = (uint32_t)N - 3u * (uint32_t)Q0;
     const uint64_t Q = Q0 + (r >> 1);
@@ -258,11 +283,11 @@ OD_HD uint64_t window_chain(const double *x, bool &ok, uint32_t &emax, uint32_t 
     }
     ok = (lo_e - 4u <= 2036u) & (hi_e - 4u <= 2036u) & (hi_e - lo_e <= 8u);
     emax = hi_e;
-    uint64_t W = m[0] << ((8u - (hi_e - e[0])) & 63u);
+    uint64_t W = shl31(m[0], 8u - (hi_e - e[0]));
     p = 0;
 #pragma unroll
     for (int t = 1; t <= K; ++t) {
-        W += m[t] << ((8u - (hi_e - e[t])) & 63u);
+        W += shl31(m[t], 8u - (hi_e - e[t]));
         p = round_window(W);
     }
     return W;
@@ -270,7 +295,7 @@ OD_HD uint64_t window_chain(const double *x, bool &ok, uint32_t &emax, uint32_t 
 
 // The window word as a binary64 (53 significant bits at position p).
 OD_HD double pack_window(uint64_t W, uint32_t emax, uint32_t p) {
-    const uint64_t M = W >> p;                            // [2^52, 2^53)
+    const uint64_t M = shr31(W, p);                       // [2^52, 2^53)
     const uint64_t E = (uint64_t)(emax - 8u + p);         // biased exponent
     return f64_from(((E - 1u) << 52) + M);
 }
@@ -278,7 +303,7 @@ OD_HD double pack_window(uint64_t W, uint32_t emax, uint32_t p) {
 // s / 6 of the window value (see div6), s's exponent emax - 8 + p >= 4.
 OD_HD double div6_window(uint64_t W, uint32_t emax, uint32_t p) {
     Unpacked u;
-    u.m = W >> p;
+    u.m = shr31(W, p);
     u.e = emax - 8u + p;
     return div6_chain(u);
 }
@@ -294,7 +319,7 @@ OD_HD double div6_fast(double s, bool &ok) {
     ok = es - 4u <= 2042u;
     const uint64_t M = (b & kFrac) | kHid;
     const uint32_t big = (uint32_t)(M >= (3ull << 51));
-    const uint64_t N = M << (2u - big);
+    const uint64_t N = shl31(M, 2u - big);
     const uint64_t Q0 = mulhi64(N, 0xAAAAAAAAAAAAAAABull) >> 1;
     const uint32_t r = (uint32_t)N - 3u * (uint32_t)Q0;  // 0, 1 or 2
     const uint64_t Q = Q0 + (r >> 1);                      // round up iff r == 2
