@@ -172,8 +172,8 @@ def profiled_traffic(args, plan):
 
 
 # bumped whenever a tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 11     # 3D 7-point
-KERNEL_REV_2D = 12  # 2D 5-point
+KERNEL_REV = 12     # 3D 7-point
+KERNEL_REV_2D = 13  # 2D 5-point
 
 
 def combine_ranks(ms: float, updates: float, world: int, device: str):
@@ -500,6 +500,7 @@ def run_ours(args):
         ctx[0].write_async(host_in)
         ctx[0].step(iters_job)
         spans = []                         # each job's iterations, as the device ran them
+        marks = [t0]                       # host time as each job's result arrived
         for j in range(1, reps):
             cur, prev = ctx[j % 2], ctx[(j - 1) % 2]
             cur.write_async(host_in)
@@ -513,6 +514,7 @@ def run_ours(args):
             k1.record(strm[j % 2])
             spans.append((k0, k1))
             prev.sync()
+            marks.append(time.perf_counter())
         ctx[(reps - 1) % 2].read_async(host_out)
         ctx[(reps - 1) % 2].sync()
         dt = time.perf_counter() - t0
@@ -524,6 +526,8 @@ def run_ours(args):
                "host_link_GBps": {"h2d": round(link[0], 1), "d2h": round(link[1], 1)},
                "iterations_ms_per_job": round(sum(a.elapsed_time(b) for a, b in spans) / len(spans), 3),
                "wall_ms_per_job": round(dt / reps * 1e3, 3),
+               "job_interval_ms": {"median": round(float(np.median(np.diff(marks))) * 1e3, 3),
+                                   "max": round(float(np.max(np.diff(marks))) * 1e3, 3)},
                "note": "e2e step = od_write_async(pinned host field) + od_step(100) + od_read_async(pinned host); "
                        "two contexts pipelined, so one job's host copies overlap the other's iterations"}
     solver.close()

@@ -131,9 +131,10 @@ typedef struct od_config {
     int32_t threads;             /* threads per CTA: 128, 256 or 512 */
     int32_t cells_per_thread;    /* 1, 2, 4 or 8; supported pairs 128 x {2,4,8},
                                     256 x {1,2,4,8}, 512 x {1,2}.  Both 0: the
-                                    planner takes the smallest of 128x4, 256x4,
-                                    256x8 that holds two rows of the widest
-                                    chare */
+                                    planner picks among 128x4, 128x2, 256x4
+                                    (and 256x8 for rows past 1024 cells) by
+                                    the lanes its tiles use, the halo rows and
+                                    the tile count, preferring 128x4 */
     int32_t stages;              /* TMA ring slots, 3..8 (0 = 4): planes k-1,
                                     k, k+1 resident, the rest in flight */
     int32_t arith;               /* where the update's operations run (the bits
@@ -145,8 +146,8 @@ typedef struct od_config {
                                     in mode 3); 9 / 10: the last one / two adds
                                     on the integer pipes and the division taken
                                     from their result; 11: 9 and 10 mixed cell
-                                    by cell; -1 = library default (7; 2 for the
-                                    2D stencil) */
+                                    by cell; -1 = library default (10; 2 for
+                                    the 2D stencil) */
     int32_t order;               /* persistent path task order, bits: 1 = reversed
                                     on odd steps, 2 = chares in Morton (Z) order
                                     instead of x-fastest; 0..3 */
@@ -435,7 +436,7 @@ typedef struct od_server_config {
     int32_t max_jobs_per_launch; /* batch table size (0 = 256) */
     int32_t device;
     int32_t threads, cells_per_thread, stages; /* tile shape for every job (0 = 128, 4, 4) */
-    int32_t arith;               /* as od_config.arith (-1 = 11) */
+    int32_t arith;               /* as od_config.arith (-1 = 10) */
     void *pool;                  /* caller device memory of hbm_budget_bytes, 256-byte
                                     aligned, or NULL: the server allocates it once */
 } od_server_config;

@@ -18,7 +18,7 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int32_t kMaxSmem = 232448;  // 227 KB opt-in per CTA on sm_100/sm_103
 constexpr int32_t kSmemHeader = 256;  // mbarriers + neighbour push table
-constexpr int32_t kDefaultArith = 7;   // modes 2 and 3 mixed cell by cell
+constexpr int32_t kDefaultArith = 10;  // the last two adds and the division on the integer pipes
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 int32_t round_up(int32_t v, int32_t a) { return (v + a - 1) / a * a; }
