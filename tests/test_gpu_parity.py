@@ -213,6 +213,9 @@ def test_async_host_transfers_need_pinned_memory(od):
     dict(threads=512, cells_per_thread=1), dict(threads=512, cells_per_thread=2, stages=3),
     dict(threads=256, cells_per_thread=4, stages=8),
     dict(threads=256, cells_per_thread=4, tile_y=3, tile_z=1),
+    # deeper rings with tiles of odd, one and two planes
+    dict(stages=5), dict(stages=5, tile_z=7), dict(stages=6, tile_z=2), dict(stages=6, tile_z=1),
+    dict(stages=5, tile_z=3, tile_y=5, arith=7),
  ] + [dict(arith=m) for m in range(12)])
 @pytest.mark.parametrize("path", ["fused", "persistent"])
 def test_launch_shapes(od, path, shape):
