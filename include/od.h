@@ -435,7 +435,11 @@ typedef struct od_server_config {
     int32_t max_active;          /* jobs resident at once (0 = no limit) */
     int32_t max_jobs_per_launch; /* batch table size (0 = 256) */
     int32_t device;
-    int32_t threads, cells_per_thread, stages; /* tile shape for every job (0 = 128, 4, 4) */
+    int32_t threads, cells_per_thread, stages; /* CTA shape for every job; threads and
+                                    cells_per_thread both 0: the planner picks
+                                    each job's shape (as od_config) and each
+                                    step runs one batched launch per shape in
+                                    use; stages 0 = 4 */
     int32_t arith;               /* as od_config.arith (-1 = 10) */
     void *pool;                  /* caller device memory of hbm_budget_bytes, 256-byte
                                     aligned, or NULL: the server allocates it once */

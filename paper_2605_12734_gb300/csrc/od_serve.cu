@@ -148,6 +148,11 @@ struct od_server {
 
 namespace {
 
+// CTA shapes the planner picks from; with per-job shapes a step runs at most
+// one batched launch for each.
+constexpr int kShapes = 4;
+constexpr int32_t kAutoShapes[kShapes][2] = {{128, 4}, {128, 2}, {256, 4}, {256, 8}};
+
 od_config job_config(od_server *s, Job *j) {
     od_config c = j->cfg;
     for (int a = 0; a < 3; ++a) {
@@ -192,11 +197,17 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
         j->admitting = false;
         s->admit_seconds += s->now() - t_create;
         progress = true;
-        if (st != OD_OK || ctx->plan.stage_doubles * s->stages * 8 + 256 > s->smem_cap) {
+        bool known_shape = false;  // one of the shapes a step launches for (at most kShapes groups)
+        for (int g = 0; st == OD_OK && g < kShapes; ++g)
+            known_shape |= s->threads ? (ctx->plan.threads == s->threads && ctx->plan.cpt == s->cpt)
+                                      : (ctx->plan.threads == kAutoShapes[g][0] && ctx->plan.cpt == kAutoShapes[g][1]);
+        if (st != OD_OK || !known_shape || ctx->plan.stage_doubles * s->stages * 8 + 256 > s->smem_cap) {
             if (ctx) od_destroy(ctx);
             s->pool.release(j->off, j->bytes);
             j->state = OD_JOB_FAILED;
-            j->err = st == OD_OK ? "tile needs more shared memory than the server's launch shape" : msg;
+            j->err = st != OD_OK ? msg
+                     : !known_shape ? "the planner chose a CTA shape the server does not launch"
+                                    : "tile needs more shared memory than the server's launch shape";
             s->failed++;
             s->cv_done.notify_all();
             continue;
@@ -253,40 +264,70 @@ cudaEvent_t take_event(od_server *s) {
     return ev;
 }
 
-// One fused step of every running job that still has steps (lock held).
+// One fused step of every running job that still has steps (lock held):
+// one batched launch per CTA shape among them (one shape unless the server
+// lets the planner pick a shape per job).  The jobs of shape group g occupy
+// hk[jo[g] .. jo[g+1]) and their first-block prefix hf[jo[g] + g ..].
 bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf) {
     hk.clear();
     hf.clear();
-    int32_t grid = 0, max_sd = 0;
     std::vector<Job *> in;
-    for (Job *j : s->running) {
-        if (j->done_batch >= 0 || j->steps_enq >= j->iters) continue;
-        KArgs a = od::base_args(j->ctx);
-        a.tile_begin = 0;
-        a.parity = (int32_t)(j->steps_enq & 1);
-        a.stages = s->stages;
-        hk.push_back(a);
-        hf.push_back(grid);
-        grid += (int32_t)j->ctx->plan.tiles.size();
-        max_sd = std::max(max_sd, j->ctx->plan.stage_doubles);
-        in.push_back(j);
+    int32_t shapes[kShapes][2];
+    int ngroups = 0;
+    std::vector<int32_t> jo, grid, max_sd;
+    for (int g = 0; g < kShapes; ++g) {
+        int32_t nt = 0, ct = 0, tiles = 0, sd = 0;
+        const size_t first = in.size();
+        for (Job *j : s->running) {
+            if (j->done_batch >= 0 || j->steps_enq >= j->iters) continue;
+            const od::Plan &p = j->ctx->plan;
+            bool seen = false;  // shape already taken by an earlier group
+            for (int h = 0; h < ngroups; ++h) seen |= shapes[h][0] == p.threads && shapes[h][1] == p.cpt;
+            if (seen) continue;
+            if (in.size() == first) {
+                nt = p.threads;
+                ct = p.cpt;
+            } else if (p.threads != nt || p.cpt != ct) {
+                continue;
+            }
+            KArgs a = od::base_args(j->ctx);
+            a.tile_begin = 0;
+            a.parity = (int32_t)(j->steps_enq & 1);
+            a.stages = s->stages;
+            if (in.size() == first) jo.push_back((int32_t)first);
+            hk.push_back(a);
+            hf.push_back(tiles);
+            tiles += (int32_t)p.tiles.size();
+            sd = std::max(sd, p.stage_doubles);
+            in.push_back(j);
+        }
+        if (in.size() == first) break;
+        hf.push_back(tiles);
+        shapes[ngroups][0] = nt;
+        shapes[ngroups][1] = ct;
+        grid.push_back(tiles);
+        max_sd.push_back(sd);
+        ++ngroups;
     }
     if (in.empty()) return false;
-    hf.push_back(grid);
+    jo.push_back((int32_t)in.size());
     const int slot = (int)(s->next_batch & 1);
     cudaMemcpyAsync(s->d_jobs[slot], hk.data(), hk.size() * sizeof(KArgs), cudaMemcpyHostToDevice, s->compute);
     cudaMemcpyAsync(s->d_first[slot], hf.data(), hf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s->compute);
-    const int smem = 256 + s->stages * max_sd * 8;
     cudaEvent_t ev0 = take_event(s);
     cudaEventRecord(ev0, s->compute);
-    cudaError_t e = od::launch_tiles_multi(s->d_jobs[slot], s->d_first[slot], (int32_t)in.size(), grid, s->threads,
-                                           s->cpt, s->arith, smem, OD_STENCIL_3D7, s->compute);
-    if (e != cudaSuccess) {
-        s->free_events.push_back(ev0);
-        s->worker_error = std::string("k_tiles_multi: ") + cudaGetErrorString(e);
-        return false;
+    for (int g = 0; g < ngroups; ++g) {
+        const int smem = 256 + s->stages * max_sd[(size_t)g] * 8;
+        cudaError_t e = od::launch_tiles_multi(s->d_jobs[slot] + jo[(size_t)g], s->d_first[slot] + jo[(size_t)g] + g,
+                                               jo[(size_t)g + 1] - jo[(size_t)g], grid[(size_t)g], shapes[g][0],
+                                               shapes[g][1], s->arith, smem, OD_STENCIL_3D7, s->compute);
+        if (e != cudaSuccess) {
+            s->free_events.push_back(ev0);
+            s->worker_error = std::string("k_tiles_multi: ") + cudaGetErrorString(e);
+            return false;
+        }
+        s->launches++;
     }
-    s->launches++;
     const int64_t idx = s->next_batch++;
     for (Job *j : in) {
         j->steps_enq++;
@@ -362,8 +403,10 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
     od_server *s = new od_server();
     s->cfg = *cfg;
     s->device = cfg->device;
-    s->threads = cfg->threads ? cfg->threads : 128;
-    s->cpt = cfg->cells_per_thread ? cfg->cells_per_thread : 4;
+    // both 0: per-job shapes chosen by the planner; one given: the other defaults
+    const bool auto_shape = cfg->threads == 0 && cfg->cells_per_thread == 0;
+    s->threads = auto_shape ? 0 : cfg->threads ? cfg->threads : 128;
+    s->cpt = auto_shape ? 0 : cfg->cells_per_thread ? cfg->cells_per_thread : 4;
     s->stages = cfg->stages ? cfg->stages : 4;
     s->arith = cfg->arith >= 0 ? cfg->arith : 10;
     s->max_jobs = cfg->max_jobs_per_launch > 0 ? cfg->max_jobs_per_launch : 256;
@@ -373,7 +416,11 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
         return fail(st, m);
     };
     if (cudaSetDevice(s->device) != cudaSuccess) return bail(OD_ECUDA, "cannot select the CUDA device");
-    if (!od::tile_shape_supported(s->threads, s->cpt, s->arith, OD_STENCIL_3D7)) return bail(OD_EINVAL, "unsupported tile shape");
+    for (int g = 0; g < kShapes; ++g) {
+        const int nt = s->threads ? s->threads : kAutoShapes[g][0], ct = s->threads ? s->cpt : kAutoShapes[g][1];
+        if (!od::tile_shape_supported(nt, ct, s->arith, OD_STENCIL_3D7)) return bail(OD_EINVAL, "unsupported tile shape");
+        if (s->threads) break;  // one fixed shape
+    }
     if (cfg->pool) {
         if ((uintptr_t)cfg->pool & 255u) return bail(OD_EINVAL, "pool must be 256-byte aligned");
         s->pool_base = (char *)cfg->pool;
@@ -391,11 +438,15 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
         return bail(OD_ECUDA, "cannot create streams");
     for (int k = 0; k < 2; ++k)
         if (cudaMalloc(&s->d_jobs[k], (size_t)s->max_jobs * sizeof(KArgs)) != cudaSuccess ||
-            cudaMalloc(&s->d_first[k], (size_t)(s->max_jobs + 1) * sizeof(int32_t)) != cudaSuccess)
+            cudaMalloc(&s->d_first[k], (size_t)(s->max_jobs + kShapes) * sizeof(int32_t)) != cudaSuccess)
             return bail(OD_ENOMEM, "cannot allocate launch tables");
     s->smem_cap = 200 * 1024;
-    if (od::prepare_tile_kernels(s->threads, s->cpt, s->arith, s->smem_cap, OD_STENCIL_3D7) != cudaSuccess)
-        return bail(OD_ECUDA, "cannot configure the tile kernels");
+    for (int g = 0; g < kShapes; ++g) {
+        if (s->threads && g > 0) break;  // one fixed shape
+        const int nt = s->threads ? s->threads : kAutoShapes[g][0], ct = s->threads ? s->cpt : kAutoShapes[g][1];
+        if (od::prepare_tile_kernels(nt, ct, s->arith, s->smem_cap, OD_STENCIL_3D7) != cudaSuccess)
+            return bail(OD_ECUDA, "cannot configure the tile kernels");
+    }
     s->worker = std::thread(worker_main, s);
     s->admitter = std::thread(admitter_main, s);
     *out = s;

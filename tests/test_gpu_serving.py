@@ -66,6 +66,27 @@ def test_jobs_in_the_mix_match_alone_and_oracle(od):
             assert same(results[jid], alone.read())
 
 
+def test_jobs_of_three_cta_shapes_in_one_step(od):
+    # the planner gives these jobs 128 x 4, 256 x 4 and 128 x 2 CTAs; every
+    # step runs one batched launch per shape, and each result is still the
+    # oracle's
+    jobs = [((240, 240, 240), (2, 2, 2), 6, 21), ((600, 20, 16), (2, 1, 1), 9, 22), ((40, 40, 40), (2, 2, 2), 7, 23),
+            ((600, 20, 16), (2, 1, 1), 4, 24)]
+    for dims, sp, _, _ in jobs[:3]:
+        assert od.plan(*dims, split=sp)["threads"] * od.plan(*dims, split=sp)["cells_per_thread"] in (256, 512, 1024)
+    with od.Server(1 << 30) as srv:
+        ids = [srv.submit(*dims, it, split=sp, seed=seed) for dims, sp, it, seed in jobs]
+        got = []
+        for jid in ids:
+            assert srv.wait(jid, 120.0) == od._native.OD_JOB_DONE, srv.info(jid)
+            got.append(srv.fetch(jid))
+            srv.release(jid)
+        st = srv.stats()
+    assert st["launches"] > max(j[2] for j in jobs)  # more than one launch per step while shapes overlap
+    for res, (dims, sp, it, seed) in zip(got, jobs):
+        assert same(res, oracle.solve(*dims, seed, 1, it)), dims
+
+
 def test_budget_admission_and_release(od):
     e, sp = 48, (2, 2, 2)
     need = od.plan(e, e, e, split=sp, threads=128, cells_per_thread=4, stages=4, arith=7)["arena_bytes"]
