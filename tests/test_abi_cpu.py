@@ -261,3 +261,10 @@ def test_read_cells_checks_arguments_first(od):
     cells = (ctypes.c_int64 * 1)(0)
     assert L.od_read_cells(None, cells, 1, ctypes.byref(d)) == od._native.OD_EINVAL  # no context
     assert L.od_read_cells(None, None, 0, None) == od._native.OD_EINVAL
+
+
+def test_async_transfers_check_arguments_first(od):
+    L = od.lib()
+    buf = (ctypes.c_double * 8)()
+    assert L.od_write_async(None, buf) == od._native.OD_EINVAL
+    assert L.od_read_async(None, buf) == od._native.OD_EINVAL
