@@ -218,7 +218,9 @@ def _time_oracle(sweep, cells: int, target_s: float):
         t1 = timed(n1)
     n2 = max(n1 + 1, int(n1 * target_s / t1))
     t2 = timed(n2)
-    rate = (n2 - n1) * cells / max(t2 - t1, 1e-9)
+    if t2 - t1 < 0.25 * t2 * (n2 - n1) / n2:  # noise swamped the difference: count the whole call
+        return n2 * cells / t2, n2, t2
+    rate = (n2 - n1) * cells / (t2 - t1)
     return rate, n2, t2
 
 
@@ -265,27 +267,28 @@ def run_reference(args):
     oracle.build()
     threads = oracle.max_threads()
     P = oracle.init_padded(edge, edge, edge, 2, inputs.INIT_UNIFORM)
-    # each "step" is one oracle iteration over the full grid; a bounded
-    # number of them keeps the run to a few minutes.  Every oracle call copies
-    # the field once, so the time of k steps is that of a (w + k)-iteration
-    # call less that of the w-iteration warm-up call.
-    k = min(args.steps, 30)
+    # Each "step" is a bounded sample: m oracle iterations over the full grid,
+    # m sized to about a second of CPU work.  Every oracle call copies the
+    # field and touches fresh pages, so the rate comes from calls of growing
+    # length (the difference of the last two cancels that one-off cost),
+    # over about K seconds of oracle work in all (4 at least, 40 at most).
+    K = max(1, args.steps)
     w = max(1, min(args.warmup, 3))
-    t0 = time.perf_counter()
-    oracle.sweep(P, w, threads)
-    t1 = time.perf_counter()
-    oracle.sweep(P, w + k, threads)
-    t2 = time.perf_counter()
-    dt = max((t2 - t1) - (t1 - t0), 1e-9)
-    ups = edge ** 3 * k / dt
+    oracle.sweep(P, w, threads)  # warm-up: OpenMP threads, the library's pages
+    ups, _, _ = _time_oracle(lambda n: oracle.sweep(P, n, threads), edge ** 3, float(min(max(K, 4), 40)))
+    m = max(1, int(round(ups / edge ** 3)))  # iterations in about a second
+    k = K
+    dt = K * m * edge ** 3 / ups
     line = {"impl": "reference", "metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": args.gpus,
             "steps": k, "warmup": w, "ms_per_step": dt * 1e3 / k, "higher_is_better": True,
+            "iters_per_step": m,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"jacobi3d-{edge}^3-odf{args.odf}", "nx": edge, "ny": edge, "nz": edge,
                        "odf": args.odf, "note": "CPU oracle (undecomposed sweep; same bits for any ODF)"},
             "cpu_baseline": {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{edge}^3 field, {k} iterations on {threads} threads (difference "
-                                       f"of a {w + k}- and a {w}-iteration call)"},
+                             "sample": f"{edge}^3 field, steps of {m} iterations on {threads} threads; rate "
+                                       f"from the difference of oracle calls of growing length over about "
+                                       f"{min(max(K, 4), 40)} s"},
             "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
