@@ -41,12 +41,14 @@
  *   - returns OD_OK or an error code; never aborts the process; the message of
  *     the last error on the calling thread is od_last_error();
  *   - device pointers are plain CUDA device addresses of the context's device;
- *     host pointers are ordinary (pageable or pinned) host memory;
+ *     host pointers are ordinary (pageable or pinned) host memory, except for
+ *     od_write_async / od_read_async, which take pinned memory only;
  *   - the caller owns every buffer it passes; the library owns everything it
  *     allocates and frees it in od_destroy;
- *   - work is enqueued on the context's stream; od_read, od_sync and od_stats
- *     synchronise that stream and report device-side errors (OD_ETIMEOUT for a
- *     bounded wait that ran out, OD_ECUDA for a CUDA error);
+ *   - work is enqueued on the context's stream; od_read, od_read_cells,
+ *     od_sync and od_stats_get synchronise that stream (and the copy stream
+ *     of a pending od_read_async) and report device-side errors (OD_ETIMEOUT
+ *     for a bounded wait that ran out, OD_ECUDA for a CUDA error);
  *   - one context is used by one host thread at a time (calls on the same
  *     od_ctx must not overlap); different contexts, and every od_server_*
  *     call, may be used from any threads concurrently.
