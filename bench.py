@@ -234,10 +234,13 @@ def oracle_cpu_baseline(edge: int, target_s: float = 10.0):
     threads = oracle.max_threads()
     P = oracle.init_padded(edge, edge, edge, 2, inputs.INIT_UNIFORM)
     ups, iters, dt = _time_oracle(lambda n: oracle.sweep(P, n, threads), edge ** 3, target_s)
+    ups1, iters1, dt1 = _time_oracle(lambda n: oracle.sweep(P, n, 1), edge ** 3, target_s / 2)
     return {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{edge}^3 field (U[0,1), seed 2), undecomposed C oracle sweep on {threads} OpenMP threads; "
                       f"rate from the difference of calls of increasing length, the last {iters} "
-                      f"iterations in {dt:.1f} s"}
+                      f"iterations in {dt:.1f} s",
+            "single_core": {"value": ups1, "unit": UNIT, "cores": 1,
+                            "sample": f"the same on one thread, the last {iters1} iterations in {dt1:.1f} s"}}
 
 
 def oracle_cpu_baseline_2d(edge: int, target_s: float = 10.0):
