@@ -150,8 +150,8 @@ constexpr int kSmemRing = 256;   // first ring slot (matches the planner's heade
 static_assert(sizeof(PushInfo) <= kSmemRing - kSmemPush, "push info overflows the header");
 
 // Per-cell word: bits 0-15 ring-slot offset r of the cell, 16-26 tile row j,
-// 27 the slot holds a real cell (its result is stored), 28/29/30/31 the cell
-// lies on a face with an x-/x+/y-/y+ neighbour.
+// 27 the slot holds a real cell (not a copy of cell 0 past the tile's end),
+// 28/29/30/31 the cell lies on a face with an x-/x+/y-/y+ neighbour.
 constexpr uint32_t kValid = 1u << 27;
 constexpr uint32_t kXlo = 1u << 28, kXhi = 1u << 29, kYlo = 1u << 30, kYhi = 1u << 31;
 
