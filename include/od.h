@@ -238,23 +238,39 @@ OD_API od_status od_plan_tiles(const od_config *cfg, int64_t *tiles, int64_t til
 
 /* Allocate device state on cfg->device, build the chare/tile tables, tune if
  * asked, and write the initial field (u^0) including every ghost layer.
- * Synchronous.  *out is NULL on error. */
+ * Synchronous.  *out is NULL on error.
+ * Defined by: the paper's Sec. III "Managing Overdecomposition" (many chares
+ * of one application share one GPU; device memory and execution resources
+ * are set up once, Sec. III "Using Kokkos in charm++ runtime") and Sec. IV
+ * (the pre-filled location table: here the neighbour table built from the
+ * decomposition). */
 OD_API od_status od_create(od_ctx **out, const od_config *cfg);
 
 /* Enqueue `iters` >= 0 Jacobi iterations on the context's stream with its
  * current path.  Asynchronous: returns once the work is enqueued.  No
  * allocation and no host synchronisation happen inside (the graph path
- * captures its graph on the first call). */
+ * captures its graphs on the first call).
+ * Defined by: Sec. V "jacobi2d" (Jacobi iterations with a halo exchange
+ * between chares, a fixed count, no convergence check), each chare's
+ * per-iteration work -- pack, intra-process delivery, unpack, compute --
+ * from Sec. III "Managing Overdecomposition" and Sec. IV item 1
+ * (intra-process transfers as device-to-device copies). */
 OD_API od_status od_step(od_ctx *ctx, int32_t iters);
 
 /* Select the execution path for later od_step calls (any path continues the
- * same iteration sequence). */
+ * same iteration sequence).  The paths are the flows of Sec. III (per-chare
+ * streams) and Sec. I (kernel fusion and CUDA graphs, prior work). */
 OD_API od_status od_set_path(od_ctx *ctx, int32_t path);
 
-/* Wait for all enqueued work; reports device-side errors. */
+/* Wait for all enqueued work; reports device-side errors.  (Sec. III "Using
+ * Kokkos in charm++ runtime": the library never fences implicitly; this is
+ * the one explicit wait besides the reads.) */
 OD_API od_status od_sync(od_ctx *ctx);
 
-/* Copy the current field u^{steps_done} (interior only, x fastest,
+/* Defined by: Sec. V "jacobi2d" (the field the iterations produce; the
+ * paper gives no output format, so the interior is returned in the
+ * undecomposed grid's order).
+ * Copy the current field u^{steps_done} (interior only, x fastest,
  * nx*ny*nz doubles) to dst.  dst_is_device != 0: dst is device memory of the
  * context's device; otherwise host memory: pinned (page-locked) host memory
  * is written in place by the gather kernel over the host link, pageable
@@ -269,7 +285,10 @@ OD_API od_status od_read(od_ctx *ctx, double *dst, int32_t dst_is_device);
  * grid. */
 OD_API od_status od_read_cells(od_ctx *ctx, const int64_t *cells, int64_t n, double *out);
 
-/* Replace the current field's interior with src (nx*ny*nz doubles, x fastest;
+/* Defined by: Sec. II "Charm++ and Overdecomposition" (chares migrate, so
+ * their state must be exported and restored: od_read and this call) and
+ * Sec. V "jacobi2d" (the iterated field); the layout is od_read's.
+ * Replace the current field's interior with src (nx*ny*nz doubles, x fastest;
  * device memory, or host memory copied through the staging buffer) and
  * refresh every internal ghost layer; the
  * Dirichlet shell is kept.  Used to import a checkpoint or a user field.
@@ -307,7 +326,9 @@ OD_API od_status od_read_async(od_ctx *ctx, double *dst);
  * the ghost layers of a shard's domain faces: import them after it. */
 OD_API od_status od_face_copy(od_ctx *ctx, int32_t face, int32_t dir, double *buf, int32_t buf_is_device);
 
-/* Counters and the plan; synchronises and reports device-side errors. */
+/* Counters and the plan; synchronises and reports device-side errors.  The
+ * launch and API-call counts are the quantities Sec. III measures (kernel
+ * launch cost per chare). */
 OD_API od_status od_stats_get(od_ctx *ctx, od_stats *out);
 
 /* Fault injection for tests: on the persistent path, tile `tile` never
@@ -528,7 +549,9 @@ OD_API od_status od_server_destroy(od_server *s);
 OD_API od_status od_jacobi_noalloc(const double *u_in, double *u_out, int64_t nx, int64_t ny, int64_t nz,
                                    int32_t iters, void *stream);
 
-/* Free everything the context owns (synchronises first).  NULL is allowed. */
+/* Free everything the context owns (synchronises first).  NULL is allowed.
+ * Defined by: Sec. III "Using Kokkos in charm++ runtime" (device state is
+ * created once and released once, never inside the iterations). */
 OD_API od_status od_destroy(od_ctx *ctx);
 
 /* Message of the last failed call on this thread ("" if none). */
