@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--edge", type=int, default=512)
     ap.add_argument("--edge2d", type=int, default=32768, help="jacobi2d: grid edge (the paper's 32768)")
     ap.add_argument("--path", default="persistent",
-                    choices=["per_chare", "fused", "graph", "persistent"])
+                    choices=["per_chare", "fused", "graph", "persistent", "fused_graph"])
     ap.add_argument("--baseline-steps", type=int, default=3,
                     help="timed steps of the per-chare-launch baseline at the same ODF (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -58,6 +58,8 @@ def parse():
                     help="also time every path at every ODF (adds a 'sweep' key; on by default for the odf "
                          "workload at N=1)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the default ODF sweep")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the default run's other workloads (uneven, ceiling, serving)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (default: od_create times candidate execution shapes first)")
     ap.add_argument("--threads", type=int, default=0)
@@ -149,10 +151,10 @@ FLOPS_PER_UPDATE = 6  # 5 additions + 1 division
 FLOPS_PER_UPDATE_2D = 4  # 3 additions + 1 division
 
 
-def profiled_traffic(args, plan):
-    """DRAM bytes per step of the tile kernel from the committed ncu summary
-    (profiles/traffic_*.json) when it was taken on this exact kernel build and
-    workload; None otherwise."""
+def profiled_kernel(args, plan):
+    """The committed ncu summary of the tile kernel (profiles/traffic_*.json:
+    DRAM bytes per step, thread instructions per update) when it was taken
+    on this exact kernel revision, shape and workload; None otherwise."""
     if args.workload == "jacobi2d":
         name = f"traffic_{args.path}2d_{args.edge2d}sq_odf{args.odf}.json"
     elif args.workload == "odf":
@@ -168,11 +170,11 @@ def profiled_traffic(args, plan):
     if d.get("arith") != plan["arith"] or d.get("threads") != plan["threads"] or \
             d.get("cells_per_thread") != plan["cells_per_thread"] or d.get("kernel_rev") != rev:
         return None
-    return d["dram_bytes_per_step"]
+    return d
 
 
 # bumped whenever a tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 12     # 3D 7-point
+KERNEL_REV = 13     # 3D 7-point
 KERNEL_REV_2D = 13  # 2D 5-point
 
 
@@ -190,6 +192,16 @@ def combine_ranks(ms: float, updates: float, world: int, device: str):
         dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
         ms, updates = float(tmax[0].item()), float(tsum[1].item())
     return ms, updates / (ms * 1e-3)
+
+
+def workload_config(name: str, dims, odf: int, stencil: str, seed: int, world: int) -> dict:
+    """The workload's description, identical in both arms' lines (the
+    execution shape of our arm goes under the line's separate "launch")."""
+    cells = dims[0] * dims[1] * dims[2]
+    return {"workload": name, "nx": dims[0], "ny": dims[1], "nz": dims[2], "odf": odf, "stencil": stencil,
+            "seed": seed, "init": "U[0,1) everywhere, Dirichlet shell fixed",
+            "l2": f"no flush: the two parity buffers ({2 * 8 * cells / 2**30:.1f} GiB) far exceed the 129 MB L2",
+            "parallelism": f"replicas x{world}"}
 
 
 def measured_peaks():
@@ -224,10 +236,13 @@ def _time_oracle(sweep, cells: int, target_s: float):
     return rate, n2, t2
 
 
-def oracle_cpu_baseline(edge: int, target_s: float = 10.0):
+def oracle_cpu_baseline(edge: int, target_s: float = 10.0, e2e_out=None, e2e_iters: int = 100):
     """Time the CPU oracle's monolithic sweep (its OpenMP z-plane split) on a
     bounded sample of the same workload: the full edge^3 field, iterated for
-    about target_s seconds."""
+    about target_s seconds.  With e2e_out (the end-to-end run's last result,
+    u^e2e_iters of the same field), also solve that job on the oracle and
+    compare every cell."""
+    import numpy as np
     import oracle
     from paper_2605_12734_gb300 import inputs
     oracle.build()
@@ -235,12 +250,19 @@ def oracle_cpu_baseline(edge: int, target_s: float = 10.0):
     P = oracle.init_padded(edge, edge, edge, 2, inputs.INIT_UNIFORM)
     ups, iters, dt = _time_oracle(lambda n: oracle.sweep(P, n, threads), edge ** 3, target_s)
     ups1, iters1, dt1 = _time_oracle(lambda n: oracle.sweep(P, n, 1), edge ** 3, target_s / 2)
-    return {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{edge}^3 field (U[0,1), seed 2), undecomposed C oracle sweep on {threads} OpenMP threads; "
-                      f"rate from the difference of calls of increasing length, the last {iters} "
-                      f"iterations in {dt:.1f} s",
-            "single_core": {"value": ups1, "unit": UNIT, "cores": 1,
-                            "sample": f"the same on one thread, the last {iters1} iterations in {dt1:.1f} s"}}
+    out = {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{edge}^3 field (U[0,1), seed 2), undecomposed C oracle sweep on {threads} OpenMP threads; "
+                     f"rate from the difference of calls of increasing length, the last {iters} "
+                     f"iterations in {dt:.1f} s",
+           "single_core": {"value": ups1, "unit": UNIT, "cores": 1,
+                           "sample": f"the same on one thread, the last {iters1} iterations in {dt1:.1f} s"}}
+    if e2e_out is not None:
+        t0 = time.perf_counter()
+        want = oracle.solve(edge, edge, edge, 2, inputs.INIT_UNIFORM, e2e_iters, threads)
+        out["e2e_oracle_seconds"] = time.perf_counter() - t0
+        diff = int(np.count_nonzero(np.ascontiguousarray(e2e_out).view(np.uint64) != want.view(np.uint64)))
+        out["e2e_cells_differing_from_oracle"] = diff
+    return out
 
 
 def oracle_cpu_baseline_2d(edge: int, target_s: float = 10.0):
@@ -276,18 +298,19 @@ def run_reference(args):
     # length (the difference of the last two cancels that one-off cost),
     # over about K seconds of oracle work in all (4 at least, 40 at most).
     K = max(1, args.steps)
-    w = max(1, min(args.warmup, 3))
-    oracle.sweep(P, w, threads)  # warm-up: OpenMP threads, the library's pages
+    W = max(0, args.warmup)
+    oracle.sweep(P, max(1, min(W, 3)), threads)  # warm-up: OpenMP threads, the library's pages
     ups, _, _ = _time_oracle(lambda n: oracle.sweep(P, n, threads), edge ** 3, float(min(max(K, 4), 40)))
     m = max(1, int(round(ups / edge ** 3)))  # iterations in about a second
-    k = K
     dt = K * m * edge ** 3 / ups
     line = {"impl": "reference", "metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": k, "warmup": w, "ms_per_step": dt * 1e3 / k, "higher_is_better": True,
+            "steps": K, "warmup": W, "ms_per_step": dt * 1e3 / K, "higher_is_better": True,
             "iters_per_step": m,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"jacobi3d-{edge}^3-odf{args.odf}", "nx": edge, "ny": edge, "nz": edge,
-                       "odf": args.odf, "note": "CPU oracle (undecomposed sweep; same bits for any ODF)"},
+            "config": workload_config(f"jacobi3d-{edge}^3-odf{args.odf}", (edge, edge, edge), args.odf, "3d7", 2,
+                                      args.gpus),
+            "note": "CPU oracle: the undecomposed sweep, which gives the same bits for any ODF; a step is "
+                    f"{m} oracle iterations (about a second)",
             "cpu_baseline": {"value": ups, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{edge}^3 field, steps of {m} iterations on {threads} threads; rate "
                                        f"from the difference of oracle calls of growing length over about "
@@ -412,73 +435,67 @@ def run_ours(args):
     updates_step = plan["cells"]
     launches = st1["kernel_launches"] - st0["kernel_launches"]
 
-    # roofline of the tile kernel (it does all of a step's arithmetic and HBM
-    # traffic).  On GB300 the update is bound by arithmetic, not by HBM: the
-    # method needs 5 FP64 adds + 1 FP64 division per cell (6 flops), and the
-    # GPU's FP64 rate is 1.25 TFLOP/s nominal.  The kernel runs fp64_adds(m) of
-    # the adds on the FP64 pipe and the rest, with the division, exactly on
-    # the integer pipes.
-    if two_d:  # 3 adds; modes 4..6 all run the three adds in the window
-        fp64_adds = {0: 3, 1: 3, 2: 2, 3: 1, 4: 0, 5: 0, 6: 0, 7: 1.5, 8: 1.75, 9: 2, 10: 1, 11: 1.5}[plan["arith"]]
+    # roofline of the tile kernel (it does all of a step's arithmetic and all
+    # of its HBM traffic): the stencil's own roof is HBM, with the
+    # algorithmic bytes of a step (16 B per cell + 16 B per internal ghost
+    # cell + 8 B per Dirichlet ghost cell) over the measured copy bandwidth.
+    # Beside it, flat keys for the two pipes the exact FP64 arithmetic loads:
+    # the FP64 pipe (adds issued there, 1 per lane-cycle, 2 lanes per SM) and
+    # the issue ports (thread instructions per update from the kernel's ncu
+    # capture, 4 x 32 per SM-cycle), both at the SM clock sampled under load.
+    if two_d:
+        fp64_adds = {0: 3, 1: 3, 2: 2, 3: 1, 4: 0, 5: 0, 6: 0, 7: 1.5, 8: 1.75, 9: 2, 10: 1, 11: 1.5,
+                     12: 1, 13: 0, 14: 0.5, 15: 2}[plan["arith"]]
     else:
         fp64_adds = {0: 5, 1: 5, 2: 4, 3: 3, 4: 2, 5: 1, 6: 0, 7: 3.5, 8: 3.75, 9: 4, 10: 3,
-                     11: 3.5}[plan["arith"]]
-    fpu = FLOPS_PER_UPDATE_2D if two_d else FLOPS_PER_UPDATE
-    fp64_pipe = FP64_LANES_PER_SM * SMS * SM_MAX_GHZ  # G FP64 instructions/s
+                     11: 3.5, 12: 2, 13: 1, 14: 1.5, 15: 1.75}[plan["arith"]]
+    if plan["arith"] == 0:
+        fp64_adds += 8  # the IEEE division is a sequence of FP64 instructions
+    ghz = (clk.get("sm_mhz") or SM_MAX_GHZ * 1e3) / 1e3
     hbm_peak, peak_kind = measured_peaks()
     bytes_step = plan["bytes_per_step"]
     ups = updates_step / (ms_step * 1e-3)
-    hbm = {"achieved": bytes_step / (ms_step * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-           "frac": bytes_step / (ms_step * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
-           "bytes_per_step": bytes_step,
-           "note": "algorithmic bytes: 16 B/cell + 16 B per internal ghost cell + 8 B per Dirichlet ghost cell"}
-    nadd = 3 if two_d else 5
-    roofline = {"bound": "alu", "achieved": fpu * ups / 1e9, "peak": FP64_NOMINAL_GFLOPS,
-                "unit": "GFLOP/s", "frac": fpu * ups / 1e9 / FP64_NOMINAL_GFLOPS, "traffic": None,
-                "note": (f"algorithmic FP64 work: {nadd} adds + 1 division per update; peak: GB300 FP64 "
-                         "1.25 TFLOP/s nominal (recipe), = 2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz x 2 flops "
-                         f"per FMA; this kernel runs {fp64_adds} adds per update on the FP64 pipe and the rest "
-                         "with the division, bit-exactly, on the integer pipes"),
-                "fp64_pipe": {"adds_per_update": fp64_adds, "peak_ginst_per_s": fp64_pipe,
-                              "busy_frac_est": fp64_adds * ups / 1e9 / fp64_pipe},
-                "hbm": hbm}
-    if two_d and hbm["frac"] > roofline["frac"]:
-        # the 2D update is light enough that HBM is the nearer roof
-        roofline = {"bound": "hbm", "achieved": hbm["achieved"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm["frac"], "traffic": None, "peak_kind": peak_kind,
-                    "note": hbm["note"] + "; the FP64 roof is reported under 'alu'",
-                    "alu": {"achieved": fpu * ups / 1e9, "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s",
-                            "frac": fpu * ups / 1e9 / FP64_NOMINAL_GFLOPS,
-                            "fp64_adds_per_update": fp64_adds}}
-    traffic = profiled_traffic(args, plan)
-    if traffic is not None:
+    achieved = bytes_step / (ms_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                "bytes_per_step": bytes_step,
+                "note": "algorithmic bytes per step: 16 B/cell + 16 B per internal ghost cell + 8 B per Dirichlet "
+                        "ghost cell; peak: measured copy bandwidth (MEASURED_PEAKS.json)"}
+    prof = profiled_kernel(args, plan)
+    if prof is not None and prof.get("dram_bytes_per_step"):
         # the timed region is one persistent launch of args.steps iterations
         per_launch = args.steps if args.path == "persistent" else 1
-        roofline["traffic"] = traffic * per_launch
-        roofline["traffic_per_step"] = traffic
-        roofline["traffic_vs_algorithmic"] = traffic / bytes_step
-        roofline["traffic_note"] = ("DRAM read+write bytes per launch of the timed region, from one ncu "
-                                    "capture of this kernel build (profiles/traffic_*.json), scaled by its "
-                                    "iterations per launch")
+        roofline["traffic"] = prof["dram_bytes_per_step"] * per_launch
+        roofline["traffic_per_step"] = prof["dram_bytes_per_step"]
+        roofline["traffic_vs_algorithmic"] = prof["dram_bytes_per_step"] / bytes_step
+    fp64_peak = FP64_LANES_PER_SM * SMS * ghz  # G FP64 lane-operations per second
+    flat = {"hbm_frac": achieved / hbm_peak, "hbm_achieved_gbps": achieved,
+            "alu_fp64_frac": fp64_adds * ups / 1e9 / fp64_peak, "fp64_ops_per_update": fp64_adds,
+            "issue_frac": None, "inst_per_update": None, "sm_ghz_used": ghz}
+    if prof is not None and prof.get("thread_inst_per_update"):
+        flat["inst_per_update"] = prof["thread_inst_per_update"]
+        flat["issue_frac"] = prof["thread_inst_per_update"] * ups / (SMS * 4 * 32 * ghz * 1e9)
 
     # end to end through the public API with pinned host buffers: each e2e
-    # step is a whole solve of the config's 100 iterations: import the initial
-    # field (H2D), iterate, export the result (D2H).  Two contexts run as a
-    # pipeline, as a serving loop would: one job's copies (copy engines) run
-    # under the other job's iterations.  A job's iterations start after the
-    # previous job's gather kernel (an event), so that short kernel is not
-    # left queued behind a whole persistent launch.
-    e2e = None
+    # step is a whole solve of 100 iterations from the config's initial
+    # field: import it (H2D), iterate, export the result (D2H).  Two contexts
+    # run as a pipeline, as a serving loop would: one job's copies (copy
+    # engines) run under the other job's iterations.  A job's iterations
+    # start after the previous job's gather kernel (an event), so that short
+    # kernel is not left queued behind a whole persistent launch.  Every job
+    # computes u^100 of the same field, which the CPU baseline's oracle solve
+    # checks below.
+    e2e, e2e_flat, e2e_last = None, {}, None
     if not args.no_e2e:
         import numpy as np
         n = plan["cells"]
         host_in = torch.empty(n, dtype=torch.float64, pin_memory=True)
         host_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
-        solver.read(host_in.numpy())       # a valid field to feed back in
         iters_job = 100
         reps = 16                          # the pipeline's fill and drain amortised over 16 jobs
         stream2 = torch.cuda.Stream(dev)
         twin = make(args.path, stream=stream2.cuda_stream, **tune_kw)
+        twin.read(host_in.numpy())         # the initial field u^0
         ctx, strm = (solver, twin), (stream, stream2)
         # the host link's bandwidth right now (the host is shared): one copy each way
         probe = torch.empty(min(n, 1 << 27), dtype=torch.float64, device=dev)
@@ -524,18 +541,21 @@ def run_ours(args):
         ctx[(reps - 1) % 2].read_async(host_out)
         ctx[(reps - 1) % 2].sync()
         dt = time.perf_counter() - t0
-        same = bool(np.array_equal(host_out.numpy().view(np.uint64), first.view(np.uint64)))
+        e2e_last = host_out.numpy().copy()
+        same = bool(np.array_equal(e2e_last.view(np.uint64), first.view(np.uint64)))
         twin.close()
+        it_ms = sum(a.elapsed_time(b) for a, b in spans) / len(spans)
+        gaps = np.diff(marks) * 1e3
         e2e = {"value": n * iters_job * reps * world / dt, "unit": UNIT,
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
                "iters_per_step": iters_job, "jobs": reps, "results_identical": same,
-               "host_link_GBps": {"h2d": round(link[0], 1), "d2h": round(link[1], 1)},
-               "iterations_ms_per_job": round(sum(a.elapsed_time(b) for a, b in spans) / len(spans), 3),
-               "wall_ms_per_job": round(dt / reps * 1e3, 3),
-               "job_interval_ms": {"median": round(float(np.median(np.diff(marks))) * 1e3, 3),
-                                   "max": round(float(np.max(np.diff(marks))) * 1e3, 3)},
-               "note": "e2e step = od_write_async(pinned host field) + od_step(100) + od_read_async(pinned host); "
+               "note": "e2e step = od_write_async(pinned host u^0) + od_step(100) + od_read_async(pinned host); "
                        "two contexts pipelined, so one job's host copies overlap the other's iterations"}
+        e2e_flat = {"e2e_host_link_h2d_gbps": round(link[0], 1), "e2e_host_link_d2h_gbps": round(link[1], 1),
+                    "e2e_iterations_ms_per_job": round(it_ms, 3), "e2e_wall_ms_per_job": round(dt / reps * 1e3, 3),
+                    "e2e_job_interval_median_ms": round(float(np.median(gaps)), 3),
+                    "e2e_job_interval_max_ms": round(float(np.max(gaps)), 3),
+                    "e2e_jobs_identical": same}
     solver.close()
 
     baseline = None
@@ -559,8 +579,8 @@ def run_ours(args):
         sweep = []
         for o in (1, 4, 16, 64, 256, 1024, 4096):
             w2 = inputs.jacobi2d_32768(o, edge=args.edge2d)
-            for path in ("fused", "persistent", "graph", "per_chare"):
-                k = args.steps if path in ("fused", "persistent") else max(2, min(10, args.steps))
+            for path in ("fused", "persistent", "fused_graph", "graph", "per_chare"):
+                k = args.steps if path in ("fused", "persistent", "fused_graph") else max(2, min(10, args.steps))
                 if path in ("graph", "per_chare") and o >= 1024:
                     k = 2
 
@@ -574,8 +594,8 @@ def run_ours(args):
     elif args.sweep and rank == 0:
         sweep = []
         for o in (1, 8, 64, 512, 4096):
-            for path in ("fused", "persistent", "graph", "per_chare"):
-                k = args.steps if path in ("fused", "persistent") else max(2, min(10, args.steps))
+            for path in ("fused", "persistent", "fused_graph", "graph", "per_chare"):
+                k = args.steps if path in ("fused", "persistent", "fused_graph") else max(2, min(10, args.steps))
                 if path in ("graph", "per_chare") and o >= 4096:
                     k = 2
                 ms_p, _, _ = time_path(pkg, edge, o, path, k, 2, stream, dict(device=dev))
@@ -585,29 +605,58 @@ def run_ours(args):
                               "eff_GBps": 16 * info["cells"] / (ms_p * 1e-3) / 1e9,
                               "alg_GBps": info["bytes_per_step"] / (ms_p * 1e-3) / 1e9})
 
+    # the metric's other workloads, one short run each beside the headline:
+    # the uneven 300-chare grid and the 1024^3 ceiling (same path, tuned),
+    # and a serving stream at a rate near saturation
+    legs = {}
+    if args.workload == "odf" and rank == 0 and world == 1 and not args.no_legs:
+        for key, w in (("uneven", inputs.uneven_768()), ("ceiling", inputs.ceiling_1024())):
+            def make_w(path, w=w, **kw):
+                dec_w = {"cuts": w.cuts} if w.cuts else {"split": w.split}
+                return pkg.Jacobi3D(w.nx, w.ny, w.nz, seed=w.seed, init_mode=1, path=path, **dec_w, **kw)
+            ms_w, _, st_w = time_path(pkg, 0, 0, args.path, args.steps, args.warmup, stream,
+                                      dict(device=dev, autotune=not args.no_tune), make=make_w)
+            info = st_w["plan"]
+            legs[f"{key}_updates_per_s"] = info["cells"] / (ms_w * 1e-3)
+            legs[f"{key}_ms_per_step"] = ms_w
+            legs[f"{key}_hbm_frac"] = info["bytes_per_step"] / (ms_w * 1e-3) / 1e9 / hbm_peak
+            legs[f"{key}_arith"] = info["arith"]
+        r = serve_stream(pkg, dev, 150, 120.0, args.budget_gb)
+        legs.update({"serve_p50_ms": r["p50_s"] * 1e3, "serve_p99_ms": r["p99_s"] * 1e3,
+                     "serve_updates_per_s": r["updates_per_s"], "serve_rate_per_s": r["rate_per_s"],
+                     "serve_jobs": r["jobs"], "serve_device_busy_frac": r["device_busy_frac"],
+                     "serve_offered_updates_per_s": r["offered_updates_per_s"]})
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_cpu_baseline_2d(dims[0]) if two_d else oracle_cpu_baseline(edge if args.workload == "odf" else 512)
+        if two_d:
+            cpu = oracle_cpu_baseline_2d(dims[0])
+        else:
+            cpu = oracle_cpu_baseline(edge if args.workload == "odf" else 512,
+                                      e2e_out=e2e_last if args.workload == "odf" else None)
+            if "e2e_cells_differing_from_oracle" in cpu:
+                e2e_flat["e2e_matches_oracle"] = cpu["e2e_cells_differing_from_oracle"] == 0
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": name, "nx": dims[0], "ny": dims[1], "nz": dims[2],
-                           "odf": plan["nchares"], "chare_edge": (edge // p) if args.workload == "odf" else None,
-                           "stencil": "2d5" if two_d else "3d7",
-                           "path": args.path, "seed": seed, "tuned": bool(st1.get("tuned")),
-                           "init": "U[0,1) everywhere, Dirichlet shell fixed",
-                           "l2": f"no flush: the two parity buffers ({plan['arena_bytes'] / 2**30:.1f} GiB "
-                                 f"with ghosts) far exceed the 129 MB L2",
-                           "parallelism": f"replicas x{world}",
-                           "tiling": {k: plan[k] for k in ("threads", "cells_per_thread", "stages", "arith",
-                                                           "tile_y", "tile_z", "smem_bytes", "ntiles")}},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk, "eff_GBps": 16 * updates_step / (ms_step * 1e-3) / 1e9,
+                "config": workload_config(name, dims, plan["nchares"], "2d5" if two_d else "3d7", seed, world),
+                "launch": {"path": args.path, "tuned": bool(st1.get("tuned")),
+                           "chare_edge": (edge // p) if args.workload == "odf" else None,
+                           **{k: plan[k] for k in ("threads", "cells_per_thread", "stages", "arith", "tile_y",
+                                                   "tile_z", "smem_bytes", "ntiles")}},
+                "roofline": roofline, **flat, "cpu_baseline": cpu, "e2e": e2e, **e2e_flat,
+                "e2e_frac_of_device": (e2e["value"] / value) if e2e else None, **legs,
+                "gpu_launches": launches, "clocks": clk, "eff_GBps": 16 * updates_step / (ms_step * 1e-3) / 1e9,
                 "per_chare_baseline": baseline}
         if sweep is not None:
             line["sweep"] = sweep
+            by = {(r["odf"], r["path"]): r["ms_per_step"] for r in sweep}
+            odfs = sorted({r["odf"] for r in sweep})
+            for pth in ("persistent", "fused", "fused_graph", "graph", "per_chare"):
+                if (odfs[0], pth) in by and (odfs[-1], pth) in by:
+                    line[f"sweep_{pth}_maxodf_vs_odf1"] = by[(odfs[-1], pth)] / by[(odfs[0], pth)]
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -734,24 +783,20 @@ def run_shards(args, pkg, torch, rank, dev):
     return 0
 
 
-def run_serve(args, pkg, torch, rank, world, dev):
-    """Serving stream: independent jobs arrive as a Poisson process (seeded),
-    each a cubic grid with edge log-uniform in [64, 384], ODF in {8, 27, 64,
-    216} and 10..200 iterations; the server admits them under the HBM budget
-    and batches every running job into one launch per iteration.  Reports
-    aggregate updates/s and p50/p99 job latency (completion - arrival)."""
+def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, arith=-1):
+    """Poisson arrivals of independent jobs into one server: each a cubic
+    grid with edge log-uniform in [64, 384], ODF in {8, 27, 64, 216} and
+    10..200 iterations (seeded); returns aggregate updates/s and the job
+    latencies (completion - arrival)."""
     from paper_2605_12734_gb300 import inputs
-    jobs = inputs.serving_stream(args.jobs, args.rate, seed=6)
-    budget = int(args.budget_gb * (1 << 30))
-    srv = pkg.Server(budget, device=dev, threads=args.threads, cells_per_thread=args.cpt,
-                     stages=args.stages, arith=args.arith)
+    jobs = inputs.serving_stream(n_jobs, rate, seed=6)
+    budget = int(budget_gb * (1 << 30))
+    srv = pkg.Server(budget, device=dev, threads=threads, cells_per_thread=cpt, stages=stages, arith=arith)
     # warm-up: one small job through the whole path
     w = srv.submit(64, 64, 64, 3, split=(2, 2, 2), seed=1)
     srv.wait(w, 60.0)
     srv.release(w)
     ids = {}
-    clocks = ClockSampler(dev)
-    clocks.start()
     t0 = time.perf_counter()
     busy0 = srv.stats()["busy_seconds"]
     for j in jobs:
@@ -771,25 +816,40 @@ def run_serve(args, pkg, torch, rank, world, dev):
         last_done = max(last_done, info["t_done"])
         upd += j.updates
         srv.release(jid)
-    clk = clocks.stop()
     st = srv.stats()
     srv.close()
     wall = last_done - first_submit
     lat_sorted = sorted(lat)
+
     def pct(q):
         return lat_sorted[min(len(lat_sorted) - 1, int(round(q * (len(lat_sorted) - 1))))]
-    line = {"metric": METRIC, "value": upd / wall, "unit": UNIT, "n_gpus": world, "steps": args.jobs,
-            "warmup": 1, "ms_per_step": wall * 1e3 / args.jobs, "higher_is_better": True, "scaling": "weak",
+    return {"updates_per_s": upd / wall, "p50_s": pct(0.50), "p99_s": pct(0.99), "mean_s": sum(lat) / len(lat),
+            "max_s": lat_sorted[-1], "wall_s": wall, "launches": st["launches"],
+            "pool_peak_gb": st["pool_peak"] / (1 << 30), "offered_updates_per_s": upd / jobs[-1].arrival_s,
+            "admit_seconds": st["admit_seconds"], "device_busy_frac": (st["busy_seconds"] - busy0) / wall,
+            "jobs": n_jobs, "rate_per_s": rate}
+
+
+def run_serve(args, pkg, torch, rank, world, dev):
+    """Serving stream: independent jobs arrive as a Poisson process (seeded),
+    each a cubic grid with edge log-uniform in [64, 384], ODF in {8, 27, 64,
+    216} and 10..200 iterations; the server admits them under the HBM budget
+    and batches every running job into one launch per iteration.  Reports
+    aggregate updates/s and p50/p99 job latency (completion - arrival)."""
+    clocks = ClockSampler(dev)
+    clocks.start()
+    r = serve_stream(pkg, dev, args.jobs, args.rate, args.budget_gb, args.threads, args.cpt, args.stages, args.arith)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": r["updates_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.jobs,
+            "warmup": 1, "ms_per_step": r["wall_s"] * 1e3 / args.jobs, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "jacobi3d-serving-poisson", "jobs": args.jobs, "rate_per_s": args.rate,
                        "edge": "log-uniform [64,384]", "odf": "{8,27,64,216}", "iters": "U[10,200]",
                        "budget_gb": args.budget_gb, "seed": 6, "note": "a step here is one job"},
-            "latency_p50_s": pct(0.50), "latency_p99_s": pct(0.99), "latency_mean_s": sum(lat) / len(lat),
-            "latency_max_s": lat_sorted[-1], "wall_s": wall, "launches": st["launches"],
-            "pool_peak_gb": st["pool_peak"] / (1 << 30), "offered_updates_per_s": upd / jobs[-1].arrival_s,
-            "admit_seconds": st["admit_seconds"],
-            "device_busy_frac": (st["busy_seconds"] - busy0) / wall,
-            "clocks": clk}
+            "latency_p50_s": r["p50_s"], "latency_p99_s": r["p99_s"], "latency_mean_s": r["mean_s"],
+            "latency_max_s": r["max_s"], "wall_s": r["wall_s"], "launches": r["launches"],
+            "pool_peak_gb": r["pool_peak_gb"], "offered_updates_per_s": r["offered_updates_per_s"],
+            "admit_seconds": r["admit_seconds"], "device_busy_frac": r["device_busy_frac"], "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

@@ -25,7 +25,11 @@
  *                       a CUDA graph and replayed (CUDA Graphs, Sec. I);
  *   OD_PATH_PERSISTENT  one launch for all iterations: CTAs take (step, tile)
  *                       tickets from a device queue and wait (bounded) on the
- *                       per-tile step counters of the tiles they read.
+ *                       per-tile step counters of the tiles they read;
+ *   OD_PATH_FUSED_GRAPH the fused path's step loop -- eight fused step kernels,
+ *                       parities alternating -- captured once as a CUDA graph
+ *                       and replayed (one-step graphs cover odd remainders):
+ *                       CUDA Graphs (Sec. I) applied on top of kernel fusion.
  *
  * Arithmetic (every path, bit-identical to an undecomposed sweep):
  *   u'[i,j,k] = (((((u[i-1]+u[i+1]) + u[j-1]) + u[j+1]) + u[k-1]) + u[k+1]) / 6.0
@@ -85,7 +89,8 @@ typedef enum {
     OD_PATH_PER_CHARE = 0,
     OD_PATH_FUSED = 1,
     OD_PATH_GRAPH = 2,
-    OD_PATH_PERSISTENT = 3
+    OD_PATH_PERSISTENT = 3,
+    OD_PATH_FUSED_GRAPH = 4
 } od_path;
 
 #define OD_INIT_ZERO_INTERIOR 0

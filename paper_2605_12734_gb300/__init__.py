@@ -116,13 +116,24 @@ def plan_tiles(nx, ny, nz, **kw):
     return tiles[:, :7], ptr, idx[:nd.value]
 
 
+def _operands(op: int) -> int:
+    """Operands per element of a self-test op (see od_arith_host)."""
+    if 10 <= op < 20 or 30 <= op < 40:
+        return 6
+    if 20 <= op < 30 or op >= 40:
+        return 4
+    return 1
+
+
 def arith_host(op: int, a: np.ndarray, b: np.ndarray | None = None) -> np.ndarray:
     """Run the kernels' exact integer-pipe arithmetic on the host: op 0
     a/6, op 1 a+b, op 10+m the 3D Jacobi update in arithmetic mode m over six
-    operands per element, op 20+m the 2D update over four (float64 arrays)."""
+    operands per element, op 20+m the 2D update over four; op 30+f / 40+f the
+    3D / 2D update in the anchored window with f adds on the FP64 pipe, b[0]
+    holding the anchor exponent (float64 arrays)."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = a if b is None else np.ascontiguousarray(b, dtype=np.float64)
-    n = a.size // 4 if op >= 20 else a.size // 6 if op >= 10 else a.size
+    n = a.size // _operands(op)
     out = np.empty(n, dtype=np.float64)
     check(lib().od_arith_host(int(op), a.ctypes.data, b.ctypes.data, out.ctypes.data, n), "od_arith_host")
     return out
@@ -133,7 +144,7 @@ def arith_device(op: int, a, b=None):
     pipe's IEEE division / add."""
     import torch
     b = a if b is None else b
-    n = a.numel() // 4 if op >= 20 else a.numel() // 6 if op >= 10 else a.numel()
+    n = a.numel() // _operands(op)
     out = torch.empty(n, dtype=torch.float64, device=a.device)
     check(lib().od_arith_device(int(op), a.data_ptr(), b.data_ptr(), out.data_ptr(), n), "od_arith_device")
     return out

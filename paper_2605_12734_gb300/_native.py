@@ -12,10 +12,10 @@ LIB_PATH = os.path.join(_PKG, "libod.so")
 OD_OK, OD_EINVAL, OD_ENOMEM, OD_ECUDA, OD_ETIMEOUT, OD_EBUDGET, OD_ESTATE, OD_ENOTFOUND = range(8)
 STATUS_NAMES = {0: "OD_OK", 1: "OD_EINVAL", 2: "OD_ENOMEM", 3: "OD_ECUDA", 4: "OD_ETIMEOUT",
                 5: "OD_EBUDGET", 6: "OD_ESTATE", 7: "OD_ENOTFOUND"}
-OD_PATH_PER_CHARE, OD_PATH_FUSED, OD_PATH_GRAPH, OD_PATH_PERSISTENT = range(4)
+OD_PATH_PER_CHARE, OD_PATH_FUSED, OD_PATH_GRAPH, OD_PATH_PERSISTENT, OD_PATH_FUSED_GRAPH = range(5)
 OD_STENCIL_3D7, OD_STENCIL_2D5 = 0, 1
 PATHS = {"per_chare": OD_PATH_PER_CHARE, "fused": OD_PATH_FUSED, "graph": OD_PATH_GRAPH,
-         "persistent": OD_PATH_PERSISTENT}
+         "persistent": OD_PATH_PERSISTENT, "fused_graph": OD_PATH_FUSED_GRAPH}
 
 _i32 = ctypes.c_int32
 _i64 = ctypes.c_int64

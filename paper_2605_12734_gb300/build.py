@@ -29,9 +29,9 @@ SOURCES = ["od_kernels.cu", "od_api.cu", "od_plan.cpp", "od_noalloc.cu", "od_ser
            "od_comm.cu"]
 # the tile kernels, compiled once per arithmetic mode (-DOD_AMODE=m)
 TILE_SOURCE = "od_tiles.cu"
-AMODES = range(12)
+AMODES = range(16)
 # the 2D 5-point kernels (-DOD_STENCIL=1): modes 4..6 coincide there (three adds)
-AMODES_2D = (0, 1, 2, 3, 4, 7, 8, 9, 10, 11)
+AMODES_2D = (0, 1, 2, 3, 4, 7, 8, 9, 10, 11, 12, 13, 14, 15)
 HEADERS = ["od_internal.h", "od_kernels.h", "od_plan.h", "od_tile.cuh", "od_arith.cuh", "od_ctx.h"]
 
 

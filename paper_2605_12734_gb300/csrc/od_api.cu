@@ -75,6 +75,8 @@ KArgs base_args_impl(const od_ctx *c) {
     a.dep_ptr = c->d_dep_ptr;
     a.dep_idx = c->d_dep_idx;
     a.order = c->d_order;
+    a.vmax = c->d_vmax;
+    a.one = 1u;
     a.ntiles = (int32_t)c->plan.tiles.size();
     a.order_mode = c->cfg.order & 1;
     a.stages = c->plan.stages;
@@ -346,6 +348,67 @@ od_status enqueue_graph(od_ctx *c, int32_t iters) {
     return OD_OK;
 }
 
+// --- fused-graph path: the fused step loop captured as CUDA graphs.  A
+// fused step's only state is the parity of its source buffer, so a graph of
+// kFusedGraphSteps steps from an even step serves every even start and the
+// two one-step graphs cover an odd start and an odd remainder.
+constexpr int32_t kFusedGraphSteps = 8;
+
+od_status capture_fused(od_ctx *c, int64_t t_first, int32_t iters, cudaGraphExec_t *out) {
+    const od::Plan &p = c->plan;
+    cudaGraph_t g = nullptr;
+    OD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int32_t s = 0; s < iters && e == cudaSuccess; ++s) {
+        KArgs a = base_args_impl(c);
+        a.tile_begin = 0;
+        a.parity = (int32_t)((t_first + s) & 1);
+        e = od::launch_tiles(a, (int)p.tiles.size(), p.threads, p.cpt, p.amode, true, p.smem_bytes, c->stream);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e != cudaSuccess ? e : e2, "capturing the fused step loop");
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return OD_OK;
+}
+
+od_status enqueue_fused_graph(od_ctx *c, int32_t iters) {
+    if (iters <= 0) return OD_OK;
+    if (!c->gf) {
+        od_status s = capture_fused(c, 0, kFusedGraphSteps, &c->gf);
+        if (s == OD_OK) s = capture_fused(c, 0, 1, &c->gf1[0]);
+        if (s == OD_OK) s = capture_fused(c, 1, 1, &c->gf1[1]);
+        if (s != OD_OK) return s;
+    }
+    auto replay = [&](cudaGraphExec_t g, int32_t steps) -> od_status {
+        OD_CUDA(cudaGraphLaunch(g, c->stream));
+        c->launches += steps;
+        c->graph_launches++;
+        c->api_calls++;
+        c->steps += steps;
+        return OD_OK;
+    };
+    int32_t left = iters;
+    od_status s = OD_OK;
+    if (c->steps & 1) {
+        s = replay(c->gf1[1], 1);
+        left--;
+    }
+    while (s == OD_OK && left >= kFusedGraphSteps) {
+        s = replay(c->gf, kFusedGraphSteps);
+        left -= kFusedGraphSteps;
+    }
+    while (s == OD_OK && left > 0) {
+        s = replay(c->gf1[c->steps & 1], 1);
+        left--;
+    }
+    return s;
+}
+
 od_status check_device_error_impl(od_ctx *c) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess && c->copy_pending) {
@@ -414,6 +477,9 @@ void release(od_ctx *c) {
     if (!c) return;
     if (c->g2) cudaGraphExecDestroy(c->g2);
     for (auto &g : c->g1)
+        if (g) cudaGraphExecDestroy(g);
+    if (c->gf) cudaGraphExecDestroy(c->gf);
+    for (auto &g : c->gf1)
         if (g) cudaGraphExecDestroy(g);
     for (auto e : c->ev) cudaEventDestroy(e);
     for (auto e : c->join) cudaEventDestroy(e);
@@ -676,22 +742,38 @@ void od_config_default(od_config *cfg) {
     cfg->arith = -1;
 }
 
+// The anchor exponent of the anchored self-test ops, passed as b[0] (a
+// double holding an integer), clamped to the range the routines accept.
+static uint32_t anchor_arg(double v) {
+    if (!(v >= (double)od::kAnchorMin)) return od::kAnchorMin;
+    if (v > (double)od::kAnchorMax) return od::kAnchorMax;
+    return (uint32_t)v;
+}
+
 od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n) {
-    if (n < 0 || (n > 0 && (!a || !out || (op == 1 && !b)))) return fail(OD_EINVAL, "bad arguments");
-    if (op != 0 && op != 1 && !(op >= 10 && op <= 18) && !(op >= 20 && op <= 26))
-        return fail(OD_EINVAL, "host op must be 0 (div6), 1 (add), 10..18 (3D update) or 20..26 (2D update)");
+    const bool anch = (op >= 30 && op <= 37) || (op >= 40 && op <= 46 && op != 43);
+    if (n < 0 || (n > 0 && (!a || !out || ((op == 1 || anch) && !b)))) return fail(OD_EINVAL, "bad arguments");
+    if (op != 0 && op != 1 && !(op >= 10 && op <= 18) && !(op >= 20 && op <= 26) && !anch)
+        return fail(OD_EINVAL,
+                    "host op must be 0 (div6), 1 (add), 10..18 (3D update), 20..26 (2D update), 30..37 or "
+                    "40..42, 44..46 (anchored updates)");
+    const uint32_t e0 = anch && n > 0 ? anchor_arg(b[0]) : 0u;
     for (int64_t i = 0; i < n; ++i)
         out[i] = op == 0   ? od::div6(a[i])
                  : op == 1 ? od::add(a[i], b[i])
                  : op < 20 ? od::jacobi_update_mode(op - 10, a + 6 * i)
-                           : od::jacobi2d_update_mode(op - 20, a + 4 * i);
+                 : op < 30 ? od::jacobi2d_update_mode(op - 20, a + 4 * i)
+                 : op < 40 ? od::jacobi_update_anchored_mode(op - 30, a + 6 * i, e0)
+                           : od::jacobi2d_update_anchored_mode(op - 40, a + 4 * i, e0);
     return OD_OK;
 }
 
 od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n) {
-    if (n < 0 || (n > 0 && (!a || !out || ((op == 1 || op == 3) && !b)))) return fail(OD_EINVAL, "bad arguments");
-    if (!((op >= 0 && op <= 3) || (op >= 10 && op <= 18) || (op >= 20 && op <= 26)))
-        return fail(OD_EINVAL, "op must be 0..3, 10..18 or 20..26");
+    const bool anch = (op >= 30 && op <= 37) || (op >= 40 && op <= 46 && op != 43);
+    if (n < 0 || (n > 0 && (!a || !out || ((op == 1 || op == 3 || anch) && !b))))
+        return fail(OD_EINVAL, "bad arguments");
+    if (!((op >= 0 && op <= 3) || (op >= 10 && op <= 18) || (op >= 20 && op <= 26) || anch))
+        return fail(OD_EINVAL, "op must be 0..3, 10..18, 20..26, 30..37, 40..42 or 44..46");
     if (n == 0) return OD_OK;
     OD_CUDA(od::launch_arith(op, a, b, out, n, 0));
     OD_CUDA(cudaStreamSynchronize(0));
@@ -844,6 +926,7 @@ od_status od_create(od_ctx **out, const od_config *cfg_in) {
     c->d_dep_ptr = (int32_t *)(A + p.off_dep_ptr);
     c->d_dep_idx = (int32_t *)(A + p.off_dep_idx);
     c->d_order = (int32_t *)(A + p.off_order);
+    c->d_vmax = (uint64_t *)(A + p.off_queue + 8);  // the queue block holds 64 bytes
     c->h_ch.resize(p.ch.size());
     for (size_t i = 0; i < p.ch.size(); ++i) {
         const od::HostChare &h = p.ch[i];
@@ -888,7 +971,12 @@ od_status od_create(od_ctx **out, const od_config *cfg_in) {
     OD_TRY(od::launch_init(c->d_ch, (int)p.ch.size(), p.gnx, p.gny, p.gnz, p.gx0, p.gy0, p.gz0, cfg->seed,
                            cfg->init_mode, p.stencil,
                            c->stream));
+    // every initial value lies in [0, 1): the largest possible one anchors
+    // the exact arithmetic's window (od_write raises it for imported fields)
+    const uint64_t vmax0 = 0x3FEFFFFFFFFFFFFFull;
+    OD_TRY(cudaMemcpyAsync(c->d_vmax, &vmax0, sizeof vmax0, cudaMemcpyHostToDevice, c->stream));
     OD_TRY(cudaStreamSynchronize(c->stream));
+    c->ghosts_current = true;
 #undef OD_TRY
     *out = c;
     return OD_OK;
@@ -900,18 +988,38 @@ od_status od_step(od_ctx *c, int32_t iters) {
     if (c->failed) return fail(OD_ESTATE, "context failed earlier; destroy it");
     if (iters == 0) return OD_OK;
     DeviceGuard dg(c->device);
+    const bool fused3d = c->plan.stencil == OD_STENCIL_3D7;
     switch (c->path) {
-        case OD_PATH_FUSED: return enqueue_fused(c, iters);
-        case OD_PATH_PERSISTENT: return enqueue_persistent(c, iters);
-        case OD_PATH_PER_CHARE: return enqueue_per_chare(c, iters);
-        case OD_PATH_GRAPH: return enqueue_graph(c, iters);
+        case OD_PATH_FUSED:
+        case OD_PATH_FUSED_GRAPH:
+        case OD_PATH_PERSISTENT: {
+            // the fused 3D sweep reads the neighbours' faces and leaves the
+            // ghost layers behind; the 2D sweep keeps them current
+            od_status s = c->path == OD_PATH_FUSED         ? enqueue_fused(c, iters)
+                          : c->path == OD_PATH_FUSED_GRAPH ? enqueue_fused_graph(c, iters)
+                                                           : enqueue_persistent(c, iters);
+            if (fused3d) c->ghosts_current = false;
+            return s;
+        }
+        case OD_PATH_PER_CHARE:
+        case OD_PATH_GRAPH: {
+            // the per-chare flow reads its own ghost layers: refresh them
+            // once after fused 3D steps (its own steps keep them current)
+            if (!c->ghosts_current) {
+                OD_CUDA(od::launch_ghost_refresh(c->d_ch, (int)c->plan.ch.size(), (int)(c->steps & 1), c->stream));
+                c->launches++;
+                c->api_calls++;
+                c->ghosts_current = true;
+            }
+            return c->path == OD_PATH_PER_CHARE ? enqueue_per_chare(c, iters) : enqueue_graph(c, iters);
+        }
         default: return fail(OD_EINVAL, "unknown path");
     }
 }
 
 od_status od_set_path(od_ctx *c, int32_t path) {
     if (!c) return fail(OD_EINVAL, "null context");
-    if (path < OD_PATH_PER_CHARE || path > OD_PATH_PERSISTENT) return fail(OD_EINVAL, "unknown path");
+    if (path < OD_PATH_PER_CHARE || path > OD_PATH_FUSED_GRAPH) return fail(OD_EINVAL, "unknown path");
     c->path = path;
     return OD_OK;
 }
@@ -1000,7 +1108,8 @@ od_status od_write(od_ctx *c, const double *src, int32_t src_is_device) {
                                 c->stream));
         g = c->d_stage;
     }
-    OD_CUDA(od::launch_scatter(c->d_ch, (int)p.ch.size(), par, p.nx, p.ny, p.nz, g, c->stream));
+    OD_CUDA(od::launch_scatter(c->d_ch, (int)p.ch.size(), par, p.nx, p.ny, p.nz, g, c->d_vmax, c->stream));
+    c->ghosts_current = true;  // the scatter writes every internal ghost cell too
     if (!src_is_device) OD_CUDA(cudaStreamSynchronize(c->stream));
     return OD_OK;
 }
@@ -1015,7 +1124,8 @@ od_status od_write_async(od_ctx *c, const double *src) {
     const od::Plan &p = c->plan;
     OD_CUDA(cudaMemcpyAsync(c->d_stage, src, (size_t)p.cells * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     OD_CUDA(od::launch_scatter(c->d_ch, (int)p.ch.size(), (int)(c->steps & 1), p.nx, p.ny, p.nz, c->d_stage,
-                               c->stream));
+                               c->d_vmax, c->stream));
+    c->ghosts_current = true;
     return OD_OK;
 }
 

@@ -308,6 +308,251 @@ OD_HD double div6_window(uint64_t W, uint32_t emax, uint32_t p) {
     return div6_chain(u);
 }
 
+// ---------------------------------------------------------------- anchored window
+//
+// The window chain above aligns each cell's operands to the largest of them,
+// which costs a maximum over their exponents and a relative shift per
+// operand.  When the whole field lies within a few binades -- a Jacobi field
+// never leaves the range of its initial values and boundary (the maximum
+// principle) -- one window can be anchored for every cell instead.  With a
+// base exponent E0, an operand with biased exponent e in [E0, E0+7] is
+// exactly the integer F = m << (e - E0) in units of 2^(E0-1075) (m its 53-bit
+// significand), so F < 2^60 and a sum of up to six such integers is exact in
+// 64 bits.  Each add of the chain is a 64-bit integer add followed by
+// rounding the partial sum to 53 significant bits at its own binade, exactly
+// as the IEEE add would round it; the division by 6 reads the rounded word.
+// An operand outside [E0, E0+7] (zero, subnormal, negative, infinite, NaN, or
+// just outside the window) sends the cell to the IEEE form (ok = false).
+// E0 only decides how many cells take the fast form: any E0 in [4, 2037]
+// gives the IEEE result for every input (the quotient's exponent stays
+// normal and below the infinities, and an infinite or NaN operand still
+// reads as outside the window).  The anchors chosen below lie in
+// [kAnchorMin, kAnchorMax], which leaves room for E0 + 1.
+
+constexpr uint32_t kAnchorMin = 4u, kAnchorMax = 2030u;
+
+// Integer and FP32 helpers with one meaning on host and device.  On the
+// device the multiply-adds are written as PTX mad instructions: with `one`
+// a register whose value (1) the compiler cannot see, an add becomes an
+// IMAD on the FMA pipe instead of an IADD on the integer ALU pipe, which the
+// exact arithmetic below would otherwise saturate.  On the host they are the
+// plain integer operations.
+OD_HD uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+#if defined(__CUDA_ARCH__)
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+#else
+    return a * b + c;
+#endif
+}
+
+OD_HD uint64_t mad_wide_u(uint32_t a, uint32_t b, uint64_t c) {
+#if defined(__CUDA_ARCH__)
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+#else
+    return (uint64_t)a * b + c;
+#endif
+}
+
+// a * b + c with a and b signed 32-bit (the product sign-extended)
+OD_HD uint64_t mad_wide_s(int32_t a, int32_t b, uint64_t c) {
+#if defined(__CUDA_ARCH__)
+    uint64_t d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+#else
+    return (uint64_t)((int64_t)a * (int64_t)b) + c;
+#endif
+}
+
+// 1 << s, 0 for s >= 32 (PTX shl clamps its count; the host matches it)
+OD_HD uint32_t pow2_u32(uint32_t s) {
+#if defined(__CUDA_ARCH__)
+    uint32_t d;
+    asm("shl.b32 %0, 1, %1;" : "=r"(d) : "r"(s));
+    return d;
+#else
+    return s < 32u ? 1u << s : 0u;
+#endif
+}
+
+OD_HD float f32_from(uint32_t u) {
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float(u);
+#else
+    float x;
+    memcpy(&x, &u, 4);
+    return x;
+#endif
+}
+
+OD_HD uint32_t f32_bits(float x) {
+#if defined(__CUDA_ARCH__)
+    return __float_as_uint(x);
+#else
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    return u;
+#endif
+}
+
+// (a + b) - b in binary32 round-to-nearest-even, both operations rounded
+// (never contracted or reassociated)
+OD_HD float f32_add_sub(float a, float b) {
+#if defined(__CUDA_ARCH__)
+    return __fsub_rn(__fadd_rn(a, b), b);
+#else
+    volatile float s = a + b;
+    volatile float r = s - b;
+    return r;
+#endif
+}
+
+// F += F(x): x's window word m * 2^sh (m its 53-bit significand, sh =
+// e - E0) added into F as two multiply-adds by 2^sh, low word then high
+// word.  nE0s = -(E0 << 20).  hb = hi - (E0 << 20) carries (e - E0) in its
+// bits 20..30 and the top fraction bits below; x lies in the window exactly
+// when hb < 2^23 (a negative x carries its sign bit into hb, a zero or
+// subnormal x makes it wrap), so the caller ORs every hb into chk and tests
+// chk < 2^23 once.  Out of the window F is meaningless (the caller discards
+// the cell's fast result), and so it is on the host, which computes the
+// same words.
+OD_HD void anchor_acc(uint64_t &F, uint32_t &chk, double x, uint32_t nE0s, uint32_t one) {
+    const uint64_t b = f64_bits(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t hb = mad_lo(hi, one, nE0s);
+    chk |= hb;
+    const uint32_t p2 = pow2_u32(hb >> 20);
+    const uint32_t mh = (hb & 0x000FFFFFu) | 0x00100000u;  // high significand word with the hidden bit
+    const uint64_t t = mad_wide_u(lo, p2, F);
+    F = ((uint64_t)mad_lo(mh, p2, (uint32_t)(t >> 32)) << 32) | (uint32_t)t;
+}
+
+OD_HD bool anchored_ok(uint32_t chk) { return chk < 0x00800000u; }
+
+// Round F, a sum of at least two window words (so its top set bit lies at
+// 52 + d with d = 11 - c in [1, 10], c = clz(hi)), to 53 significant bits,
+// nearest even; returns c.  Only F's low 23 bits x take part (d < 23): the
+// binary32 sum (2^23 + x) + 2^(23+d) lies in [2^(23+d), 2^(24+d)], where
+// binary32 numbers are 2^d apart, so the addition rounds 2^23 + x to a
+// multiple of 2^d, nearest even, exactly as the rounding to 53 bits needs
+// (the kept part's last bit is x's bit d), and subtracting 2^(23+d) again
+// is exact.  F then moves by the difference of the two binary32 words.
+OD_HD uint32_t round_acc(uint64_t &F, uint32_t one) {
+    const uint32_t c = clz32((uint32_t)(F >> 32));
+    const uint32_t mb = mad_lo(c, 0xFF800000u, 161u << 23);         // binary32 2^(23+d): exponent 150 + d
+    const uint32_t fb = ((uint32_t)F & 0x007FFFFFu) | 0x4B000000u;  // binary32 2^23 + x
+    const uint32_t hb = f32_bits(f32_add_sub(f32_from(fb), f32_from(mb)));
+    F = mad_wide_s((int32_t)(hb - fb), (int32_t)one, F);
+    return c;
+}
+
+// (x+1)/3 rounded down for x < 2^62: the high half of x * ceil(2^64/3)
+// equals floor(x/3) for every x < 2^63 (its error, 2x/(3*2^64), stays below
+// the distance 1/3 from x/3 to the next integer), and adding the constant
+// once more turns x into x+1.
+OD_HD uint64_t div3_up1(uint64_t x) {
+    const uint64_t C = 0x5555555555555556ull;
+    return mulhi64(x + 1u, C);
+}
+
+// s/6 correctly rounded, for the window word F of s as its last rounding
+// left it: c = clz(hi) before that rounding, d = 11 - c >= 2, and F a
+// multiple of 2^d in [2^(52+d), 2^(53+d)] -- the top end when the rounding
+// carried into the next binade.  As in div6: the quotient's significand is
+// N/3 for N = 2M or 4M (M = F >> d, N = 2M when M >= 3*2^51), N/3 is never a
+// tie, and rounding it to nearest is floor((N+1)/3).  N = F >> (d - 2 + big)
+// is exact because F's d low bits are zero.  The two bits of F below and at
+// its expected top position, h = hi >> (30 - c), are 2 or 3 (big when 3);
+// a carried F = 2^(53+d) reads h = 4 and is big too, which is right: its
+// significand is 2^52 one binade up, whose N = 4 * 2^52 = F >> (d - 1).
+// The result's biased exponent is E0 + d - 3 + big.
+OD_HD double div6_anchored(uint64_t F, uint32_t c, uint32_t E0) {
+    const uint32_t hi = (uint32_t)(F >> 32);
+    const uint32_t big = (hi >> (30u - c)) >= 3u ? 1u : 0u;  // M >= 3*2^51, or a carried F
+    const uint32_t sh = 9u - c + big;             // d - 2 + big
+    const uint64_t Q = div3_up1(shr31(F, sh));    // [2^52, 2^53]; 2^53 carries into the exponent
+    const uint32_t em1 = E0 + 7u - c + big;       // biased exponent - 1
+    return f64_from(((uint64_t)mad_lo(em1, 1u << 20, (uint32_t)(Q >> 32)) << 32) | (uint32_t)Q);
+}
+
+// s/4 exactly (2D): the significand M = F >> d keeps its bits and the
+// exponent drops by two: biased exponent E0 + d - 2.  A last rounding that
+// carried into the next binade leaves M = 2^53, and the packing's addition
+// carries it into the exponent field.
+OD_HD double div4_anchored(uint64_t F, uint32_t c, uint32_t E0) {
+    const uint64_t M = shr31(F, 11u - c);
+    return f64_from(((uint64_t)mad_lo(E0 + 8u - c, 1u << 20, (uint32_t)(M >> 32)) << 32) | (uint32_t)M);
+}
+
+// The 3D update with its first NF adds (0..3) on the FP64 pipe and the rest
+// in the anchored window, the division from the window word.  ok = false
+// when the FP64 partial sum or a later operand leaves the window (or, with
+// NF = 3, when the window sum is below 2^54 so that d = 1).  `one` must be 1
+// (see mad_lo).
+template <int NF>
+OD_HD double jacobi_update_anchored(double W, double E, double S, double N, double D, double U, uint32_t E0,
+                                    bool &ok, uint32_t one = 1u) {
+    static_assert(NF >= 0 && NF <= 3, "zero to three adds on the FP64 pipe");
+    const double x[6] = {W, E, S, N, D, U};
+    double s = x[0];
+#pragma unroll
+    for (int t = 1; t <= NF; ++t) s = ieee_add(s, x[t]);
+    const uint32_t nE0s = 0u - (E0 << 20);
+    uint64_t F = 0;
+    uint32_t chk = 0, c = 0;
+    anchor_acc(F, chk, s, nE0s, one);
+#pragma unroll
+    for (int t = NF + 1; t <= 5; ++t) {
+        anchor_acc(F, chk, x[t], nE0s, one);
+        c = round_acc(F, one);
+    }
+    ok = anchored_ok(chk);
+    if constexpr (NF == 3) ok = ok & (c <= 9u);
+    return div6_anchored(F, c, E0);
+}
+
+// The 2D update (((W+E)+S)+N)/4 with its first NF adds (0..2) on the FP64
+// pipe and the rest in the anchored window.
+template <int NF>
+OD_HD double jacobi2d_update_anchored(double W, double E, double S, double N, uint32_t E0, bool &ok,
+                                      uint32_t one = 1u) {
+    static_assert(NF >= 0 && NF <= 2, "zero to two adds on the FP64 pipe");
+    const double x[4] = {W, E, S, N};
+    double s = x[0];
+#pragma unroll
+    for (int t = 1; t <= NF; ++t) s = ieee_add(s, x[t]);
+    const uint32_t nE0s = 0u - (E0 << 20);
+    uint64_t F = 0;
+    uint32_t chk = 0, c = 0;
+    anchor_acc(F, chk, s, nE0s, one);
+#pragma unroll
+    for (int t = NF + 1; t <= 3; ++t) {
+        anchor_acc(F, chk, x[t], nE0s, one);
+        c = round_acc(F, one);
+    }
+    ok = anchored_ok(chk);
+    return div4_anchored(F, c, E0);
+}
+
+// The anchor for a field whose largest value has bit pattern vmax (a
+// positive double, or 0 when unknown).  The window [E0, E0+7] must hold the
+// operands and the FP64 partial sum that joins them: up to twice the largest
+// value with NF <= 1 (E0 = emax - 6: values down to 2^-6 of the largest stay
+// in), up to three or four times it with NF = 2 or 3 (E0 = emax - 5).  A sum
+// of three values near the top would otherwise leave the window whenever
+// the field is locally above two thirds of its largest value.
+OD_HD uint32_t anchor_for(uint64_t vmax, int nf) {
+    const int64_t emax = (int64_t)(vmax >> 52) & 0x7FF;
+    int64_t e0 = emax - (nf >= 2 ? 5 : 6);
+    if (e0 < (int64_t)kAnchorMin) e0 = kAnchorMin;
+    if (e0 > (int64_t)kAnchorMax) e0 = kAnchorMax;
+    return (uint32_t)e0;
+}
+
 // ---------------------------------------------------------------- update
 
 // s / 6 on the integer pipes without a branch; ok = false when s is outside
@@ -513,6 +758,63 @@ OD_HD double jacobi2d_update_tail_checked(double W, double E, double S, double N
     bool ok;
     const double v = jacobi2d_update_tail<KT>(W, E, S, N, ok);
     return ok ? v : jacobi2d_update_ieee<false>(W, E, S, N);
+}
+
+// The anchored forms with their IEEE fallback, and their run-time dispatch
+// over the number of adds on the FP64 pipe (tests).
+template <int NF>
+OD_HD double jacobi_update_anchored_checked(const double *x, uint32_t E0) {
+    bool ok;
+    const double v = jacobi_update_anchored<NF>(x[0], x[1], x[2], x[3], x[4], x[5], E0, ok);
+    return ok ? v : jacobi_update_ieee<false>(x[0], x[1], x[2], x[3], x[4], x[5]);
+}
+
+template <int NF>
+OD_HD double jacobi2d_update_anchored_checked(const double *x, uint32_t E0) {
+    bool ok;
+    const double v = jacobi2d_update_anchored<NF>(x[0], x[1], x[2], x[3], E0, ok);
+    return ok ? v : jacobi2d_update_ieee<false>(x[0], x[1], x[2], x[3]);
+}
+
+// The fast form alone, NaN where the cell would leave it (tests: how many
+// cells take the fast form, and that every one of them is exact).
+template <int NF>
+OD_HD double jacobi_update_anchored_fast(const double *x, uint32_t E0) {
+    bool ok;
+    const double v = jacobi_update_anchored<NF>(x[0], x[1], x[2], x[3], x[4], x[5], E0, ok);
+    return ok ? v : f64_from(0x7FF8000000000000ull);
+}
+
+template <int NF>
+OD_HD double jacobi2d_update_anchored_fast(const double *x, uint32_t E0) {
+    bool ok;
+    const double v = jacobi2d_update_anchored<NF>(x[0], x[1], x[2], x[3], E0, ok);
+    return ok ? v : f64_from(0x7FF8000000000000ull);
+}
+
+// nf 0..3 (3D) / 0..2 (2D): the checked form; nf + 4: the fast form alone.
+OD_HD double jacobi_update_anchored_mode(int nf, const double *x, uint32_t E0) {
+    switch (nf) {
+        case 0: return jacobi_update_anchored_checked<0>(x, E0);
+        case 1: return jacobi_update_anchored_checked<1>(x, E0);
+        case 2: return jacobi_update_anchored_checked<2>(x, E0);
+        case 3: return jacobi_update_anchored_checked<3>(x, E0);
+        case 4: return jacobi_update_anchored_fast<0>(x, E0);
+        case 5: return jacobi_update_anchored_fast<1>(x, E0);
+        case 6: return jacobi_update_anchored_fast<2>(x, E0);
+        default: return jacobi_update_anchored_fast<3>(x, E0);
+    }
+}
+
+OD_HD double jacobi2d_update_anchored_mode(int nf, const double *x, uint32_t E0) {
+    switch (nf) {
+        case 0: return jacobi2d_update_anchored_checked<0>(x, E0);
+        case 1: return jacobi2d_update_anchored_checked<1>(x, E0);
+        case 2: return jacobi2d_update_anchored_checked<2>(x, E0);
+        case 4: return jacobi2d_update_anchored_fast<0>(x, E0);
+        case 5: return jacobi2d_update_anchored_fast<1>(x, E0);
+        default: return jacobi2d_update_anchored_fast<2>(x, E0);
+    }
 }
 
 // Run-time dispatch of the 2D update (tests): 0..4 head modes, 5 / 6 the

@@ -25,6 +25,9 @@ struct od_ctx {
     ErrDev *d_err = nullptr;
     int32_t *d_queue = nullptr, *d_epoch = nullptr, *d_dep_ptr = nullptr, *d_dep_idx = nullptr,
             *d_order = nullptr;
+    uint64_t *d_vmax = nullptr;       // largest value of the field (bits), in the arena's queue block
+    bool ghosts_current = true;       // internal ghost layers of the current parity hold the
+                                      // neighbours' faces (false after a fused 3D step)
     std::vector<ChareDev> h_ch;       // host copy (device pointers)
     double *d_stage = nullptr;        // lazily allocated host-transfer staging
     // od_read_async: the device-to-host copy of the staging buffer runs on
@@ -48,6 +51,9 @@ struct od_ctx {
     std::vector<cudaEvent_t> join;
     // graph path
     cudaGraphExec_t g2 = nullptr, g1[2] = {nullptr, nullptr};
+    // fused-graph path: kFusedGraphSteps fused steps from an even step, and
+    // one step from each parity
+    cudaGraphExec_t gf = nullptr, gf1[2] = {nullptr, nullptr};
     int64_t g2_kernels = 0, g1_kernels[2] = {0, 0};
     int64_t g2_calls = 0, g1_calls[2] = {0, 0};
 };

@@ -21,9 +21,16 @@
 // `rows` rows and interior row j sits at row j + row0 of it: rows = by+2,
 // row0 = 1 in 3D; rows = 1, row0 = 0 in 2D.
 //
-// A neighbour "delivers" a face by storing straight into these ghost cells
-// (the chare's mailbox).  Faces on the domain boundary hold the Dirichlet
-// shell in both parities and are never written after initialisation.
+// On the per-chare path a neighbour delivers a face into these ghost cells
+// (pack, copy, unpack: the chare's mailbox).  The fused 3D tile sweep instead
+// reads a face straight from the neighbour's own array -- its boundary
+// planes and rows by bulk copies into the tile's ring slots, its boundary
+// column by plain loads -- so an internal ghost layer of a chare is only
+// current after a per-chare step, od_create or od_write (the context tracks
+// this and refreshes the ghosts before a per-chare step needs them).  The
+// fused 2D sweep stores each boundary value into the neighbour's ghost
+// cells.  Faces on the domain boundary hold the Dirichlet shell in both
+// parities and are never written after initialisation.
 #pragma once
 #include <stdint.h>
 
@@ -77,6 +84,8 @@ struct KArgs {
     const int32_t *dep_ptr;  // persistent: CSR of the tiles each tile reads
     const int32_t *dep_idx;
     const int32_t *order;    // persistent: tile of each queue position
+    const uint64_t *vmax;    // bit pattern of the largest value the field holds (a positive
+                             // double), from which the anchored arithmetic takes its window
     int32_t tile_begin;      // static launch: tile of blockIdx.x == 0
     int32_t ntiles;          // tiles per step
     int32_t parity;          // static launch: parity of the source buffer
@@ -86,7 +95,8 @@ struct KArgs {
     int32_t stages;          // TMA ring depth
     int32_t stage_doubles;   // doubles per ring slot
     int32_t stencil;         // OD_STENCIL_3D7 or OD_STENCIL_2D5
-    int32_t pad0;
+    uint32_t one;            // 1, passed at run time so that the arithmetic's adds written as
+                             // multiply-adds by it stay on the FMA pipe (od_arith.cuh)
     int64_t stall_tile;      // fault injection (-1 = off)
     uint64_t spin_ns;        // bound on every device-side wait
 };

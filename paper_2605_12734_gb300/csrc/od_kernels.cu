@@ -25,6 +25,10 @@ void *tile_kernel_am8(int threads, int cpt, int kind);
 void *tile_kernel_am9(int threads, int cpt, int kind);
 void *tile_kernel_am10(int threads, int cpt, int kind);
 void *tile_kernel_am11(int threads, int cpt, int kind);
+void *tile_kernel_am12(int threads, int cpt, int kind);
+void *tile_kernel_am13(int threads, int cpt, int kind);
+void *tile_kernel_am14(int threads, int cpt, int kind);
+void *tile_kernel_am15(int threads, int cpt, int kind);
 void *tile_kernel2d_am0(int threads, int cpt, int kind);
 void *tile_kernel2d_am1(int threads, int cpt, int kind);
 void *tile_kernel2d_am2(int threads, int cpt, int kind);
@@ -35,6 +39,10 @@ void *tile_kernel2d_am8(int threads, int cpt, int kind);
 void *tile_kernel2d_am9(int threads, int cpt, int kind);
 void *tile_kernel2d_am10(int threads, int cpt, int kind);
 void *tile_kernel2d_am11(int threads, int cpt, int kind);
+void *tile_kernel2d_am12(int threads, int cpt, int kind);
+void *tile_kernel2d_am13(int threads, int cpt, int kind);
+void *tile_kernel2d_am14(int threads, int cpt, int kind);
+void *tile_kernel2d_am15(int threads, int cpt, int kind);
 
 namespace {
 
@@ -52,6 +60,10 @@ void *tile_kernel(int stencil, int amode, int threads, int cpt, int kind) {
         case 9: return tile_kernel2d_am9(threads, cpt, kind);
         case 10: return tile_kernel2d_am10(threads, cpt, kind);
         case 11: return tile_kernel2d_am11(threads, cpt, kind);
+        case 12: return tile_kernel2d_am12(threads, cpt, kind);
+        case 13: return tile_kernel2d_am13(threads, cpt, kind);
+        case 14: return tile_kernel2d_am14(threads, cpt, kind);
+        case 15: return tile_kernel2d_am15(threads, cpt, kind);
         default: return nullptr;
     }
     if (stencil != OD_STENCIL_3D7) return nullptr;
@@ -68,6 +80,10 @@ void *tile_kernel(int stencil, int amode, int threads, int cpt, int kind) {
         case 9: return tile_kernel_am9(threads, cpt, kind);
         case 10: return tile_kernel_am10(threads, cpt, kind);
         case 11: return tile_kernel_am11(threads, cpt, kind);
+        case 12: return tile_kernel_am12(threads, cpt, kind);
+        case 13: return tile_kernel_am13(threads, cpt, kind);
+        case 14: return tile_kernel_am14(threads, cpt, kind);
+        case 15: return tile_kernel_am15(threads, cpt, kind);
         default: return nullptr;
     }
 }
@@ -173,6 +189,26 @@ __global__ void k_unpack(const ChareDev *ch, int c, int p, int slot) {
     }
 }
 
+// Internal ghost layers of parity p from the neighbours' boundary layers,
+// every chare at once (face element q of face f is the neighbour's element
+// q of the opposite face, as in pack / unpack).  Run before a per-chare step
+// that follows fused 3D steps, which read the neighbours' faces directly and
+// leave the ghost layers behind.
+__global__ void k_ghost_refresh(const ChareDev *ch, int nch, int p) {
+    for (int c = blockIdx.y; c < nch; c += gridDim.y) {
+        const ChareDev &C = ch[c];
+        double *A = C.A[p];
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < C.foff[6]; e += gridDim.x * blockDim.x) {
+            int f = 0;
+            while (e >= C.foff[f + 1]) ++f;
+            if (C.nbr[f] < 0) continue;
+            const ChareDev &N = ch[C.nbr[f]];
+            const int q = e - C.foff[f];
+            A[face_offset(C, f, q, true)] = N.A[p][face_offset(N, f ^ 1, q, false)];
+        }
+    }
+}
+
 // Domain-face exchange of a shard: the chares on domain face f (no neighbour
 // there) copy, cell by cell, their boundary layer of parity p into buf
 // (dir 0) or buf into their ghost layer (dir 1).  buf is the whole face,
@@ -228,9 +264,14 @@ __global__ void k_gather(const ChareDev *ch, int nch, int p, int64_t nx, int64_t
 // parity p (ghosts on the context's own boundary keep their values: the
 // Dirichlet shell, or a shard's imported faces).  One warp per padded row;
 // edge and corner ghosts (never read) are skipped.
+// The largest positive finite value written goes into *vmax (its bit
+// pattern, atomic maximum: positive doubles order like their bit patterns),
+// which anchors the exact arithmetic's window (od_arith.cuh); one atomic per
+// warp.
 __global__ void k_scatter(const ChareDev *ch, int nch, int p, int64_t nx, int64_t ny, int64_t nz,
-                          const double *g) {
+                          const double *g, unsigned long long *vmax) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    unsigned long long vm = 0;
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
         const int nrow = C.rows * (C.bz + 2);
@@ -247,16 +288,28 @@ __global__ void k_scatter(const ChareDev *ch, int nch, int p, int64_t nx, int64_
                 if ((gy_ghost || gz_ghost) && (cp == 0 || cp == C.bx + 1)) continue;
                 const int64_t gx = C.x0 + cp;
                 if (gx == 0 || gx == nx + 1) continue;
-                dst[cp] = src[gx];
+                const double v = src[gx];
+                dst[cp] = v;
+                const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+                if (b < 0x7FF0000000000000ull && b > vm) vm = b;  // positive and finite
             }
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xFFFFFFFFu, vm, o);
+        vm = w > vm ? w : vm;
+    }
+    if (lane == 0 && vm != 0 && vmax) atomicMax(vmax, vm);
 }
 
 // Arithmetic self-test: op 0 div6, 1 add (integer pipes); 2 division by 6,
 // 3 add (FP64 pipe); 10+m the whole Jacobi update in arithmetic mode m over
 // six operands per element (a[6i .. 6i+5]).
 __global__ void k_arith(int op, const double *a, const double *b, double *out, int64_t n) {
+    // anchored ops: b[0] holds the anchor exponent (clamped as on the host)
+    const uint32_t e0 =
+        op >= 30 ? (uint32_t)fmin(fmax(b[0], (double)kAnchorMin), (double)kAnchorMax) : kAnchorMin;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double r;
         switch (op) {
@@ -265,7 +318,9 @@ __global__ void k_arith(int op, const double *a, const double *b, double *out, i
             case 2: r = __ddiv_rn(a[i], 6.0); break;
             case 3: r = __dadd_rn(a[i], b[i]); break;
             default:
-                r = op < 20 ? jacobi_update_mode(op - 10, a + 6 * i) : jacobi2d_update_mode(op - 20, a + 4 * i);
+                if (op >= 40) r = jacobi2d_update_anchored_mode(op - 40, a + 4 * i, e0);
+                else if (op >= 30) r = jacobi_update_anchored_mode(op - 30, a + 6 * i, e0);
+                else r = op < 20 ? jacobi_update_mode(op - 10, a + 6 * i) : jacobi2d_update_mode(op - 20, a + 4 * i);
                 break;
         }
         out[i] = r;
@@ -385,8 +440,14 @@ cudaError_t launch_gather(const ChareDev *ch, int nch, int parity, int64_t nx, i
 }
 
 cudaError_t launch_scatter(const ChareDev *ch, int nch, int parity, int64_t nx, int64_t ny, int64_t nz,
-                           const double *g, cudaStream_t s) {
-    k_scatter<<<dim3(io_grid_x(nch), io_grid_y(nch)), 256, 0, s>>>(ch, nch, parity, nx, ny, nz, g);
+                           const double *g, uint64_t *vmax, cudaStream_t s) {
+    k_scatter<<<dim3(io_grid_x(nch), io_grid_y(nch)), 256, 0, s>>>(ch, nch, parity, nx, ny, nz, g,
+                                                                    (unsigned long long *)vmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ghost_refresh(const ChareDev *ch, int nch, int parity, cudaStream_t s) {
+    k_ghost_refresh<<<dim3(8, io_grid_y(nch)), 256, 0, s>>>(ch, nch, parity);
     return cudaGetLastError();
 }
 

@@ -8,7 +8,7 @@
 namespace od {
 
 // Tile kernels exist for (threads, cells per thread) in {128}x{2,4,8},
-// {256}x{1,2,4,8}, {512}x{1,2}, arithmetic modes 0..8 and both stencils
+// {256}x{1,2,4,8}, {512}x{1,2}, arithmetic modes 0..15 and both stencils
 // (OD_STENCIL_3D7, OD_STENCIL_2D5) (od_tile.cuh).
 bool tile_shape_supported(int threads, int cpt, int amode, int stencil);
 
@@ -50,7 +50,11 @@ cudaError_t launch_gather(const ChareDev *ch, int nch, int parity, int64_t nx, i
 // Arithmetic self-test over device arrays (op: 0 div6, 1 add on the integer
 // pipes; 2 division by 6, 3 add on the FP64 pipe).
 cudaError_t launch_arith(int op, const double *a, const double *b, double *out, int64_t n, cudaStream_t s);
+// Import (od_write): also raises *vmax (device word, may be null) to the
+// bit pattern of the largest positive finite value written.
 cudaError_t launch_scatter(const ChareDev *ch, int nch, int parity, int64_t nx, int64_t ny, int64_t nz,
-                           const double *g, cudaStream_t s);
+                           const double *g, uint64_t *vmax, cudaStream_t s);
+// Internal ghost layers of parity `parity` from the neighbours' boundaries.
+cudaError_t launch_ghost_refresh(const ChareDev *ch, int nch, int parity, cudaStream_t s);
 
 }  // namespace od

@@ -15,6 +15,7 @@
 // layout instead of the context arena.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -37,15 +38,23 @@ double *g_scratch_ptr[kMaxDevices] = {nullptr};
 od_status set_error(od_status s, const std::string &m) { return od::set_last_error(s, m); }
 
 // One step over the interior of a padded field (x fastest, row length nx+2):
-// the same update as the fused tile kernel (arithmetic mode 2).
-__global__ void k_noalloc_step(const double *__restrict__ src, double *__restrict__ dst, int64_t nx, int64_t ny,
-                               int64_t nz) {
-    const int64_t sx = nx + 2, sxy = sx * (ny + 2), n = nx * ny * nz;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % nx, r = e / nx, j = r % ny, k = r / ny;
-        const int64_t c = (k + 1) * sxy + (j + 1) * sx + i + 1;
-        dst[c] = od::jacobi_update<2>(src[c - 1], src[c + 1], src[c - sx], src[c + sx], src[c - sxy], src[c + sxy]);
-    }
+// the same update as the fused tile kernel (arithmetic mode 2).  The padded
+// grid holds at most OD_NOALLOC_MAX_PADDED_CELLS (2^23) cells, so every index
+// fits 32 bits; threads run along x, blocks along y (grid y) and z (grid z),
+// striding when a grid axis is shorter than the field's, so no index needs
+// a division.
+__global__ void k_noalloc_step(const double *__restrict__ src, double *__restrict__ dst, uint32_t nx, uint32_t ny,
+                               uint32_t nz) {
+    const uint32_t sx = nx + 2u, sxy = sx * (ny + 2u);
+    for (uint32_t k = blockIdx.z; k < nz; k += gridDim.z)
+        for (uint32_t j = blockIdx.y; j < ny; j += gridDim.y) {
+            const uint32_t row = (k + 1u) * sxy + (j + 1u) * sx + 1u;
+            for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x) {
+                const uint32_t c = row + i;
+                dst[c] = od::jacobi_update<2>(src[c - 1u], src[c + 1u], src[c - sx], src[c + sx], src[c - sxy],
+                                              src[c + sxy]);
+            }
+        }
 }
 
 // Device address of the static scratch array on the current device, looked
@@ -92,14 +101,14 @@ extern "C" OD_API od_status od_jacobi_noalloc(const double *u_in, double *u_out,
     cudaError_t e = cudaMemcpyAsync(u_out, u_in, bytes, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && iters > 1) e = cudaMemcpyAsync(scratch, u_in, bytes, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return set_error(OD_ECUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
-    const int64_t n = nx * ny * nz;
-    const int block = 256;
-    const int grid = (int)((n + block - 1) / block < 4096 ? (n + block - 1) / block : 4096);
+    const int block = 128;
+    const dim3 grid((unsigned)std::min<int64_t>((nx + block - 1) / block, 64), (unsigned)std::min<int64_t>(ny, 65535),
+                    (unsigned)std::min<int64_t>(nz, 65535));
     // step t writes u_out when iters-1-t is even, so the last step lands there
     const double *src = u_in;
     for (int32_t t = 0; t < iters; ++t) {
         double *dst = ((iters - 1 - t) % 2 == 0) ? u_out : scratch;
-        k_noalloc_step<<<grid, block, 0, st>>>(src, dst, nx, ny, nz);
+        k_noalloc_step<<<grid, block, 0, st>>>(src, dst, (uint32_t)nx, (uint32_t)ny, (uint32_t)nz);
         e = cudaGetLastError();
         if (e != cudaSuccess) return set_error(OD_ECUDA, std::string("k_noalloc_step: ") + cudaGetErrorString(e));
         src = dst;

@@ -117,7 +117,7 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
         *err = "init_mode must be 0 or 1";
         return OD_EINVAL;
     }
-    if (cfg->path < OD_PATH_PER_CHARE || cfg->path > OD_PATH_PERSISTENT) {
+    if (cfg->path < OD_PATH_PER_CHARE || cfg->path > OD_PATH_FUSED_GRAPH) {
         *err = "unknown path";
         return OD_EINVAL;
     }
@@ -139,8 +139,8 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
     // window; in 2D one window add (measured best for each: 154 and 254 G
     // updates/s on the reference shapes)
     p.amode = cfg->arith >= 0 ? cfg->arith : cfg->stencil == OD_STENCIL_2D5 ? 2 : kDefaultArith;
-    if (p.amode > 11) {
-        *err = "arith must be in [0, 11] (or -1 for the default)";
+    if (p.amode > 15) {
+        *err = "arith must be in [0, 15] (or -1 for the default)";
         return OD_EINVAL;
     }
     if (p.threads != 128 && p.threads != 256 && p.threads != 512) {

@@ -9,9 +9,13 @@
 // and k+1 resident while plane k is computed, with the other `stages` - 3
 // slots in flight.  Every thread owns the same cells of every plane and reads
 // all six neighbours from shared memory.  The new value is stored once to
-// HBM, coalesced, and, on a chare boundary, once more straight into the
-// neighbour's ghost layer (the fused paths' pack + delivery + unpack).  The
-// 2D task (run_tile_2d) is a row segment over a run of rows, the same way.
+// HBM, coalesced.  On the fused paths a tile reads the faces of its
+// neighbour chares straight from their arrays (their boundary planes and
+// rows by further bulk copies into the same ring slot, their boundary column
+// by plain loads issued a plane ahead): delivery and unpack are fused into
+// the load, pack needs nothing, and the cell loop has no face branches.  The
+// 2D task (run_tile_2d) is a row segment over a run of rows, the same way,
+// storing its boundary values into the neighbours' ghost cells.
 //
 // The arithmetic is the Jacobi update of the paper's stencil proxy (Sec. V,
 // "jacobi2d"; 3D 7-point, or the paper's own 2D 5-point) with round-to-
@@ -100,6 +104,11 @@ __device__ __forceinline__ int32_t ld_relaxed(const int32_t *p) {
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
+// orders this CTA's generic stores to shared memory before later bulk copies into it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = now_ns();
@@ -133,43 +142,115 @@ struct Ring {
     uint32_t seq;      // planes issued by this CTA before the current tile
 };
 
-// Where a tile's boundary values go (the neighbours' ghost cells of the
-// destination parity), prepared once per tile by thread 0 in shared memory.
-// For a cell with ring-slot offset r in tile row j and plane k:
-//   x-: xlo + (k+1)*xlo_plane + (j+1)*xlo_pitch    x+: same with xhi
-//   y-: ylo + (k+1)*ylo_plane + r                  y+: same with yhi
-//   z-: zlo + r (plane k == 0)                      z+: zhi + r (k == bz-1)
+// The anchored arithmetic's parameters for one launch: the window anchor for
+// cells with one or no FP64 add (e0), +1 for cells with two or three, and
+// the run-time 1 of the multiply-adds.
+struct Arith {
+    uint32_t e0, one;
+};
+
+template <int AM>
+__device__ __forceinline__ Arith arith_setup(const KArgs &a) {
+    Arith r;
+    r.one = a.one;
+    r.e0 = AM >= 12 ? anchor_for(a.vmax ? *a.vmax : 0ull, 1) : 0u;
+    return r;
+}
+
+// Where a 3D fused tile reads the faces of its neighbours (source parity),
+// prepared once per tile by thread 0 in shared memory:
+//   x-/x+: the neighbour's column next to the face, cell (row, plane) at
+//          x? + (plane+1)*x?_plane + row*x?_pitch (padded coordinates)
+//   y-/y+: the neighbour's row next to the face in padded plane q at
+//          y? + q*y?_plane (same x extent, so the same pitch)
+//   z-/z+: the neighbour's plane next to the face, the tile's rows (same x
+//          and y extents, so the same layout)
+// (null: a domain face, whose ghost layer holds the Dirichlet shell).
+struct PullInfo {
+    const double *xlo, *xhi, *ylo, *yhi, *zlo, *zhi;
+    int32_t xlo_pitch, xlo_plane, xhi_pitch, xhi_plane, ylo_plane, yhi_plane;
+};
+
+// Where a 2D fused tile's boundary values go (the neighbours' ghost cells of
+// the destination parity): x-: xlo + (row+1)*xlo_plane, x+: likewise; z-/z+:
+// the neighbour's ghost row, zlo + r / zhi + r.
 struct PushInfo {
     double *xlo, *xhi, *ylo, *yhi, *zlo, *zhi;
     int32_t xlo_pitch, xlo_plane, xhi_pitch, xhi_plane, ylo_plane, yhi_plane;
 };
 
 constexpr int kSmemBars = 0;     // up to 8 mbarriers
-constexpr int kSmemPush = 64;    // PushInfo
+constexpr int kSmemPush = 64;    // PullInfo (3D) / PushInfo (2D)
 constexpr int kSmemRing = 256;   // first ring slot (matches the planner's header)
 static_assert(sizeof(PushInfo) <= kSmemRing - kSmemPush, "push info overflows the header");
+static_assert(sizeof(PullInfo) <= kSmemRing - kSmemPush, "pull info overflows the header");
 
-// Per-cell word: bits 0-15 ring-slot offset r of the cell, 16-26 tile row j,
-// 27 the slot holds a real cell (not a copy of cell 0 past the tile's end),
-// 28/29/30/31 the cell lies on a face with an x-/x+/y-/y+ neighbour.
+// Per-cell word of the 2D sweep: bits 0-15 ring-slot offset r of the cell,
+// 27 the slot holds a real cell, 28/29 the cell lies on a face with an x-/x+
+// neighbour.
 constexpr uint32_t kValid = 1u << 27;
-constexpr uint32_t kXlo = 1u << 28, kXhi = 1u << 29, kYlo = 1u << 30, kYhi = 1u << 31;
+constexpr uint32_t kXlo = 1u << 28, kXhi = 1u << 29;
+
+// The 3D update of one cell in arithmetic mode AM (see od_config.arith);
+// ok = false sends the cell to update_slow.  m is the cell's slot in its
+// thread (a compile-time constant after unrolling), which the mixed modes
+// use to alternate forms.
+template <int AM>
+__device__ __forceinline__ double update_cell(const double *sd, const double *sc, const double *su, int r, int pitch,
+                                              int m, const Arith &ar, bool &ok) {
+    const double W = sc[r - 1], E = sc[r + 1], S = sc[r - pitch], N = sc[r + pitch], D = sd[r], U = su[r];
+    if constexpr (AM == 12) {
+        return jacobi_update_anchored<2>(W, E, S, N, D, U, ar.e0 + 1u, ok, ar.one);
+    } else if constexpr (AM == 13) {
+        return jacobi_update_anchored<1>(W, E, S, N, D, U, ar.e0, ok, ar.one);
+    } else if constexpr (AM == 14 || AM == 15) {
+        // 14: one FP64 add on every other cell, 15: on every fourth cell
+        if ((AM == 14 && (m & 1)) || (AM == 15 && (m & 3) == 0))
+            return jacobi_update_anchored<1>(W, E, S, N, D, U, ar.e0, ok, ar.one);
+        return jacobi_update_anchored<2>(W, E, S, N, D, U, ar.e0 + 1u, ok, ar.one);
+    } else if constexpr (AM == 9 || AM == 10 || AM == 11) {
+        // the tail form: the last one or two adds in the window, the division
+        // from the window word; 11 mixes them cell by cell
+        if ((AM == 11 && (m & 1)) || AM == 10) return jacobi_update_tail<2>(W, E, S, N, D, U, ok);
+        return jacobi_update_tail<1>(W, E, S, N, D, U, ok);
+    } else if constexpr ((AM == 7 || AM == 8)) {
+        // 7: every other cell with two window adds, 8: one cell in four
+        if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0))
+            return jacobi_update_fast<3>(W, E, S, N, D, U, ok);
+        return jacobi_update_fast<2>(W, E, S, N, D, U, ok);
+    } else {
+        return jacobi_update_fast<AM>(W, E, S, N, D, U, ok);
+    }
+}
 
 // Sweep one tile from parity sp into parity sp^1.  Returns false (all
 // threads agree) if a wait ran out; the error is recorded and thread 0 has
 // waited, bounded, for the copies this tile still had in flight.
-template <int NT, int CPT, bool PUSH, int AM>
-__device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ring &ring, PushInfo *pi,
-                                         int step) {
+//
+// FUSED = false (the per-chare path): the chare's own ghost layers are
+// current (unpacked), and the tile reads them with its rows.  FUSED = true
+// (the fused and persistent paths): every internal face is read from the
+// neighbour's array in the source parity, which the neighbour finished in
+// the previous step -- a z-ghost plane is copied from the neighbour's
+// boundary plane, a y-ghost row from its boundary row (a second and third
+// bulk copy beside the tile's own rows), and the x-ghost column of each
+// computed plane is patched into the ring slot from the neighbour's boundary
+// column by plain loads, issued one plane ahead.  Nothing is written outside
+// the chare's own interior, so the cell loop has no face branches.
+template <int NT, int CPT, bool FUSED, int AM>
+__device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ring &ring, PullInfo *pi, int step,
+                                         const Arith &ar) {
     const TileDev T = a.tiles[tile_id];
     const ChareDev &C = a.ch[T.c];
     const int bx = C.bx, by = C.by, bz = C.bz, pitch = C.pitch;
     const int plane = (by + 2) * pitch;
     const int dp = sp ^ 1;
+    const int nj = T.nj, j0 = T.j0;
     // row j0 (the tile's lower y-halo row) of plane 0; plane p+1 holds interior plane p
-    const double *__restrict__ src = C.A[sp] + (size_t)T.j0 * pitch;
-    double *__restrict__ dst = C.A[dp] + (size_t)T.j0 * pitch;
-    const uint32_t run_bytes = (uint32_t)((T.nj + 2) * pitch) * 8u;  // one plane's rows
+    const double *__restrict__ src = C.A[sp] + (size_t)j0 * pitch;
+    double *__restrict__ dst = C.A[dp] + (size_t)j0 * pitch;
+    const uint32_t row_bytes = (uint32_t)pitch * 8u;
+    const uint32_t run_bytes = (uint32_t)(nj + 2) * row_bytes;  // one plane's rows
     const int S = a.stages, SD = a.stage_doubles;
     const int kb = T.k0 - 1, ke = T.k0 + T.nk;  // planes kb..ke are loaded
     const int tid = threadIdx.x;
@@ -179,10 +260,33 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     // the slot's use count & 1.
     auto slot = [&](int p) -> uint32_t { return (seq0 + (uint32_t)(p - kb)) % (uint32_t)S; };
     auto phase = [&](int p) -> uint32_t { return ((seq0 + (uint32_t)(p - kb)) / (uint32_t)S) & 1u; };
-    auto issue = [&](int p, uint32_t s) {  // s = slot(p)
+    // (thread 0) the copies of plane p into slot s
+    auto issue = [&](int p, uint32_t s) {
         uint64_t *bar = ring.bars + s;
+        double *slot_p = ring.base + (size_t)s * SD;
         mbar_expect_tx(bar, run_bytes);
-        bulk_g2s(ring.base + (size_t)s * SD, src + (size_t)(p + 1) * plane, run_bytes, bar);
+        if (FUSED && p < 0 && pi->zlo) {  // the z- neighbour's top plane
+            bulk_g2s(slot_p, pi->zlo, run_bytes, bar);
+        } else if (FUSED && p >= bz && pi->zhi) {  // the z+ neighbour's bottom plane
+            bulk_g2s(slot_p, pi->zhi, run_bytes, bar);
+        } else {
+            // a computed plane's y-ghost rows come from the y neighbours (the
+            // planes below and above the tile are read at its own cells only)
+            const bool computed = p >= T.k0 && p < ke;
+            const double *row0 = src + (size_t)(p + 1) * plane;
+            int first = 0, last = nj + 1;  // rows of the run taken from this chare
+            if (FUSED && computed && pi->ylo) {  // the run's first row is the y-ghost row
+                bulk_g2s(slot_p, pi->ylo + (size_t)(p + 1) * pi->ylo_plane, row_bytes, bar);
+                first = 1;
+            }
+            if (FUSED && computed && pi->yhi) {
+                bulk_g2s(slot_p + (size_t)(nj + 1) * pitch, pi->yhi + (size_t)(p + 1) * pi->yhi_plane, row_bytes,
+                         bar);
+                last = nj;
+            }
+            bulk_g2s(slot_p + (size_t)first * pitch, row0 + (size_t)first * pitch,
+                     (uint32_t)(last - first + 1) * row_bytes, bar);
+        }
     };
     int issued_hi = kb - 1;  // highest plane issued so far (same value in every thread)
     // (a ring of S slots holds planes k-1, k, k+1 and S-3 planes in flight)
@@ -193,172 +297,149 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     };
 
     if (tid == 0) {
-        const int last = min(ke, kb + S - 1);
-        for (int p = kb; p <= last; ++p) issue(p, slot(p));
-        if (PUSH) {
-            PushInfo q;
+        if (FUSED) {
+            PullInfo q;
             q.xlo = q.xhi = q.ylo = q.yhi = q.zlo = q.zhi = nullptr;
             q.xlo_pitch = q.xlo_plane = q.xhi_pitch = q.xhi_plane = q.ylo_plane = q.yhi_plane = 0;
-            if (C.nbr[OD_FACE_XLO] >= 0) {
+            if (C.nbr[OD_FACE_XLO] >= 0) {  // its column bx_n
                 const ChareDev &N = a.ch[C.nbr[OD_FACE_XLO]];
                 q.xlo_pitch = N.pitch;
                 q.xlo_plane = (N.by + 2) * N.pitch;
-                q.xlo = N.A[dp] + (size_t)T.j0 * N.pitch + (N.bx + 1);
+                q.xlo = N.A[sp] + N.bx;
             }
-            if (C.nbr[OD_FACE_XHI] >= 0) {
+            if (C.nbr[OD_FACE_XHI] >= 0) {  // its column 1
                 const ChareDev &N = a.ch[C.nbr[OD_FACE_XHI]];
                 q.xhi_pitch = N.pitch;
                 q.xhi_plane = (N.by + 2) * N.pitch;
-                q.xhi = N.A[dp] + (size_t)T.j0 * N.pitch;
+                q.xhi = N.A[sp] + 1;
             }
-            if (C.nbr[OD_FACE_YLO] >= 0) {  // cell row 0 -> its ghost row by_n+1
+            if (j0 == 0 && C.nbr[OD_FACE_YLO] >= 0) {  // its row by_n
                 const ChareDev &N = a.ch[C.nbr[OD_FACE_YLO]];
                 q.ylo_plane = (N.by + 2) * pitch;
-                q.ylo = N.A[dp] + (size_t)N.by * pitch;
+                q.ylo = N.A[sp] + (size_t)N.by * pitch;
             }
-            if (C.nbr[OD_FACE_YHI] >= 0) {  // cell row by-1 -> its ghost row 0
+            if (j0 + nj == by && C.nbr[OD_FACE_YHI] >= 0) {  // its row 1
                 const ChareDev &N = a.ch[C.nbr[OD_FACE_YHI]];
                 q.yhi_plane = (N.by + 2) * pitch;
-                q.yhi = N.A[dp] - (ptrdiff_t)(by - T.j0) * pitch;
+                q.yhi = N.A[sp] + pitch;
             }
-            if (C.nbr[OD_FACE_ZLO] >= 0) {  // plane 0 -> its ghost plane bz_n+1
+            if (kb < 0 && C.nbr[OD_FACE_ZLO] >= 0) {  // its plane bz_n, the tile's rows
                 const ChareDev &N = a.ch[C.nbr[OD_FACE_ZLO]];
-                q.zlo = N.A[dp] + (size_t)(N.bz + 1) * plane + (size_t)T.j0 * pitch;
+                q.zlo = N.A[sp] + (size_t)N.bz * plane + (size_t)j0 * pitch;
             }
-            if (C.nbr[OD_FACE_ZHI] >= 0) q.zhi = a.ch[C.nbr[OD_FACE_ZHI]].A[dp] + (size_t)T.j0 * pitch;
+            if (ke >= bz && C.nbr[OD_FACE_ZHI] >= 0)  // its plane 1
+                q.zhi = a.ch[C.nbr[OD_FACE_ZHI]].A[sp] + plane + (size_t)j0 * pitch;
             *pi = q;
         }
+        const int last = min(ke, kb + S - 1);
+        for (int p = kb; p <= last; ++p) issue(p, slot(p));
     }
     issued_hi = min(ke, kb + S - 1);
 
-    // this thread's cells: q = tid + m*NT in the tile plane, row-major.  A slot
-    // past the end of the tile repeats the tile's first cell (it stores the
-    // same value to the same place, and pushes nothing), so the cell loop
-    // needs no validity branch.
-    const int ncell = T.nj * bx;
-    uint32_t rf[CPT];
+    // this thread's cells: q = tid + m*NT in the tile plane, row-major, as
+    // ring-slot offsets.  A slot past the end of the tile repeats the tile's
+    // first cell (it stores the same value to the same place), so the cell
+    // loop needs no validity branch.
+    const int ncell = nj * bx;
+    int rf[CPT];
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
         const int q0 = tid + m * NT;
-        const bool valid = q0 < ncell;
-        const int q = valid ? q0 : 0;
-        const int j = q / bx, i = q - j * bx, gj = T.j0 + j;
-        uint32_t w = (uint32_t)((j + 1) * pitch + i + 1) | ((uint32_t)j << 16);
-        if (valid) {
-            w |= kValid;
-            if (PUSH) {
-                if (i == 0 && C.nbr[OD_FACE_XLO] >= 0) w |= kXlo;
-                if (i == bx - 1 && C.nbr[OD_FACE_XHI] >= 0) w |= kXhi;
-                if (gj == 0 && C.nbr[OD_FACE_YLO] >= 0) w |= kYlo;
-                if (gj == by - 1 && C.nbr[OD_FACE_YHI] >= 0) w |= kYhi;
-            }
-        }
-        rf[m] = w;
+        const int q = q0 < ncell ? q0 : 0;
+        const int j = q / bx, i = q - j * bx;
+        rf[m] = (j + 1) * pitch + i + 1;
     }
 
-    // Planes k-1, k and k+1 must be resident while plane k is computed (the
-    // z-1 value is read from the ring, not kept in registers), so a slot is
-    // refilled once the plane after next has been computed.
+    // x-halo patches of a plane (fused only): item t < 2*nj is row t % nj of
+    // face t / nj; ring-slot offset of its ghost cell and the neighbour cell
+    // it copies
+    const int npatch = FUSED ? 2 * nj : 0;
+    auto patch_src = [&](int t, int p) -> const double * {
+        const bool hi = t >= nj;
+        const int j = hi ? t - nj : t;
+        const double *base = hi ? pi->xhi : pi->xlo;
+        if (!base) return nullptr;
+        const int pl = hi ? pi->xhi_plane : pi->xlo_plane, pt = hi ? pi->xhi_pitch : pi->xlo_pitch;
+        return base + (size_t)(p + 1) * pl + (size_t)(j0 + j + 1) * pt;
+    };
+    auto patch_dst = [&](int t) -> int {
+        const bool hi = t >= nj;
+        return ((hi ? t - nj : t) + 1) * pitch + (hi ? bx + 1 : 0);
+    };
+
+    // Planes k-1, k and k+1 must be resident while plane k is computed, so a
+    // slot is refilled once the plane after next has been computed.
+    if (FUSED) __syncthreads();  // the pull info
     bool fail = !mbar_wait_bounded(ring.bars + slot(kb), phase(kb), a.spin_ns);
     if (!fail) fail = !mbar_wait_bounded(ring.bars + slot(kb + 1), phase(kb + 1), a.spin_ns);
+    if (FUSED && !fail) {  // the first computed plane's x halo
+        double *sl = ring.base + (size_t)slot(kb + 1) * SD;
+        for (int t = tid; t < npatch; t += NT) {
+            const double *g = patch_src(t, kb + 1);
+            if (g) sl[patch_dst(t)] = *g;
+        }
+    }
     if (__syncthreads_or(fail)) {
         if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
         drain(kb);
         return false;
     }
 
-    // One plane: ZP = the plane is a chare z-face with a neighbour there, so
-    // every cell is also stored into that neighbour's ghost plane (zp).
-    auto compute_plane = [&](auto zp_tag, int k, double *zp, const double *sd, const double *sc,
-                             const double *su) {
-        constexpr bool ZP = decltype(zp_tag)::value;
-        double *dpl = dst + (size_t)(k + 1) * plane;
-        // no validity branch: a slot past the tile's end repeats the tile's
-        // first cell, so it stores the same value to the same place
-        auto store = [&](uint32_t w, int r, double v) {
-            dpl[r] = v;
-            if (PUSH) {
-                const uint32_t xf = w & (kXlo | kXhi);
-                if (xf) {  // a row's first and last lanes take one path together
-                    const int j1 = (int)((w >> 16) & 0x7FFu) + 1;
-                    const bool lo = (w & kXlo) != 0;
-                    double *base = lo ? pi->xlo : pi->xhi;
-                    const int pl = lo ? pi->xlo_plane : pi->xhi_plane, pt = lo ? pi->xlo_pitch : pi->xhi_pitch;
-                    base[(size_t)(k + 1) * pl + (size_t)j1 * pt] = v;
-                    if (xf == (kXlo | kXhi))  // bx == 1: the cell is on both x faces
-                        pi->xhi[(size_t)(k + 1) * pi->xhi_plane + (size_t)j1 * pi->xhi_pitch] = v;
-                }
-                const uint32_t yf = w & (kYlo | kYhi);
-                if (yf) {  // whole rows: the branch is uniform across a row's lanes
-                    const bool lo = (w & kYlo) != 0;
-                    double *base = lo ? pi->ylo : pi->yhi;
-                    base[(size_t)(k + 1) * (lo ? pi->ylo_plane : pi->yhi_plane) + r] = v;
-                    if (yf == (kYlo | kYhi))  // by == 1: the row is on both y faces
-                        pi->yhi[(size_t)(k + 1) * pi->yhi_plane + r] = v;
-                }
-                if (ZP) zp[r] = v;
-            }
-        };
-        uint32_t bad = 0;  // bit m: cell m left the integer routines' domain
-#pragma unroll
-        for (int m = 0; m < CPT; ++m) {
-            const uint32_t w = rf[m];
-            const int r = (int)(w & 0xFFFFu);
-            bool ok;
-            // modes 7 and 8 mix the per-cell placement to balance the FP64 and
-            // integer pipes: 7 = every other cell with two window adds, 8 =
-            // one cell in four (m is a compile-time constant after unrolling)
-            // modes 9-11: the tail form (the last one or two adds in the window,
-            // the division from the window word); 11 mixes them like 7
-            [[maybe_unused]] constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
-            double v;
-            if constexpr (AM == 9 || AM == 10 || AM == 11) {
-                if ((AM == 11 && (m & 1)) || AM == 10)
-                    v = jacobi_update_tail<2>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
-                else
-                    v = jacobi_update_tail<1>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
-            } else if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0)) {
-                v = jacobi_update_fast<3>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
-            } else {
-                v = jacobi_update_fast<AMa>(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r], ok);
-            }
-            bad |= (ok ? 0u : 1u) << m;
-            store(w, r, v);
-        }
-        if (bad) {  // rare: recompute those cells with IEEE operations and store them again
-#pragma unroll
-            for (int m = 0; m < CPT; ++m) {
-                const uint32_t w = rf[m];
-                const int r = (int)(w & 0xFFFFu);
-                if (bad & (1u << m))
-                    store(w, r, update_slow(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r]));
-            }
-        }
-    };
-
     // ring slots of planes k-1, k, k+1 and the phase of k+1, advanced by one
     // position per plane (no division by the run-time ring depth in the loop)
     uint32_t sl_m1 = slot(kb), sl_0 = slot(kb + 1), sl_p1 = slot(kb + 2), ph_p1 = phase(kb + 2);
     for (int k = T.k0; k < ke; ++k) {
+        // the next plane's x halo, loaded while this plane is computed
+        const bool patch_next = FUSED && k + 1 < ke;
+        double xv = 0.0;
+        const double *xg = nullptr;
+        if (patch_next && tid < npatch) {
+            xg = patch_src(tid, k + 1);
+            if (xg) xv = *xg;
+        }
         fail = !mbar_wait_bounded(ring.bars + sl_p1, ph_p1, a.spin_ns);
         if (!fail) {
             const double *sd = ring.base + (size_t)sl_m1 * SD;
             const double *sc = ring.base + (size_t)sl_0 * SD;
-            const double *su = ring.base + (size_t)sl_p1 * SD;
-            double *z0 = (PUSH && k == 0) ? pi->zlo : nullptr;
-            double *z1 = (PUSH && k == bz - 1) ? pi->zhi : nullptr;
-            if (z0) compute_plane(std::true_type(), k, z0, sd, sc, su);
-            if (z1) compute_plane(std::true_type(), k, z1, sd, sc, su);  // bz == 1 with both: the plane twice
-            if (!z0 && !z1) compute_plane(std::false_type(), k, nullptr, sd, sc, su);
+            double *su = ring.base + (size_t)sl_p1 * SD;
+            double *dpl = dst + (size_t)(k + 1) * plane;
+            uint32_t bad = 0;  // bit m: cell m left the integer routines' domain
+#pragma unroll
+            for (int m = 0; m < CPT; ++m) {
+                const int r = rf[m];
+                bool ok;
+                const double v = update_cell<AM>(sd, sc, su, r, pitch, m, ar, ok);
+                bad |= (ok ? 0u : 1u) << m;
+                dpl[r] = v;
+            }
+            if (bad) {  // rare: recompute those cells with IEEE operations and store them again
+#pragma unroll
+                for (int m = 0; m < CPT; ++m) {
+                    const int r = rf[m];
+                    if (bad & (1u << m))
+                        dpl[r] = update_slow(sc[r - 1], sc[r + 1], sc[r - pitch], sc[r + pitch], sd[r], su[r]);
+                }
+            }
+            if (patch_next) {  // plane k+1's x halo (its slot is only read at interior cells above)
+                if (xg) su[patch_dst(tid)] = xv;
+                for (int t = tid + NT; t < npatch; t += NT) {  // tiles of more than NT/2 rows
+                    const double *g = patch_src(t, k + 1);
+                    if (g) su[patch_dst(t)] = *g;
+                }
+            }
         }
         if (__syncthreads_or(fail)) {
             if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
             drain(k + 1);
             return false;
         }
-        // plane k-1 is no longer needed: refill its slot
+        // plane k-1 is no longer needed: refill its slot (after the barrier,
+        // and after a proxy fence when the slot took generic stores of a halo)
         if (k - 1 + S <= ke) {
-            if (tid == 0) issue(k - 1 + S, sl_m1);
+            if (tid == 0) {
+                if (FUSED) fence_proxy_async_smem();
+                issue(k - 1 + S, sl_m1);
+            }
             issued_hi = k - 1 + S;
         }
         sl_m1 = sl_0;
@@ -369,6 +450,7 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
         }
     }
     ring.seq = seq0 + (uint32_t)(ke - kb + 1);
+    if (FUSED && tid == 0) fence_proxy_async_smem();  // before the next tile's copies into these slots
     return true;
 }
 
@@ -387,9 +469,33 @@ static __device__ __noinline__ double update2d_slow(double W, double E, double S
 // i0+i+1, i.e. the tile's cell i.
 // The update reads W = slot[r-1], E = slot[r+1] of plane k, S = plane k-1,
 // N = plane k+1 at r, summed in that order and divided by 4.
+// The 2D update of one cell in arithmetic mode AM (m as in update_cell).
+template <int AM>
+__device__ __forceinline__ double update_cell_2d(double W, double E, double S, double N, int m, const Arith &ar,
+                                                 bool &ok) {
+    if constexpr (AM == 12) {
+        return jacobi2d_update_anchored<1>(W, E, S, N, ar.e0, ok, ar.one);
+    } else if constexpr (AM == 13) {
+        return jacobi2d_update_anchored<0>(W, E, S, N, ar.e0, ok, ar.one);
+    } else if constexpr (AM == 14) {  // no FP64 add on every other cell
+        if (m & 1) return jacobi2d_update_anchored<0>(W, E, S, N, ar.e0, ok, ar.one);
+        return jacobi2d_update_anchored<1>(W, E, S, N, ar.e0, ok, ar.one);
+    } else if constexpr (AM == 15) {
+        return jacobi2d_update_anchored<2>(W, E, S, N, ar.e0 + 1u, ok, ar.one);
+    } else if constexpr (AM == 9 || AM == 10 || AM == 11) {
+        if ((AM == 11 && (m & 1)) || AM == 10) return jacobi2d_update_tail<2>(W, E, S, N, ok);
+        return jacobi2d_update_tail<1>(W, E, S, N, ok);
+    } else if constexpr (AM == 7 || AM == 8) {
+        if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0)) return jacobi2d_update_fast<3>(W, E, S, N, ok);
+        return jacobi2d_update_fast<2>(W, E, S, N, ok);
+    } else {
+        return jacobi2d_update_fast<AM>(W, E, S, N, ok);
+    }
+}
+
 template <int NT, int CPT, bool PUSH, int AM>
 __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp, Ring &ring, PushInfo *pi,
-                                            int step) {
+                                            int step, const Arith &ar) {
     const TileDev T = a.tiles[tile_id];
     const ChareDev &C = a.ch[T.c];
     const int bx = C.bx, bz = C.bz, pitch = C.pitch;
@@ -490,18 +596,7 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
             const uint32_t w = rf[m];
             const int r = (int)(w & 0xFFFFu);
             bool ok;
-            [[maybe_unused]] constexpr int AMa = AM == 7 || AM == 8 ? 2 : AM;
-            double v;
-            if constexpr (AM == 9 || AM == 10 || AM == 11) {
-                if ((AM == 11 && (m & 1)) || AM == 10)
-                    v = jacobi2d_update_tail<2>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
-                else
-                    v = jacobi2d_update_tail<1>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
-            } else if ((AM == 7 && (m & 1)) || (AM == 8 && (m & 3) == 0)) {
-                v = jacobi2d_update_fast<3>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
-            } else {
-                v = jacobi2d_update_fast<AMa>(sc[r - 1], sc[r + 1], sd[r], su[r], ok);
-            }
+            double v = update_cell_2d<AM>(sc[r - 1], sc[r + 1], sd[r], su[r], m, ar, ok);
             if (!ok) v = update2d_slow(sc[r - 1], sc[r + 1], sd[r], su[r]);
             store(w, r, v);
         }
@@ -541,11 +636,15 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
 }
 
 // Stencil dispatch at compile time: ST = OD_STENCIL_3D7 or OD_STENCIL_2D5.
-template <int NT, int CPT, bool PUSH, int AM, int ST>
-__device__ __forceinline__ bool run_any_tile(const KArgs &a, int tile_id, int sp, Ring &ring, PushInfo *pi,
-                                             int step) {
-    if constexpr (ST == OD_STENCIL_2D5) return run_tile_2d<NT, CPT, PUSH, AM>(a, tile_id, sp, ring, pi, step);
-    else return run_tile<NT, CPT, PUSH, AM>(a, tile_id, sp, ring, pi, step);
+// FUSED: the fused and persistent paths' tile (3D: halos pulled from the
+// neighbours; 2D: boundary values pushed into theirs).
+template <int NT, int CPT, bool FUSED, int AM, int ST>
+__device__ __forceinline__ bool run_any_tile(const KArgs &a, int tile_id, int sp, Ring &ring, unsigned char *info,
+                                             int step, const Arith &ar) {
+    if constexpr (ST == OD_STENCIL_2D5)
+        return run_tile_2d<NT, CPT, FUSED, AM>(a, tile_id, sp, ring, reinterpret_cast<PushInfo *>(info), step, ar);
+    else
+        return run_tile<NT, CPT, FUSED, AM>(a, tile_id, sp, ring, reinterpret_cast<PullInfo *>(info), step, ar);
 }
 
 template <int NT>
@@ -562,7 +661,7 @@ __device__ __forceinline__ Ring ring_setup(const KArgs &a, unsigned char *smem) 
     return r;
 }
 
-// One CTA per tile (per-chare compute when !PUSH, fused step when PUSH).
+// One CTA per tile (per-chare compute when !FUSED, fused step when FUSED).
 // Resident threads per SM the register budget must allow (1280 = 51
 // registers a thread): the FP64 pipe needs many warps to hide shared-memory
 // and pipe latency.  A build may override it (-DOD_MIN_THREADS_PER_SM=...).
@@ -578,16 +677,16 @@ constexpr int min_blocks(int nt, int st) {
     return (st == OD_STENCIL_2D5 ? OD_MIN_THREADS_PER_SM_2D : OD_MIN_THREADS_PER_SM) / nt;
 }
 
-template <int NT, int CPT, bool PUSH, int AM, int ST>
+template <int NT, int CPT, bool FUSED, int AM, int ST>
 __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_tiles(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     if (blockDim.x != NT) {
         if (threadIdx.x == 0) record_err(a.err, OD_ERR_BAD_LAUNCH, -1, -1);
         return;
     }
+    const Arith ar = arith_setup<AM>(a);
     Ring ring = ring_setup<NT>(a, smem);
-    run_any_tile<NT, CPT, PUSH, AM, ST>(a, a.tile_begin + (int)blockIdx.x, a.parity, ring,
-                                        reinterpret_cast<PushInfo *>(smem + kSmemPush), -1);
+    run_any_tile<NT, CPT, FUSED, AM, ST>(a, a.tile_begin + (int)blockIdx.x, a.parity, ring, smem + kSmemPush, -1, ar);
 }
 
 // Continuous batching: one fused step of several independent jobs in one
@@ -614,9 +713,10 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_tiles_multi(const KA
         if (threadIdx.x == 0) record_err(a.err, OD_ERR_BAD_LAUNCH, -1, -1);
         return;
     }
+    const Arith ar = arith_setup<AM>(a);
     Ring ring = ring_setup<NT>(a, smem);
-    run_any_tile<NT, CPT, true, AM, ST>(a, (int)blockIdx.x - first[s_job], a.parity, ring,
-                                        reinterpret_cast<PushInfo *>(smem + kSmemPush), -1);
+    run_any_tile<NT, CPT, true, AM, ST>(a, (int)blockIdx.x - first[s_job], a.parity, ring, smem + kSmemPush, -1,
+                                        ar);
 }
 
 // Persistent kernel: CTAs take tickets in step-major order; ticket
@@ -633,6 +733,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_persistent(const KAr
         if (threadIdx.x == 0) record_err(a.err, OD_ERR_BAD_LAUNCH, -1, -1);
         return;
     }
+    const Arith ar = arith_setup<AM>(a);
     Ring ring = ring_setup<NT>(a, smem);
     const int64_t total = (int64_t)a.iters * a.ntiles;
     for (;;) {
@@ -669,9 +770,7 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_persistent(const KAr
             fence_proxy_async();
         }
         if (!__syncthreads_and(ok)) break;
-        if (!run_any_tile<NT, CPT, true, AM, ST>(a, tile, step & 1, ring,
-                                                 reinterpret_cast<PushInfo *>(smem + kSmemPush), step))
-            break;
+        if (!run_any_tile<NT, CPT, true, AM, ST>(a, tile, step & 1, ring, smem + kSmemPush, step, ar)) break;
         if (threadIdx.x == 0 && (int64_t)tile != a.stall_tile) {
             __threadfence();
             st_release(a.epoch + tile, r + 1);

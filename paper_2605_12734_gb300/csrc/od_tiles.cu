@@ -1,5 +1,5 @@
 // od_tiles.cu -- instantiates the tile kernels for one arithmetic mode and
-// one stencil.  Built once per (mode, stencil) with -DOD_AMODE=<0..8> and
+// one stencil.  Built once per (mode, stencil) with -DOD_AMODE=<0..15> and
 // -DOD_STENCIL=<0 (3D 7-point) | 1 (2D 5-point)> (the build compiles the
 // copies in parallel); od_kernels.cu dispatches on both at launch time.
 #include "od_tile.cuh"

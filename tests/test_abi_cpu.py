@@ -116,7 +116,7 @@ def test_plan_model_bytes(od, odf):
     dict(split=(1, 1, 1), dims=(4, 4, 4), threads=96),
     dict(split=(1, 1, 1), dims=(4, 4, 4), cells_per_thread=3),
     dict(split=(1, 1, 1), dims=(4, 4, 4), threads=512, cells_per_thread=4),
-    dict(split=(1, 1, 1), dims=(4, 4, 4), arith=12),
+    dict(split=(1, 1, 1), dims=(4, 4, 4), arith=16),
     dict(split=(1, 1, 1), dims=(4, 4, 4), stages=9),
     dict(split=(1, 1, 1), dims=(4, 4, 4), stages=2),
     dict(split=(1, 1, 1), dims=(4, 4, 4), order=4),

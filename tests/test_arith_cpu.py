@@ -268,3 +268,185 @@ def test_tail_forms_in_the_solver_regime(od, op, n_ops):
             want = want + x[:, k]
         want = want / (6.0 if n_ops == 6 else 4.0)
     same(od.arith_host(op, np.ascontiguousarray(x).ravel()), want)
+
+
+# ---------------------------------------------------------------- anchored window
+#
+# The anchored forms: op 30+f (3D) / 40+f (2D) with f adds on the FP64 pipe,
+# the rest in one window anchored at the exponent b[0] for every cell; op
+# 34+f / 44+f return the fast form alone (NaN where a cell leaves it), so a
+# test can check both that the fast form is taken and that it is exact.
+
+def _anchor(e0):
+    return np.array([float(e0)])
+
+
+def _regime(rng, n, k, lo=-7):
+    """k operands per cell in a Jacobi field's regime: values in [2^lo, 1),
+    most of them near 0.5 (after some smoothing), a tenth spread over every
+    binade of the window, so that partial sums cross binades and round at
+    every position with ties among them."""
+    x = 0.4 + 0.2 * rng.random((n, k))
+    m = n // 10
+    x[:m] = rng.random((m, k)) * 2.0 ** rng.integers(lo, 0, (m, k))
+    x[:m] = np.maximum(x[:m], 2.0 ** lo)
+    return x
+
+
+def _ieee3d(x):
+    with np.errstate(all="ignore"):
+        return (((((x[:, 0] + x[:, 1]) + x[:, 2]) + x[:, 3]) + x[:, 4]) + x[:, 5]) / 6.0
+
+
+def _ieee2d(x):
+    with np.errstate(all="ignore"):
+        return (((x[:, 0] + x[:, 1]) + x[:, 2]) + x[:, 3]) / 4.0
+
+
+@pytest.mark.parametrize("nf", range(4))
+@pytest.mark.parametrize("e0", [4, 1016, 1020, 2030])
+def test_anchored_update_matches_ieee_everywhere(od, nf, e0):
+    # every kind of input (zeros, negatives, subnormals, huge and tiny
+    # exponents, ties), with anchors inside and far from the data
+    rng = np.random.default_rng(300 + 10 * nf + e0 % 7)
+    x = _update_inputs(rng, 200_000)
+    same(od.arith_host(30 + nf, np.ascontiguousarray(x).ravel(), _anchor(e0)), _ieee3d(x))
+
+
+@pytest.mark.parametrize("nf", range(3))
+@pytest.mark.parametrize("e0", [4, 1016, 1020, 2030])
+def test_anchored_update2d_matches_ieee_everywhere(od, nf, e0):
+    rng = np.random.default_rng(400 + 10 * nf + e0 % 7)
+    x = _update2d_inputs(rng, 200_000)
+    same(od.arith_host(40 + nf, np.ascontiguousarray(x).ravel(), _anchor(e0)), _ieee2d(x))
+
+
+@pytest.mark.parametrize("nf", range(4))
+def test_anchored_fast_form_is_taken_and_exact(od, nf):
+    # in the solver's regime with the anchor the library derives for a field
+    # in [0, 1) (largest exponent 1022), every cell takes the fast form and
+    # gives the IEEE bits -- including the many rounding ties of sums whose
+    # operands sit in different binades
+    rng = np.random.default_rng(500 + nf)
+    e0 = 1022 - (5 if nf >= 2 else 6)
+    x = _regime(rng, 1_000_000, 6, lo=e0 - 1023)
+    got = od.arith_host(34 + nf, np.ascontiguousarray(x).ravel(), _anchor(e0))
+    assert not np.isnan(got).any(), f"{int(np.isnan(got).sum())} cells left the fast form"
+    same(got, _ieee3d(x))
+
+
+@pytest.mark.parametrize("nf", range(3))
+def test_anchored2d_fast_form_is_taken_and_exact(od, nf):
+    rng = np.random.default_rng(600 + nf)
+    x = _regime(rng, 1_000_000, 4)
+    got = od.arith_host(44 + nf, np.ascontiguousarray(x).ravel(), _anchor(1016))
+    assert not np.isnan(got).any()
+    same(got, _ieee2d(x))
+
+
+def test_anchored_window_edges(od):
+    # operands at the window's two ends (exponents E0 and E0+7, all-ones and
+    # all-zero significands), partial sums just below powers of two that a
+    # round-up carries into the next binade, and one binade past each end
+    # (which must leave the fast form, not give a wrong value)
+    e0 = 1016
+    rng = np.random.default_rng(700)
+    n = 200_000
+    e = rng.choice([e0, e0 + 1, e0 + 6, e0 + 7], (n, 6)).astype(np.uint64)
+    mant = rng.choice([0, (1 << 52) - 1, (1 << 51), (1 << 52) - 2, 1, 3], (n, 6)).astype(np.uint64)
+    mant[::2] = rng.integers(0, 1 << 52, (n // 2, 6), dtype=np.uint64)
+    x = from_bits((e << np.uint64(52)) | mant)
+    # with no FP64 add every such cell stays in the fast form; with FP64 adds
+    # first, a partial sum past the window's top leaves it (exact either way)
+    for nf in range(4):
+        same(od.arith_host(30 + nf, np.ascontiguousarray(x).ravel(), _anchor(e0)), _ieee3d(x))
+    fast = od.arith_host(34, np.ascontiguousarray(x).ravel(), _anchor(e0))
+    assert not np.isnan(fast).any()
+    x2 = np.ascontiguousarray(x[:, :4])
+    for nf in range(3):
+        same(od.arith_host(40 + nf, x2.ravel(), _anchor(e0)), _ieee2d(x2))
+    assert not np.isnan(od.arith_host(44, x2.ravel(), _anchor(e0))).any()
+    out = x.copy()
+    out[:, 5] = from_bits((np.uint64(e0 - 1) << np.uint64(52)) | mant[:, 5])
+    out[::2, 5] = from_bits((np.uint64(e0 + 8) << np.uint64(52)) | mant[::2, 5])
+    for nf in range(4):
+        same(od.arith_host(30 + nf, np.ascontiguousarray(out).ravel(), _anchor(e0)), _ieee3d(out))
+        fast = od.arith_host(34 + nf, np.ascontiguousarray(out).ravel(), _anchor(e0))
+        assert np.isnan(fast).all(), "an operand outside the window must leave the fast form"
+
+
+def test_anchored_planted_rounding_mistakes_are_caught(od):
+    # the solver-regime inputs distinguish round-to-nearest-even from the
+    # nearby wrong roundings: round half up, truncation and a per-step
+    # rounding at the wrong binade all differ from the IEEE bits on them
+    # (computed here in plain integer arithmetic as the fast form does), so
+    # the tests above would catch such a mistake in the fast form
+    rng = np.random.default_rng(800)
+    x = _regime(rng, 20_000, 6)
+    e0 = 1016
+
+    def fixed(v):
+        b = v.view(np.uint64)
+        e = (b >> np.uint64(52)).astype(np.int64)
+        m = (b & np.uint64((1 << 52) - 1)) | np.uint64(1 << 52)
+        return [int(mi) << int(ei - e0) for mi, ei in zip(m, e)]
+
+    def chain(rule):
+        cols = [fixed(x[:, t]) for t in range(6)]
+        out = []
+        for i in range(len(x)):
+            F = cols[0][i]
+            for t in range(1, 6):
+                F += cols[t][i]
+                d = F.bit_length() - 53
+                q, r = divmod(F, 1 << d)
+                half = 1 << (d - 1)
+                if rule == "even":
+                    q += 1 if (r > half or (r == half and q & 1)) else 0
+                elif rule == "half_up":
+                    q += 1 if r >= half else 0
+                elif rule == "shifted":  # rounds one bit too low
+                    d -= 1
+                    q, r = divmod(F, 1 << d)
+                    if d > 0:
+                        q += 1 if (r > (1 << (d - 1)) or (r == 1 << (d - 1) and q & 1)) else 0
+                F = q << d
+            out.append(F)
+        return np.array([float(F) * 2.0 ** (e0 - 1075) for F in out])
+
+    want = ((((x[:, 0] + x[:, 1]) + x[:, 2]) + x[:, 3]) + x[:, 4]) + x[:, 5]
+    assert np.array_equal(chain("even"), want)
+    for rule in ("half_up", "trunc", "shifted"):
+        assert not np.array_equal(chain(rule), want), rule
+
+
+def test_anchored_last_rounding_carries_into_next_binade(od):
+    # operand sets whose last partial sum rounds up to an exact power of two
+    # (the window word's top bit moves up one place): the division by 6 and
+    # the 2D division by 4 must read the carried word correctly
+    rng = np.random.default_rng(900)
+    e0 = 1016
+    rows = []
+    for _ in range(20_000):
+        k = int(rng.integers(-4, 2))  # target power 2^k + a little less
+        parts = 0.9 + 0.2 * rng.random(5)
+        parts = parts / parts.sum() * (2.0 ** k) * (1 + 2.0 ** -50)
+        last = 2.0 ** k - np.sum(parts[:-1])
+        v = np.concatenate([parts[:-1], [last]])
+        v = np.maximum(v, 2.0 ** -7)
+        s = ((((v[0] + v[1]) + v[2]) + v[3]) + v[4])
+        # choose the sixth operand so the total sits within an ulp of 2^(k+1)
+        sixth = 2.0 ** (k + 1) - s
+        sixth = np.nextafter(sixth, 0.0) if rng.random() < 0.5 else sixth
+        rows.append(np.concatenate([v[:5], [sixth]]))
+    x = np.array(rows)
+    x = x[(x >= 2.0 ** -7).all(axis=1) & (x < 1.0).all(axis=1)]
+    assert len(x) > 1000
+    tot = _ieee3d(x) * 6.0
+    assert np.any(np.log2(tot) == np.round(np.log2(tot))), "no sum landed on a power of two"
+    for nf in range(3):
+        same(od.arith_host(30 + nf, np.ascontiguousarray(x).ravel(), _anchor(e0)), _ieee3d(x))
+        assert not np.isnan(od.arith_host(34 + nf, np.ascontiguousarray(x).ravel(), _anchor(e0))).any()
+    x2 = np.ascontiguousarray(x[:, [0, 1, 2, 5]])
+    for nf in range(3):
+        same(od.arith_host(40 + nf, x2.ravel(), _anchor(e0)), _ieee2d(x2))

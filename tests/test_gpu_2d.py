@@ -14,7 +14,7 @@ from paper_2605_12734_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-PATHS = ["per_chare", "fused", "graph", "persistent"]
+PATHS = ["per_chare", "fused", "graph", "persistent", "fused_graph"]
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +84,7 @@ def test_2d_zero_iterations_is_initial_field(od, path):
     dict(threads=512, cells_per_thread=1), dict(threads=512, cells_per_thread=2, stages=3),
     dict(threads=256, cells_per_thread=4, stages=8),
     dict(threads=128, cells_per_thread=4, tile_y=6, tile_z=1),
-] + [dict(arith=m) for m in range(12)])
+] + [dict(arith=m) for m in range(16)])
 @pytest.mark.parametrize("path", ["fused", "persistent"])
 def test_2d_launch_shapes(od, path, shape):
     nx, ny = 777, 45

@@ -73,3 +73,44 @@ def test_update_every_mode_device(env, mode):
     xd = torch.from_numpy(np.ascontiguousarray(x).ravel()).to("cuda:0")
     got = pkg.arith_device(10 + mode, xd).cpu().numpy()
     host.same(got, want)
+
+
+def _anchor_dev(torch, e0):
+    return torch.tensor([float(e0)], dtype=torch.float64, device="cuda:0")
+
+
+@pytest.mark.parametrize("nf", range(4))
+def test_anchored_update_device(env, nf):
+    # the anchored window on the GPU (multiply-adds on the FMA pipe, the
+    # binary32 rounding of the low word) equals the host IEEE chain on every
+    # kind of input, and in the solver's regime takes the fast form on every
+    # cell with every result exact
+    pkg, torch = env
+    import test_arith_cpu as host
+    rng = np.random.default_rng(300 + nf)
+    x = host._update_inputs(rng, 2_000_000)
+    xd = torch.from_numpy(np.ascontiguousarray(x).ravel()).to("cuda:0")
+    for e0 in (4, 1016, 1017, 2030):
+        host.same(pkg.arith_device(30 + nf, xd, _anchor_dev(torch, e0)).cpu().numpy(), host._ieee3d(x))
+    e0 = 1022 - (5 if nf >= 2 else 6)
+    r = host._regime(rng, 4_000_000, 6, lo=e0 - 1023)
+    rd = torch.from_numpy(np.ascontiguousarray(r).ravel()).to("cuda:0")
+    fast = pkg.arith_device(34 + nf, rd, _anchor_dev(torch, e0)).cpu().numpy()
+    assert not np.isnan(fast).any()
+    host.same(fast, host._ieee3d(r))
+
+
+@pytest.mark.parametrize("nf", range(3))
+def test_anchored_update2d_device(env, nf):
+    pkg, torch = env
+    import test_arith_cpu as host
+    rng = np.random.default_rng(400 + nf)
+    x = host._update2d_inputs(rng, 2_000_000)
+    xd = torch.from_numpy(np.ascontiguousarray(x).ravel()).to("cuda:0")
+    for e0 in (4, 1016, 1017, 2030):
+        host.same(pkg.arith_device(40 + nf, xd, _anchor_dev(torch, e0)).cpu().numpy(), host._ieee2d(x))
+    r = host._regime(rng, 4_000_000, 4, lo=-6 if nf == 2 else -7)
+    rd = torch.from_numpy(np.ascontiguousarray(r).ravel()).to("cuda:0")
+    fast = pkg.arith_device(44 + nf, rd, _anchor_dev(torch, 1017 if nf == 2 else 1016)).cpu().numpy()
+    assert not np.isnan(fast).any()
+    host.same(fast, host._ieee2d(r))

@@ -3,10 +3,12 @@ memory where they call (a framework owning all device memory through its own
 pool, or a latency-critical loop where cudaMalloc would synchronise the
 device).  Its double buffer is a static device array shared by every call.
 
-It is checked through the C ABI against the existing entry points
-(od_create / od_step / od_read on a decomposed grid), bit for bit -- the
-tolerance every parity test here uses -- on two calls in a row with different
-sizes, so the second call cannot lean on what the first one left in the shared
+It is checked through the C ABI against the CPU oracle's undecomposed sweep
+and against the existing entry points (od_create / od_step / od_read on a
+decomposed grid), bit for bit -- the tolerance every parity test here uses --
+on calls in a row with different sizes and iteration counts, including 0 (the
+input comes back) and 1 (the scratch is never seeded; the one step writes
+u_out), so no call can lean on what an earlier one left in the shared
 scratch.  This file is collected last so that a run stopping at its first
 failure has run every other test already."""
 import ctypes
@@ -49,11 +51,15 @@ def run_noalloc(pkg, torch, nx, ny, nz, seed, mode, iters):
     return out, src
 
 
-def test_noalloc_matches_existing_entry_points_twice(env):
+def test_noalloc_matches_oracle_and_existing_entry_points_in_a_row(env):
     pkg, torch = env
-    cases = [(40, 36, 30, 12, 1, 7, (2, 3, 2)), (24, 20, 18, 5, 0, 4, (3, 2, 2))]
+    # odd and even counts, one step (the scratch is not used) and none
+    cases = [(40, 36, 30, 12, 1, 7, (2, 3, 2)), (24, 20, 18, 5, 0, 4, (3, 2, 2)),
+             (17, 9, 13, 3, 1, 1, (2, 1, 3)), (8, 8, 8, 2, 1, 0, (2, 2, 2)), (33, 5, 7, 9, 1, 2, (1, 1, 1))]
     for (nx, ny, nz, seed, mode, iters, split) in cases:
-        want = reference_interior(pkg, nx, ny, nz, seed, mode, iters, split)
+        want = oracle.solve(nx, ny, nz, seed, mode, iters)
+        fused = reference_interior(pkg, nx, ny, nz, seed, mode, iters, split)
+        assert np.array_equal(fused.view(np.uint64), want.view(np.uint64)), (nx, ny, nz, iters)
         out, src = run_noalloc(pkg, torch, nx, ny, nz, seed, mode, iters)
         got = np.ascontiguousarray(out[1:-1, 1:-1, 1:-1]).ravel()
         assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), (nx, ny, nz, iters)
