@@ -147,14 +147,22 @@ typedef struct od_config {
     int32_t arith;               /* where the update's operations run (the bits
                                     never change): 0 all on the FP64 pipe;
                                     1 division by 6 on the integer pipes;
-                                    1+k (k = 1..5) also the first k adds on the
-                                    integer pipes; 7 / 8: modes 2 and 3 mixed
-                                    cell by cell (half / a quarter of the cells
-                                    in mode 3); 9 / 10: the last one / two adds
-                                    on the integer pipes and the division taken
-                                    from their result; 11: 9 and 10 mixed cell
-                                    by cell; -1 = library default (10; 2 for
-                                    the 2D stencil) */
+                                    1+k (k = 1..5) also the first k adds in an
+                                    integer window aligned per cell; 7 / 8:
+                                    modes 2 and 3 mixed cell by cell (half / a
+                                    quarter of the cells in mode 3); 9 / 10:
+                                    the last one / two adds in that window and
+                                    the division from their result; 11: 9 and
+                                    10 mixed; 12: two FP64 adds, the other
+                                    three adds and the division in one integer
+                                    window anchored for the whole field at its
+                                    largest value (see od_write); 13: one FP64
+                                    add, four window adds; 14 / 15: 13 on every
+                                    other / every fourth cell, 12 on the rest.
+                                    2D: 12 one FP64 add and two window adds,
+                                    13 none and three, 14 the two mixed, 15
+                                    two FP64 adds and one window add.  -1 =
+                                    library default (12) */
     int32_t order;               /* persistent path task order, bits: 1 = reversed
                                     on odd steps, 2 = chares in Morton (Z) order
                                     instead of x-fastest; 0..3 */
@@ -297,7 +305,12 @@ OD_API od_status od_read_cells(od_ctx *ctx, const int64_t *cells, int64_t n, dou
  * device memory, or host memory copied through the staging buffer) and
  * refresh every internal ghost layer; the
  * Dirichlet shell is kept.  Used to import a checkpoint or a user field.
- * Enqueued on the stream (host sources are copied before return). */
+ * Enqueued on the stream (host sources are copied before return).  The
+ * context keeps the largest positive value its field has held (the initial
+ * field's values lie in [0, 1)), raised here by the values written; the
+ * anchored arithmetic modes place their integer window there, so a field
+ * that later lies far below that value runs mostly in the IEEE form --
+ * slower, with the same bits. */
 OD_API od_status od_write(od_ctx *ctx, const double *src, int32_t src_is_device);
 
 /* Asynchronous forms of od_write / od_read for pinned (page-locked) host
@@ -350,9 +363,13 @@ OD_API od_status od_debug_stall_tile(od_ctx *ctx, int64_t tile);
  * arithmetic mode m (see od_config.arith), b unused; op 17 / 18: the same
  * update in the tail form with one / two window adds (modes 9 and 10); op
  * 20+m (m = 0..4): the 2D update (((a0+a1)+a2)+a3)/4 of a[4i..4i+3] in mode m
- * (m = 4: three window adds); op 25 / 26: its tail form.  od_arith_host runs the routines on the host CPU
- * over host arrays; od_arith_device runs them in a kernel over device arrays
- * of the current device and synchronises.  n >= 0 elements. */
+ * (m = 4: three window adds); op 25 / 26: its tail form; op 30+f (f = 0..3)
+ * / 40+f (f = 0..2): the 3D / 2D update in the anchored window with its
+ * first f adds on the FP64 pipe, b[0] holding the anchor exponent E0 (an
+ * integer, clamped to [4, 2030]); op 34+f / 44+f: the anchored form alone,
+ * NaN where a cell leaves it.  od_arith_host runs the routines on the host
+ * CPU over host arrays; od_arith_device runs them in a kernel over device
+ * arrays of the current device and synchronises.  n >= 0 elements. */
 OD_API od_status od_arith_host(int32_t op, const double *a, const double *b, double *out, int64_t n);
 OD_API od_status od_arith_device(int32_t op, const double *a, const double *b, double *out, int64_t n);
 
@@ -468,7 +485,7 @@ typedef struct od_server_config {
                                     each job's shape (as od_config) and each
                                     step runs one batched launch per shape in
                                     use; stages 0 = 4 */
-    int32_t arith;               /* as od_config.arith (-1 = 10) */
+    int32_t arith;               /* as od_config.arith (-1 = 12) */
     void *pool;                  /* caller device memory of hbm_budget_bytes, 256-byte
                                     aligned, or NULL: the server allocates it once */
 } od_server_config;

@@ -549,7 +549,9 @@ std::string tune_key(const od_config *cfg, const od::Plan &p, int device) {
     mix(-1);
     for (auto v : p.ez) mix(v);
     char buf[256];
-    snprintf(buf, sizeof buf, "%s/%d/path%d/st%d/%lldx%lldx%lld/%016llx", name.c_str(), sms, cfg->path,
+    // "k2": the kernel generation (pulled 3D halos, anchored arithmetic); an
+    // entry timed on another generation's kernels is not reused
+    snprintf(buf, sizeof buf, "k2/%s/%d/path%d/st%d/%lldx%lldx%lld/%016llx", name.c_str(), sms, cfg->path,
              p.stencil, (long long)p.nx, (long long)p.ny, (long long)p.nz, (unsigned long long)h);
     return buf;
 }
@@ -594,10 +596,15 @@ od_status run_tuning(const od_config *cfg, TuneChoice *best) {
     if (tune_cache_lookup(key, best)) return OD_OK;
 
     const int shapes[6][2] = {{128, 4}, {128, 8}, {256, 4}, {256, 8}, {128, 2}, {256, 2}};
-    const int ariths[5] = {2, 7, 8, 10, 11};
+    // arithmetic modes worth timing: the anchored forms and the best earlier
+    // integer-window forms of each stencil
+    const int ariths3[5] = {12, 14, 15, 13, 10};
+    const int ariths2[5] = {12, 14, 13, 2, 15};
+    const int *ariths = base.stencil == OD_STENCIL_2D5 ? ariths2 : ariths3;
     std::vector<TuneChoice> round1;
     for (auto &sh : shapes)
-        for (int am : ariths) {
+        for (int k = 0; k < 5; ++k) {
+            const int am = ariths[k];
             TuneChoice c;
             c.threads = sh[0];
             c.cpt = sh[1];

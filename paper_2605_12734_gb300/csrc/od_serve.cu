@@ -408,7 +408,7 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
     s->threads = auto_shape ? 0 : cfg->threads ? cfg->threads : 128;
     s->cpt = auto_shape ? 0 : cfg->cells_per_thread ? cfg->cells_per_thread : 4;
     s->stages = cfg->stages ? cfg->stages : 4;
-    s->arith = cfg->arith >= 0 ? cfg->arith : 10;
+    s->arith = cfg->arith >= 0 ? cfg->arith : 12;
     s->max_jobs = cfg->max_jobs_per_launch > 0 ? cfg->max_jobs_per_launch : 256;
     s->t0 = Clock::now();
     auto bail = [&](od_status st, const std::string &m) {

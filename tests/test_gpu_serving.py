@@ -66,6 +66,33 @@ def test_jobs_in_the_mix_match_alone_and_oracle(od):
             assert same(results[jid], alone.read())
 
 
+def test_serving_stream_at_full_job_sizes(od):
+    # jobs from the serving workload's own ranges -- edges up to 384, ODF up
+    # to 216 with balanced splits that do not divide the edge (100 = 6 x 16 +
+    # 4, 203 = 3 x 67 + 2, 250 = 4 x 62 + 2), 10..200 iterations -- submitted
+    # while the others run; each result equals the job alone and the oracle
+    jobs = [(384, 6, 30, 61), (100, 6, 200, 62), (203, 3, 57, 63), (64, 2, 10, 64), (250, 4, 41, 65),
+            (384, 2, 12, 66), (77, 3, 133, 67), (128, 6, 88, 68)]
+    results = {}
+    with od.Server(120 << 30) as srv:
+        ids = []
+        for k, (e, p, it, seed) in enumerate(jobs):
+            ids.append(srv.submit(e, e, e, it, split=(p, p, p), seed=seed))
+            if k % 2 == 1:
+                time.sleep(0.005)
+        for jid in ids:
+            assert srv.wait(jid, 300.0) == od._native.OD_JOB_DONE, srv.info(jid)
+            results[jid] = srv.fetch(jid)
+            srv.release(jid)
+    threads = oracle.max_threads()
+    for jid, (e, p, it, seed) in zip(ids, jobs):
+        want = oracle.solve(e, e, e, seed, 1, it, threads=threads)
+        assert same(results[jid], want), (e, p, it)
+        with od.Jacobi3D(e, e, e, split=(p, p, p), seed=seed, init_mode=1, path="persistent") as alone:
+            alone.step(it)
+            assert same(results[jid], alone.read()), (e, p, it)
+
+
 def test_jobs_of_three_cta_shapes_in_one_step(od):
     # the planner gives these jobs 128 x 4, 256 x 4 and 128 x 2 CTAs; every
     # step runs one batched launch per shape, and each result is still the
