@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--jobs", type=int, default=300, help="serve: number of jobs")
     ap.add_argument("--rate", type=float, default=60.0, help="serve: Poisson arrival rate (jobs/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
+    ap.add_argument("--batch-steps", type=int, default=0,
+                    help="serve: steps of every running job per batched launch (0 = the server's default)")
     ap.add_argument("--odf", type=int, default=4096)
     ap.add_argument("--edge", type=int, default=512)
     ap.add_argument("--edge2d", type=int, default=32768, help="jacobi2d: grid edge (the paper's 32768)")
@@ -549,12 +551,15 @@ def run_ours(args):
         e2e = {"value": n * iters_job * reps * world / dt, "unit": UNIT,
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
                "iters_per_step": iters_job, "jobs": reps, "results_identical": same,
+               "job_intervals_ms": [round(float(g), 2) for g in gaps],
+               "iterations_ms": [round(a.elapsed_time(b), 2) for a, b in spans],
                "note": "e2e step = od_write_async(pinned host u^0) + od_step(100) + od_read_async(pinned host); "
                        "two contexts pipelined, so one job's host copies overlap the other's iterations"}
         e2e_flat = {"e2e_host_link_h2d_gbps": round(link[0], 1), "e2e_host_link_d2h_gbps": round(link[1], 1),
                     "e2e_iterations_ms_per_job": round(it_ms, 3), "e2e_wall_ms_per_job": round(dt / reps * 1e3, 3),
                     "e2e_job_interval_median_ms": round(float(np.median(gaps)), 3),
                     "e2e_job_interval_max_ms": round(float(np.max(gaps)), 3),
+                    "e2e_first_interval_ms": round(float(gaps[0]), 3),
                     "e2e_jobs_identical": same}
     solver.close()
 
@@ -783,7 +788,7 @@ def run_shards(args, pkg, torch, rank, dev):
     return 0
 
 
-def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, arith=-1):
+def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, arith=-1, batch_steps=0):
     """Poisson arrivals of independent jobs into one server: each a cubic
     grid with edge log-uniform in [64, 384], ODF in {8, 27, 64, 216} and
     10..200 iterations (seeded); returns aggregate updates/s and the job
@@ -791,7 +796,8 @@ def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, 
     from paper_2605_12734_gb300 import inputs
     jobs = inputs.serving_stream(n_jobs, rate, seed=6)
     budget = int(budget_gb * (1 << 30))
-    srv = pkg.Server(budget, device=dev, threads=threads, cells_per_thread=cpt, stages=stages, arith=arith)
+    srv = pkg.Server(budget, device=dev, threads=threads, cells_per_thread=cpt, stages=stages, arith=arith,
+                     batch_steps=batch_steps)
     # warm-up: one small job through the whole path
     w = srv.submit(64, 64, 64, 3, split=(2, 2, 2), seed=1)
     srv.wait(w, 60.0)
@@ -838,14 +844,16 @@ def run_serve(args, pkg, torch, rank, world, dev):
     aggregate updates/s and p50/p99 job latency (completion - arrival)."""
     clocks = ClockSampler(dev)
     clocks.start()
-    r = serve_stream(pkg, dev, args.jobs, args.rate, args.budget_gb, args.threads, args.cpt, args.stages, args.arith)
+    r = serve_stream(pkg, dev, args.jobs, args.rate, args.budget_gb, args.threads, args.cpt, args.stages, args.arith,
+                     args.batch_steps)
     clk = clocks.stop()
     line = {"metric": METRIC, "value": r["updates_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.jobs,
             "warmup": 1, "ms_per_step": r["wall_s"] * 1e3 / args.jobs, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "jacobi3d-serving-poisson", "jobs": args.jobs, "rate_per_s": args.rate,
                        "edge": "log-uniform [64,384]", "odf": "{8,27,64,216}", "iters": "U[10,200]",
-                       "budget_gb": args.budget_gb, "seed": 6, "note": "a step here is one job"},
+                       "budget_gb": args.budget_gb, "seed": 6, "batch_steps": args.batch_steps,
+                       "note": "a step here is one job"},
             "latency_p50_s": r["p50_s"], "latency_p99_s": r["p99_s"], "latency_mean_s": r["mean_s"],
             "latency_max_s": r["max_s"], "wall_s": r["wall_s"], "launches": r["launches"],
             "pool_peak_gb": r["pool_peak_gb"], "offered_updates_per_s": r["offered_updates_per_s"],

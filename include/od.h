@@ -459,9 +459,9 @@ OD_API od_status od_bench_launch_rate(int32_t device, int32_t host_threads, int3
  *
  * A server admits independent solves as they arrive, keeps their state
  * resident in one device pool of hbm_budget_bytes and advances every running
- * job by one iteration per launch of a batched fused kernel (continuous
- * batching: jobs that arrive while others run join the next launch, finished
- * jobs drop out).  Admission is first come, first served, while a slot is free
+ * job by batch_steps iterations per batched launch (continuous batching:
+ * jobs that arrive while others run join the next launch, finished jobs drop
+ * out).  Admission is first come, first served, while a slot is free
  * (max_active, 0 = no limit) and the pool has room for the job's arena.  A
  * worker thread inside the server drives the device; every call below is
  * thread-safe.  Each job's result is bit-identical to the same job solved
@@ -488,6 +488,11 @@ typedef struct od_server_config {
     int32_t arith;               /* as od_config.arith (-1 = 12) */
     void *pool;                  /* caller device memory of hbm_budget_bytes, 256-byte
                                     aligned, or NULL: the server allocates it once */
+    int32_t batch_steps;         /* steps of every running job that one launch advances
+                                    (0 = 8): a persistent launch per CTA shape takes
+                                    (step, job, tile) tickets, so no step ends in a
+                                    partial wave; jobs admitted meanwhile join the next
+                                    launch.  1: one fused step per launch */
 } od_server_config;
 
 typedef struct od_job_info {

@@ -346,8 +346,9 @@ bool tile_shape_supported(int threads, int cpt, int amode, int stencil) {
 // (227 KB per CTA less the kernel's static shared memory) and never lowered:
 // the launch's own size decides occupancy, the cap only permits it.
 cudaError_t prepare_tile_kernels(int threads, int cpt, int amode, int smem_bytes, int stencil) {
-    void *fns[4] = {tile_kernel(stencil, amode, threads, cpt, 0), tile_kernel(stencil, amode, threads, cpt, 1),
-                    tile_kernel(stencil, amode, threads, cpt, 2), tile_kernel(stencil, amode, threads, cpt, 3)};
+    void *fns[5] = {tile_kernel(stencil, amode, threads, cpt, 0), tile_kernel(stencil, amode, threads, cpt, 1),
+                    tile_kernel(stencil, amode, threads, cpt, 2), tile_kernel(stencil, amode, threads, cpt, 3),
+                    tile_kernel(stencil, amode, threads, cpt, 4)};
     for (void *f : fns) {
         if (!f) return cudaErrorInvalidValue;
         cudaFuncAttributes fa;
@@ -388,6 +389,23 @@ cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t 
     if (grid <= 0 || njobs <= 0) return cudaSuccess;
     void *args[] = {(void *)&jobs, (void *)&first, (void *)&njobs};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, (size_t)smem_bytes, s);
+}
+
+cudaError_t launch_persistent_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int32_t steps,
+                                    int32_t *queue, int grid, int threads, int cpt, int amode, int smem_bytes,
+                                    int stencil, cudaStream_t s) {
+    void *f = tile_kernel(stencil, amode, threads, cpt, 4);
+    if (!f) return cudaErrorInvalidValue;
+    if (grid <= 0 || njobs <= 0 || steps <= 0) return cudaSuccess;
+    void *args[] = {(void *)&jobs, (void *)&first, (void *)&njobs, (void *)&steps, (void *)&queue};
+    return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, (size_t)smem_bytes, s);
+}
+
+cudaError_t persistent_multi_occupancy(int threads, int cpt, int amode, int smem_bytes, int stencil,
+                                       int *blocks_per_sm) {
+    void *f = tile_kernel(stencil, amode, threads, cpt, 4);
+    if (!f) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, (size_t)smem_bytes);
 }
 
 cudaError_t persistent_occupancy(int threads, int cpt, int amode, int smem_bytes, int stencil,

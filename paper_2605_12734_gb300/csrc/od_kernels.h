@@ -27,11 +27,21 @@ cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, int amo
 cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int grid, int threads,
                                int cpt, int amode, int smem_bytes, int stencil, cudaStream_t s);
 
+// Several fused steps of several jobs in one persistent launch: jobs[j]
+// (device array) carries job j's tables, its absolute first step (t0) and
+// its steps in this launch (iters <= steps); first[] as for
+// launch_tiles_multi; queue a zeroed device counter.
+cudaError_t launch_persistent_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int32_t steps,
+                                    int32_t *queue, int grid, int threads, int cpt, int amode, int smem_bytes,
+                                    int stencil, cudaStream_t s);
+
 // Persistent ticket kernel over a.iters steps.
 cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, int amode, int smem_bytes,
                               cudaStream_t s);
 cudaError_t persistent_occupancy(int threads, int cpt, int amode, int smem_bytes, int stencil,
                                  int *blocks_per_sm);
+cudaError_t persistent_multi_occupancy(int threads, int cpt, int amode, int smem_bytes, int stencil,
+                                       int *blocks_per_sm);
 
 // The initial field of a shard at offset (gx0, gy0, gz0) of a global grid
 // gnx x gny x gnz (the whole grid: offsets 0, global = local extents).

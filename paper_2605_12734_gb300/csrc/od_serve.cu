@@ -6,10 +6,13 @@
 //   1. admits queued jobs in arrival order while a slot is free and the
 //      budget pool (one device allocation, first-fit) has room for the job's
 //      arena -- a job larger than the whole budget is refused at submit;
-//   2. launches ONE fused step for every running job (k_tiles_multi: each
-//      block runs one tile of one job, each job at its own step and parity),
-//      so jobs that arrive while others run join the very next launch and a
-//      finished job simply drops out of the next one;
+//   2. launches batch_steps fused steps of every running job in one
+//      persistent launch per CTA shape (k_persistent_multi: CTAs take (step,
+//      job, tile) tickets and wait, bounded, on the per-tile step counters of
+//      the tiles they read, each job at its own step and parity), or, with
+//      batch_steps = 1, one fused step (k_tiles_multi: each block one tile of
+//      one job); jobs that arrive while others run join the very next launch
+//      and a finished job simply drops out of the next one;
 //   3. watches the events of launches in flight (at most two ahead) and marks
 //      a job done when the launch holding its last step has completed.
 // A job's result stays on the device until the client fetches and releases
@@ -124,6 +127,8 @@ struct od_server {
     int32_t *d_first[2] = {nullptr, nullptr};
     int32_t max_jobs = 0;
     int threads = 128, cpt = 4, stages = 4, arith = 2, smem_cap = 0;
+    int batch_steps = 8, num_sms = 0;
+    int32_t *d_queue = nullptr;  // ticket counters: [in-flight slot][shape group]
     std::vector<cudaEvent_t> free_events;
     std::deque<Batch> inflight;
     int64_t next_batch = 0;
@@ -294,6 +299,8 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
             a.tile_begin = 0;
             a.parity = (int32_t)(j->steps_enq & 1);
             a.stages = s->stages;
+            a.t0 = (int32_t)j->steps_enq;  // persistent batches: absolute first step, steps in the batch
+            a.iters = (int32_t)std::min<int64_t>(s->batch_steps, j->iters - j->steps_enq);
             if (in.size() == first) jo.push_back((int32_t)first);
             hk.push_back(a);
             hf.push_back(tiles);
@@ -316,21 +323,39 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
     cudaMemcpyAsync(s->d_first[slot], hf.data(), hf.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s->compute);
     cudaEvent_t ev0 = take_event(s);
     cudaEventRecord(ev0, s->compute);
+    int32_t steps = 1;  // steps of the batch: the most any of its jobs runs
+    for (const KArgs &a : hk) steps = std::max(steps, a.iters);
     for (int g = 0; g < ngroups; ++g) {
         const int smem = 256 + s->stages * max_sd[(size_t)g] * 8;
-        cudaError_t e = od::launch_tiles_multi(s->d_jobs[slot] + jo[(size_t)g], s->d_first[slot] + jo[(size_t)g] + g,
-                                               jo[(size_t)g + 1] - jo[(size_t)g], grid[(size_t)g], shapes[g][0],
-                                               shapes[g][1], s->arith, smem, OD_STENCIL_3D7, s->compute);
+        const KArgs *dj = s->d_jobs[slot] + jo[(size_t)g];
+        const int32_t *df = s->d_first[slot] + jo[(size_t)g] + g;
+        const int32_t nj = jo[(size_t)g + 1] - jo[(size_t)g];
+        cudaError_t e;
+        if (s->batch_steps > 1) {
+            int bps = 0;
+            e = od::persistent_multi_occupancy(shapes[g][0], shapes[g][1], s->arith, smem, OD_STENCIL_3D7, &bps);
+            int32_t *q = s->d_queue + slot * kShapes + g;
+            if (e == cudaSuccess && bps < 1) e = cudaErrorInvalidConfiguration;
+            if (e == cudaSuccess) e = cudaMemsetAsync(q, 0, sizeof(int32_t), s->compute);
+            if (e == cudaSuccess)
+                e = od::launch_persistent_multi(dj, df, nj, steps, q,
+                                                std::min(grid[(size_t)g], bps * s->num_sms), shapes[g][0],
+                                                shapes[g][1], s->arith, smem, OD_STENCIL_3D7, s->compute);
+        } else {
+            e = od::launch_tiles_multi(dj, df, nj, grid[(size_t)g], shapes[g][0], shapes[g][1], s->arith, smem,
+                                       OD_STENCIL_3D7, s->compute);
+        }
         if (e != cudaSuccess) {
             s->free_events.push_back(ev0);
-            s->worker_error = std::string("k_tiles_multi: ") + cudaGetErrorString(e);
+            s->worker_error = std::string("batched launch: ") + cudaGetErrorString(e);
             return false;
         }
         s->launches++;
     }
     const int64_t idx = s->next_batch++;
-    for (Job *j : in) {
-        j->steps_enq++;
+    for (size_t k = 0; k < in.size(); ++k) {
+        Job *j = in[k];
+        j->steps_enq += s->batch_steps > 1 ? hk[k].iters : 1;
         if (j->steps_enq == j->iters) j->done_batch = idx;
     }
     cudaEvent_t ev = take_event(s);
@@ -410,6 +435,11 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
     s->stages = cfg->stages ? cfg->stages : 4;
     s->arith = cfg->arith >= 0 ? cfg->arith : 12;
     s->max_jobs = cfg->max_jobs_per_launch > 0 ? cfg->max_jobs_per_launch : 256;
+    s->batch_steps = cfg->batch_steps > 0 ? cfg->batch_steps : 8;
+    if (cfg->batch_steps < 0 || cfg->batch_steps > 4096) {
+        delete s;
+        return fail(OD_EINVAL, "batch_steps must be in [0, 4096]");
+    }
     s->t0 = Clock::now();
     auto bail = [&](od_status st, const std::string &m) {
         od_server_destroy(s);
@@ -440,6 +470,10 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
         if (cudaMalloc(&s->d_jobs[k], (size_t)s->max_jobs * sizeof(KArgs)) != cudaSuccess ||
             cudaMalloc(&s->d_first[k], (size_t)(s->max_jobs + kShapes) * sizeof(int32_t)) != cudaSuccess)
             return bail(OD_ENOMEM, "cannot allocate launch tables");
+    if (cudaMalloc(&s->d_queue, 2 * kShapes * sizeof(int32_t)) != cudaSuccess)
+        return bail(OD_ENOMEM, "cannot allocate ticket counters");
+    if (cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess)
+        return bail(OD_ECUDA, "cannot query the SM count");
     s->smem_cap = 200 * 1024;
     for (int g = 0; g < kShapes; ++g) {
         if (s->threads && g > 0) break;  // one fixed shape
@@ -618,6 +652,7 @@ od_status od_server_destroy(od_server *s) {
         if (s->d_jobs[k]) cudaFree(s->d_jobs[k]);
         if (s->d_first[k]) cudaFree(s->d_first[k]);
     }
+    if (s->d_queue) cudaFree(s->d_queue);
     if (s->compute) cudaStreamDestroy(s->compute);
     if (s->admit) cudaStreamDestroy(s->admit);
     if (s->own_pool && s->pool_base) cudaFree(s->pool_base);

@@ -136,6 +136,12 @@ static __device__ __noinline__ double update_slow(double W, double E, double S, 
     return jacobi_update_ieee<false>(W, E, S, N, D, U);
 }
 
+// Which thread refills a ring slot: lane 0 of a different warp each plane
+// (1) or thread 0 always (0); a build may choose (-DOD_ROTATE_ISSUE=0).
+#ifndef OD_ROTATE_ISSUE
+#define OD_ROTATE_ISSUE 1
+#endif
+
 struct Ring {
     double *base;      // first slot
     uint64_t *bars;    // one mbarrier per slot
@@ -351,9 +357,13 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     }
 
     // x-halo patches of a plane (fused only): item t < 2*nj is row t % nj of
-    // face t / nj; ring-slot offset of its ghost cell and the neighbour cell
-    // it copies
+    // face t / nj, handled by thread t (the first warps: spreading the items
+    // over every warp measured slower, each warp then running the patch
+    // code for a few lanes); ring-slot offset of its ghost cell and the
+    // neighbour cell it copies
+    constexpr int kWarps = NT / 32;
     const int npatch = FUSED ? 2 * nj : 0;
+    const int pt = tid;
     auto patch_src = [&](int t, int p) -> const double * {
         const bool hi = t >= nj;
         const int j = hi ? t - nj : t;
@@ -374,7 +384,7 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     if (!fail) fail = !mbar_wait_bounded(ring.bars + slot(kb + 1), phase(kb + 1), a.spin_ns);
     if (FUSED && !fail) {  // the first computed plane's x halo
         double *sl = ring.base + (size_t)slot(kb + 1) * SD;
-        for (int t = tid; t < npatch; t += NT) {
+        for (int t = pt; t < npatch; t += NT) {
             const double *g = patch_src(t, kb + 1);
             if (g) sl[patch_dst(t)] = *g;
         }
@@ -393,8 +403,8 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
         const bool patch_next = FUSED && k + 1 < ke;
         double xv = 0.0;
         const double *xg = nullptr;
-        if (patch_next && tid < npatch) {
-            xg = patch_src(tid, k + 1);
+        if (patch_next && pt < npatch) {
+            xg = patch_src(pt, k + 1);
             if (xg) xv = *xg;
         }
         fail = !mbar_wait_bounded(ring.bars + sl_p1, ph_p1, a.spin_ns);
@@ -421,8 +431,8 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
                 }
             }
             if (patch_next) {  // plane k+1's x halo (its slot is only read at interior cells above)
-                if (xg) su[patch_dst(tid)] = xv;
-                for (int t = tid + NT; t < npatch; t += NT) {  // tiles of more than NT/2 rows
+                if (xg) su[patch_dst(pt)] = xv;
+                for (int t = pt + NT; t < npatch; t += NT) {  // tiles of more than NT/2 rows
                     const double *g = patch_src(t, k + 1);
                     if (g) su[patch_dst(t)] = *g;
                 }
@@ -434,9 +444,10 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
             return false;
         }
         // plane k-1 is no longer needed: refill its slot (after the barrier,
-        // and after a proxy fence when the slot took generic stores of a halo)
+        // and after a proxy fence when the slot took generic stores of a
+        // halo), from lane 0 of a different warp each plane
         if (k - 1 + S <= ke) {
-            if (tid == 0) {
+            if (tid == (OD_ROTATE_ISSUE ? (k % kWarps) << 5 : 0)) {
                 if (FUSED) fence_proxy_async_smem();
                 issue(k - 1 + S, sl_m1);
             }
@@ -620,8 +631,8 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
             drain(k + 1);
             return false;
         }
-        if (k - 1 + S <= ke) {
-            if (tid == 0) issue(k - 1 + S, sl_m1);
+        if (k - 1 + S <= ke) {  // refilled from lane 0 of a different warp each plane
+            if (tid == (OD_ROTATE_ISSUE ? (k % (NT / 32)) << 5 : 0)) issue(k - 1 + S, sl_m1);
             issued_hi = k - 1 + S;
         }
         sl_m1 = sl_0;
@@ -778,6 +789,85 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_persistent(const KAr
     }
 }
 
+// Continuous batching over several steps: the persistent form of
+// k_tiles_multi.  jobs[j] holds job j's tables, the absolute step t0 at which
+// it enters this launch and the steps it runs in it (iters <= S); job j owns
+// the tile positions [first[j], first[j+1]) of the launch (first[njobs] =
+// total).  Ticket r*total + pos is step t0+r of tile pos - first[j] of job j,
+// and a ticket with r >= jobs[j].iters does nothing.  A tile publishes the
+// absolute number of steps it has finished, in the job's own step counters
+// (zero when the job was created, never reset), so before step t0+r a tile
+// waits until every tile it reads has finished t0+r steps.  As in
+// k_persistent, a waited-on ticket is always smaller than the waiter's, so
+// the waits cannot form a cycle.  Every job of a launch shares its CTA
+// shape, ring depth and slot size; queue is the launch's ticket counter
+// (zeroed before the launch).
+template <int NT, int CPT, int AM, int ST>
+__global__ void __launch_bounds__(NT, min_blocks(NT, ST))
+    k_persistent_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int32_t S, int32_t *queue) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int32_t s_ticket, s_job;
+    if (blockDim.x != NT) {
+        if (threadIdx.x == 0) record_err(jobs[0].err, OD_ERR_BAD_LAUNCH, -1, -1);
+        return;
+    }
+    Ring ring = ring_setup<NT>(jobs[0], smem);
+    const int32_t total = first[njobs];
+    const int64_t tickets = (int64_t)S * total;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int32_t tk = atomicAdd(queue, 1);
+            s_ticket = tk;
+            if ((int64_t)tk < tickets) {  // the job owning tile position tk % total
+                const int32_t pos = tk % total;
+                int lo = 0, hi = njobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (first[mid] <= pos) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_job = lo;
+            }
+        }
+        __syncthreads();
+        const int32_t tk = s_ticket;
+        if ((int64_t)tk >= tickets) break;
+        const int job = s_job;
+        const int r = tk / total, tile = tk - r * total - first[job];
+        const KArgs &a = jobs[job];
+        if (r >= a.iters) {  // this job runs fewer steps in the launch
+            __syncthreads();   // every thread has read the ticket before thread 0 takes the next
+            continue;
+        }
+        const int step = a.t0 + r;
+        const Arith ar = arith_setup<AM>(a);
+        int ok = 1;
+        if (threadIdx.x == 0) {
+            const int q1 = a.dep_ptr[tile + 1];
+            for (int q = a.dep_ptr[tile]; q < q1 && ok; ++q) {
+                const int32_t *e = a.epoch + a.dep_idx[q];
+                if (ld_acquire(e) >= step) continue;
+                const uint64_t t0 = now_ns();
+                while (ld_acquire(e) < step) {
+                    if (ld_relaxed(&a.err->code) != 0) { ok = 0; break; }
+                    if (now_ns() - t0 > a.spin_ns) {
+                        record_err(a.err, OD_ERR_DEP_TIMEOUT, tile, step);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            fence_proxy_async();
+        }
+        if (!__syncthreads_and(ok)) break;
+        if (!run_any_tile<NT, CPT, true, AM, ST>(a, tile, step & 1, ring, smem + kSmemPush, step, ar)) break;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(a.epoch + tile, step + 1);
+        }
+    }
+}
 
 }  // namespace tile
 }  // namespace od

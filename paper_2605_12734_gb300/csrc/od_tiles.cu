@@ -21,8 +21,8 @@
 
 namespace od {
 
-// kind 0: k_tiles without push, 1: k_tiles with push, 2: k_persistent,
-// 3: k_tiles_multi
+// kind 0: k_tiles (per-chare compute), 1: k_tiles (fused step), 2:
+// k_persistent, 3: k_tiles_multi, 4: k_persistent_multi
 void *OD_TILE_FN(int threads, int cpt, int kind) {
     using namespace tile;
 #define OD_CASE(NT_, C_)                                                          \
@@ -30,6 +30,7 @@ void *OD_TILE_FN(int threads, int cpt, int kind) {
         if (kind == 0) return (void *)k_tiles<NT_, C_, false, OD_AMODE, OD_STENCIL>; \
         if (kind == 1) return (void *)k_tiles<NT_, C_, true, OD_AMODE, OD_STENCIL>;  \
         if (kind == 3) return (void *)k_tiles_multi<NT_, C_, OD_AMODE, OD_STENCIL>;  \
+        if (kind == 4) return (void *)k_persistent_multi<NT_, C_, OD_AMODE, OD_STENCIL>; \
         return (void *)k_persistent<NT_, C_, OD_AMODE, OD_STENCIL>;                  \
     }
     OD_CASE(128, 2) OD_CASE(128, 4) OD_CASE(128, 8)

@@ -41,9 +41,12 @@ JOBS = [  # (edge, split, iters, seed, init_mode)
 ]
 
 
-def test_jobs_in_the_mix_match_alone_and_oracle(od):
+@pytest.mark.parametrize("batch_steps", [0, 1, 3])
+def test_jobs_in_the_mix_match_alone_and_oracle(od, batch_steps):
+    # 0: the default persistent batches of 8 steps; 1: one fused step per
+    # launch; 3: batches that end inside most jobs' step counts
     results = {}
-    with od.Server(256 << 20, max_active=4) as srv:
+    with od.Server(256 << 20, max_active=4, batch_steps=batch_steps) as srv:
         ids = []
         for k, (e, sp, it, seed, mode) in enumerate(JOBS):
             ids.append(srv.submit(e, e, e, it, split=sp, seed=seed, init_mode=mode))
@@ -57,7 +60,9 @@ def test_jobs_in_the_mix_match_alone_and_oracle(od):
             srv.release(jid)
         st = srv.stats()
         assert st["done"] == len(JOBS) and st["failed"] == 0
-        assert st["pool_used"] == 0 and st["launches"] >= max(j[2] for j in JOBS)
+        assert st["pool_used"] == 0
+        if batch_steps == 1:
+            assert st["launches"] >= max(j[2] for j in JOBS)
     for jid, (e, sp, it, seed, mode) in zip(ids, JOBS):
         want = oracle.solve(e, e, e, seed, mode, it)
         assert same(results[jid], want), (e, sp, it)
@@ -93,15 +98,16 @@ def test_serving_stream_at_full_job_sizes(od):
             assert same(results[jid], alone.read()), (e, p, it)
 
 
-def test_jobs_of_three_cta_shapes_in_one_step(od):
+@pytest.mark.parametrize("batch_steps", [0, 1])
+def test_jobs_of_three_cta_shapes_in_one_step(od, batch_steps):
     # the planner gives these jobs 128 x 4, 256 x 4 and 128 x 2 CTAs; every
-    # step runs one batched launch per shape, and each result is still the
-    # oracle's
+    # batch (8 steps, or 1) runs one batched launch per shape, and each result
+    # is still the oracle's
     jobs = [((240, 240, 240), (2, 2, 2), 6, 21), ((600, 20, 16), (2, 1, 1), 9, 22), ((40, 40, 40), (2, 2, 2), 7, 23),
             ((600, 20, 16), (2, 1, 1), 4, 24)]
     for dims, sp, _, _ in jobs[:3]:
         assert od.plan(*dims, split=sp)["threads"] * od.plan(*dims, split=sp)["cells_per_thread"] in (256, 512, 1024)
-    with od.Server(1 << 30) as srv:
+    with od.Server(1 << 30, batch_steps=batch_steps) as srv:
         ids = [srv.submit(*dims, it, split=sp, seed=seed) for dims, sp, it, seed in jobs]
         got = []
         for jid in ids:
@@ -109,7 +115,9 @@ def test_jobs_of_three_cta_shapes_in_one_step(od):
             got.append(srv.fetch(jid))
             srv.release(jid)
         st = srv.stats()
-    assert st["launches"] > max(j[2] for j in jobs)  # more than one launch per step while shapes overlap
+    # more than one launch per batch while shapes overlap
+    steps = 1 if batch_steps == 1 else 8
+    assert st["launches"] > -(-max(j[2] for j in jobs) // steps)
     for res, (dims, sp, it, seed) in zip(got, jobs):
         assert same(res, oracle.solve(*dims, seed, 1, it)), dims
 
