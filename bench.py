@@ -177,7 +177,7 @@ def profiled_kernel(args, plan):
 
 # bumped whenever a tile kernel changes, so stale profiler counters are not reused
 KERNEL_REV = 13     # 3D 7-point
-KERNEL_REV_2D = 13  # 2D 5-point
+KERNEL_REV_2D = 14  # 2D 5-point
 
 
 def combine_ranks(ms: float, updates: float, world: int, device: str):
