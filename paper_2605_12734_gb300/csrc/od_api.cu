@@ -995,23 +995,22 @@ od_status od_step(od_ctx *c, int32_t iters) {
     if (c->failed) return fail(OD_ESTATE, "context failed earlier; destroy it");
     if (iters == 0) return OD_OK;
     DeviceGuard dg(c->device);
-    const bool fused3d = c->plan.stencil == OD_STENCIL_3D7;
     switch (c->path) {
         case OD_PATH_FUSED:
         case OD_PATH_FUSED_GRAPH:
         case OD_PATH_PERSISTENT: {
-            // the fused 3D sweep reads the neighbours' faces and leaves the
-            // ghost layers behind; the 2D sweep keeps them current
+            // the fused sweeps read the neighbours' faces and leave the
+            // ghost layers behind
             od_status s = c->path == OD_PATH_FUSED         ? enqueue_fused(c, iters)
                           : c->path == OD_PATH_FUSED_GRAPH ? enqueue_fused_graph(c, iters)
                                                            : enqueue_persistent(c, iters);
-            if (fused3d) c->ghosts_current = false;
+            c->ghosts_current = false;
             return s;
         }
         case OD_PATH_PER_CHARE:
         case OD_PATH_GRAPH: {
             // the per-chare flow reads its own ghost layers: refresh them
-            // once after fused 3D steps (its own steps keep them current)
+            // once after fused steps (its own steps keep them current)
             if (!c->ghosts_current) {
                 OD_CUDA(od::launch_ghost_refresh(c->d_ch, (int)c->plan.ch.size(), (int)(c->steps & 1), c->stream));
                 c->launches++;

@@ -22,15 +22,14 @@
 // row0 = 1 in 3D; rows = 1, row0 = 0 in 2D.
 //
 // On the per-chare path a neighbour delivers a face into these ghost cells
-// (pack, copy, unpack: the chare's mailbox).  The fused 3D tile sweep instead
-// reads a face straight from the neighbour's own array -- its boundary
+// (pack, copy, unpack: the chare's mailbox).  The fused tile sweeps instead
+// read a face straight from the neighbour's own array -- its boundary
 // planes and rows by bulk copies into the tile's ring slots, its boundary
 // column by plain loads -- so an internal ghost layer of a chare is only
 // current after a per-chare step, od_create or od_write (the context tracks
-// this and refreshes the ghosts before a per-chare step needs them).  The
-// fused 2D sweep stores each boundary value into the neighbour's ghost
-// cells.  Faces on the domain boundary hold the Dirichlet shell in both
-// parities and are never written after initialisation.
+// this and refreshes the ghosts before a per-chare step needs them).  Faces
+// on the domain boundary hold the Dirichlet shell in both parities and are
+// never written after initialisation.
 #pragma once
 #include <stdint.h>
 

@@ -382,22 +382,22 @@ cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, in
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, (size_t)smem_bytes, s);
 }
 
-cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int grid, int threads,
-                               int cpt, int amode, int smem_bytes, int stencil, cudaStream_t s) {
+cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, const KArgs &geom, int grid,
+                               int threads, int cpt, int amode, int smem_bytes, int stencil, cudaStream_t s) {
     void *f = tile_kernel(stencil, amode, threads, cpt, 3);
     if (!f) return cudaErrorInvalidValue;
     if (grid <= 0 || njobs <= 0) return cudaSuccess;
-    void *args[] = {(void *)&jobs, (void *)&first, (void *)&njobs};
+    void *args[] = {(void *)&jobs, (void *)&first, (void *)&njobs, (void *)&geom};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, (size_t)smem_bytes, s);
 }
 
 cudaError_t launch_persistent_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int32_t steps,
-                                    int32_t *queue, int grid, int threads, int cpt, int amode, int smem_bytes,
-                                    int stencil, cudaStream_t s) {
+                                    int32_t *queue, const KArgs &geom, int grid, int threads, int cpt, int amode,
+                                    int smem_bytes, int stencil, cudaStream_t s) {
     void *f = tile_kernel(stencil, amode, threads, cpt, 4);
     if (!f) return cudaErrorInvalidValue;
     if (grid <= 0 || njobs <= 0 || steps <= 0) return cudaSuccess;
-    void *args[] = {(void *)&jobs, (void *)&first, (void *)&njobs, (void *)&steps, (void *)&queue};
+    void *args[] = {(void *)&jobs, (void *)&first, (void *)&njobs, (void *)&steps, (void *)&queue, (void *)&geom};
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, (size_t)smem_bytes, s);
 }
 

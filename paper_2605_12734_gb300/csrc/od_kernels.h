@@ -23,17 +23,19 @@ cudaError_t launch_tiles(const KArgs &a, int grid, int threads, int cpt, int amo
 
 // One fused step of several jobs (continuous batching): jobs[j] (device
 // array) is job j's KArgs with its source parity, first[j] its first block
-// (device array of njobs+1 prefix sums, first[njobs] = grid).
-cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int grid, int threads,
-                               int cpt, int amode, int smem_bytes, int stencil, cudaStream_t s);
+// (device array of njobs+1 prefix sums, first[njobs] = grid); geom (host)
+// carries the launch's ring geometry and wait limit: stages, stage_doubles
+// (at least every job's) and spin_ns.
+cudaError_t launch_tiles_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, const KArgs &geom, int grid,
+                               int threads, int cpt, int amode, int smem_bytes, int stencil, cudaStream_t s);
 
 // Several fused steps of several jobs in one persistent launch: jobs[j]
 // (device array) carries job j's tables, its absolute first step (t0) and
 // its steps in this launch (iters <= steps); first[] as for
 // launch_tiles_multi; queue a zeroed device counter.
 cudaError_t launch_persistent_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int32_t steps,
-                                    int32_t *queue, int grid, int threads, int cpt, int amode, int smem_bytes,
-                                    int stencil, cudaStream_t s);
+                                    int32_t *queue, const KArgs &geom, int grid, int threads, int cpt, int amode,
+                                    int smem_bytes, int stencil, cudaStream_t s);
 
 // Persistent ticket kernel over a.iters steps.
 cudaError_t launch_persistent(const KArgs &a, int grid, int threads, int cpt, int amode, int smem_bytes,

@@ -104,7 +104,9 @@ int32_t stage_doubles_for(int32_t nj, int32_t pitch) {
     return round_up((nj + 2) * pitch, 16);     // keep slots 128-byte aligned
 }
 
-od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
+od_status build_plan(const od_config *cfg, Plan *P, std::string *err) { return build_plan(cfg, P, err, true); }
+
+od_status build_plan(const od_config *cfg, Plan *P, std::string *err, bool fill_gpu) {
     Plan &p = *P;
     p = Plan();
     if (!cfg) { *err = "null config"; return OD_EINVAL; }
@@ -260,7 +262,8 @@ od_status build_plan(const od_config *cfg, Plan *P, std::string *err) {
                         tiles += (double)slabs * chunks;
                     }
             const double resident = 0.5 * 152.0 * (1280 / shapes[i][0]);
-            const double score = used / cells * (1.0 - 0.2 / (rows / used)) * std::min(1.0, tiles / resident);
+            const double score = used / cells * (1.0 - 0.2 / (rows / used)) *
+                                 (fill_gpu ? std::min(1.0, tiles / resident) : 1.0);
             if (i == 0) base = score;
             if (score > best) {
                 best = score;

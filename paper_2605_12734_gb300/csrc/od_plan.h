@@ -54,6 +54,10 @@ struct Plan {
 
 // Build the full plan; returns OD_OK or OD_EINVAL with *err set.
 od_status build_plan(const od_config *cfg, Plan *plan, std::string *err);
+// The same, choosing the default CTA shape by the lanes its tiles use alone
+// when fill_gpu is false (a batch of many jobs fills the GPU, so a job's own
+// tile count does not count against a shape), as the serving loop does.
+od_status build_plan(const od_config *cfg, Plan *plan, std::string *err, bool fill_gpu);
 
 // Ring-slot size for a tile of `nj` rows in a chare of row pitch `pitch`
 // (the rows plus the two y-halo rows), in doubles.

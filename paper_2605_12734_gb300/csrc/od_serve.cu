@@ -106,6 +106,7 @@ struct Job {
     od_ctx *ctx = nullptr;
     int64_t done_batch = -1;    // launch index holding the job's last step
     int64_t cells = 0;
+    int32_t threads = 0, cpt = 0;  // the job's CTA shape (from its plan)
     std::string err;
 };
 
@@ -168,8 +169,8 @@ od_config job_config(od_server *s, Job *j) {
     }
     c.path = OD_PATH_FUSED;
     c.autotune = 0;
-    c.threads = s->threads;
-    c.cells_per_thread = s->cpt;
+    c.threads = s->threads ? s->threads : j->threads;
+    c.cells_per_thread = s->threads ? s->cpt : j->cpt;
     c.stages = s->stages;
     c.arith = s->arith;
     c.stream_pool = 1;
@@ -330,6 +331,11 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
         const KArgs *dj = s->d_jobs[slot] + jo[(size_t)g];
         const int32_t *df = s->d_first[slot] + jo[(size_t)g] + g;
         const int32_t nj = jo[(size_t)g + 1] - jo[(size_t)g];
+        KArgs geom;  // the launch's ring geometry: every job's slots fit the largest
+        memset(&geom, 0, sizeof geom);
+        geom.stages = s->stages;
+        geom.stage_doubles = max_sd[(size_t)g];
+        geom.spin_ns = hk[(size_t)jo[(size_t)g]].spin_ns;
         cudaError_t e;
         if (s->batch_steps > 1) {
             int bps = 0;
@@ -338,11 +344,11 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
             if (e == cudaSuccess && bps < 1) e = cudaErrorInvalidConfiguration;
             if (e == cudaSuccess) e = cudaMemsetAsync(q, 0, sizeof(int32_t), s->compute);
             if (e == cudaSuccess)
-                e = od::launch_persistent_multi(dj, df, nj, steps, q,
+                e = od::launch_persistent_multi(dj, df, nj, steps, q, geom,
                                                 std::min(grid[(size_t)g], bps * s->num_sms), shapes[g][0],
                                                 shapes[g][1], s->arith, smem, OD_STENCIL_3D7, s->compute);
         } else {
-            e = od::launch_tiles_multi(dj, df, nj, grid[(size_t)g], shapes[g][0], shapes[g][1], s->arith, smem,
+            e = od::launch_tiles_multi(dj, df, nj, geom, grid[(size_t)g], shapes[g][0], shapes[g][1], s->arith, smem,
                                        OD_STENCIL_3D7, s->compute);
         }
         if (e != cudaSuccess) {
@@ -501,11 +507,17 @@ od_status od_server_submit(od_server *s, const od_config *job, int32_t iters, ui
     od::Plan plan;
     std::string err;
     od_config c = job_config(s, j);
-    od_status st = od::build_plan(&c, &plan, &err);
+    // per-job shapes: chosen by the lanes the job's tiles use -- the batch
+    // fills the GPU, so a small job's own tile count does not count against
+    // a shape (measured with 24 jobs of 160^3 in 27 chares batched: 128 x 4
+    // 127, 128 x 2 110 G updates/s)
+    od_status st = od::build_plan(&c, &plan, &err, false);
     if (st != OD_OK) {
         delete j;
         return fail(st, err);
     }
+    j->threads = plan.threads;
+    j->cpt = plan.cpt;
     j->bytes = plan.arena_bytes;
     j->cells = plan.cells;
     if (j->bytes > s->pool.size()) {

@@ -177,25 +177,10 @@ struct PullInfo {
     int32_t xlo_pitch, xlo_plane, xhi_pitch, xhi_plane, ylo_plane, yhi_plane;
 };
 
-// Where a 2D fused tile's boundary values go (the neighbours' ghost cells of
-// the destination parity): x-: xlo + (row+1)*xlo_plane, x+: likewise; z-/z+:
-// the neighbour's ghost row, zlo + r / zhi + r.
-struct PushInfo {
-    double *xlo, *xhi, *ylo, *yhi, *zlo, *zhi;
-    int32_t xlo_pitch, xlo_plane, xhi_pitch, xhi_plane, ylo_plane, yhi_plane;
-};
-
 constexpr int kSmemBars = 0;     // up to 8 mbarriers
-constexpr int kSmemPush = 64;    // PullInfo (3D) / PushInfo (2D)
+constexpr int kSmemPush = 64;    // PullInfo
 constexpr int kSmemRing = 256;   // first ring slot (matches the planner's header)
-static_assert(sizeof(PushInfo) <= kSmemRing - kSmemPush, "push info overflows the header");
 static_assert(sizeof(PullInfo) <= kSmemRing - kSmemPush, "pull info overflows the header");
-
-// Per-cell word of the 2D sweep: bits 0-15 ring-slot offset r of the cell,
-// 27 the slot holds a real cell, 28/29 the cell lies on a face with an x-/x+
-// neighbour.
-constexpr uint32_t kValid = 1u << 27;
-constexpr uint32_t kXlo = 1u << 28, kXhi = 1u << 29;
 
 // The 3D update of one cell in arithmetic mode AM (see od_config.arith);
 // ok = false sends the cell to update_slow.  m is the cell's slot in its
@@ -230,8 +215,10 @@ __device__ __forceinline__ double update_cell(const double *sd, const double *sc
 }
 
 // Sweep one tile from parity sp into parity sp^1.  Returns false (all
-// threads agree) if a wait ran out; the error is recorded and thread 0 has
-// waited, bounded, for the copies this tile still had in flight.
+// threads agree) if a wait ran out, after thread 0 has waited, bounded, for
+// the copies this tile still had in flight; the caller records the error
+// (keeping the error record out of the sweep keeps the job's arguments out
+// of its registers).
 //
 // FUSED = false (the per-chare path): the chare's own ghost layers are
 // current (unpacked), and the tile reads them with its rows.  FUSED = true
@@ -245,7 +232,7 @@ __device__ __forceinline__ double update_cell(const double *sd, const double *sc
 // the chare's own interior, so the cell loop has no face branches.
 template <int NT, int CPT, bool FUSED, int AM>
 __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ring &ring, PullInfo *pi, int step,
-                                         const Arith &ar) {
+                                         const Arith &ar, const KArgs &g) {
     const TileDev T = a.tiles[tile_id];
     const ChareDev &C = a.ch[T.c];
     const int bx = C.bx, by = C.by, bz = C.bz, pitch = C.pitch;
@@ -257,7 +244,7 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     double *__restrict__ dst = C.A[dp] + (size_t)j0 * pitch;
     const uint32_t row_bytes = (uint32_t)pitch * 8u;
     const uint32_t run_bytes = (uint32_t)(nj + 2) * row_bytes;  // one plane's rows
-    const int S = a.stages, SD = a.stage_doubles;
+    const int S = g.stages, SD = g.stage_doubles;
     const int kb = T.k0 - 1, ke = T.k0 + T.nk;  // planes kb..ke are loaded
     const int tid = threadIdx.x;
     const uint32_t seq0 = ring.seq;
@@ -298,45 +285,37 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
     // (a ring of S slots holds planes k-1, k, k+1 and S-3 planes in flight)
     auto drain = [&](int from) {
         if (tid == 0)
-            for (int p = from; p <= issued_hi; ++p) mbar_wait_bounded(ring.bars + slot(p), phase(p), a.spin_ns);
+            for (int p = from; p <= issued_hi; ++p) mbar_wait_bounded(ring.bars + slot(p), phase(p), g.spin_ns);
         ring.seq = seq0 + (uint32_t)(issued_hi - kb + 1);
     };
 
-    if (tid == 0) {
-        if (FUSED) {
-            PullInfo q;
-            q.xlo = q.xhi = q.ylo = q.yhi = q.zlo = q.zhi = nullptr;
-            q.xlo_pitch = q.xlo_plane = q.xhi_pitch = q.xhi_plane = q.ylo_plane = q.yhi_plane = 0;
-            if (C.nbr[OD_FACE_XLO] >= 0) {  // its column bx_n
-                const ChareDev &N = a.ch[C.nbr[OD_FACE_XLO]];
-                q.xlo_pitch = N.pitch;
-                q.xlo_plane = (N.by + 2) * N.pitch;
-                q.xlo = N.A[sp] + N.bx;
-            }
-            if (C.nbr[OD_FACE_XHI] >= 0) {  // its column 1
-                const ChareDev &N = a.ch[C.nbr[OD_FACE_XHI]];
-                q.xhi_pitch = N.pitch;
-                q.xhi_plane = (N.by + 2) * N.pitch;
-                q.xhi = N.A[sp] + 1;
-            }
-            if (j0 == 0 && C.nbr[OD_FACE_YLO] >= 0) {  // its row by_n
-                const ChareDev &N = a.ch[C.nbr[OD_FACE_YLO]];
-                q.ylo_plane = (N.by + 2) * pitch;
-                q.ylo = N.A[sp] + (size_t)N.by * pitch;
-            }
-            if (j0 + nj == by && C.nbr[OD_FACE_YHI] >= 0) {  // its row 1
-                const ChareDev &N = a.ch[C.nbr[OD_FACE_YHI]];
-                q.yhi_plane = (N.by + 2) * pitch;
-                q.yhi = N.A[sp] + pitch;
-            }
-            if (kb < 0 && C.nbr[OD_FACE_ZLO] >= 0) {  // its plane bz_n, the tile's rows
-                const ChareDev &N = a.ch[C.nbr[OD_FACE_ZLO]];
-                q.zlo = N.A[sp] + (size_t)N.bz * plane + (size_t)j0 * pitch;
-            }
-            if (ke >= bz && C.nbr[OD_FACE_ZHI] >= 0)  // its plane 1
-                q.zhi = a.ch[C.nbr[OD_FACE_ZHI]].A[sp] + plane + (size_t)j0 * pitch;
-            *pi = q;
+    if (FUSED && tid < 6) {  // the pull info: one face per thread, their table reads in parallel
+        const int f = tid, n = C.nbr[f];
+        const ChareDev *N = n >= 0 ? &a.ch[n] : nullptr;
+        if (f == OD_FACE_XLO) {  // its column bx_n
+            pi->xlo = N ? N->A[sp] + N->bx : nullptr;
+            pi->xlo_pitch = N ? N->pitch : 0;
+            pi->xlo_plane = N ? (N->by + 2) * N->pitch : 0;
+        } else if (f == OD_FACE_XHI) {  // its column 1
+            pi->xhi = N ? N->A[sp] + 1 : nullptr;
+            pi->xhi_pitch = N ? N->pitch : 0;
+            pi->xhi_plane = N ? (N->by + 2) * N->pitch : 0;
+        } else if (f == OD_FACE_YLO) {  // its row by_n, when the tile's first halo row is the ghost row
+            const bool on = N && j0 == 0;
+            pi->ylo = on ? N->A[sp] + (size_t)N->by * pitch : nullptr;
+            pi->ylo_plane = on ? (N->by + 2) * pitch : 0;
+        } else if (f == OD_FACE_YHI) {  // its row 1
+            const bool on = N && j0 + nj == by;
+            pi->yhi = on ? N->A[sp] + pitch : nullptr;
+            pi->yhi_plane = on ? (N->by + 2) * pitch : 0;
+        } else if (f == OD_FACE_ZLO) {  // its plane bz_n, the tile's rows
+            pi->zlo = N && kb < 0 ? N->A[sp] + (size_t)N->bz * plane + (size_t)j0 * pitch : nullptr;
+        } else {  // its plane 1
+            pi->zhi = N && ke >= bz ? N->A[sp] + plane + (size_t)j0 * pitch : nullptr;
         }
+    }
+    if (FUSED) __syncthreads();  // the pull info
+    if (tid == 0) {
         const int last = min(ke, kb + S - 1);
         for (int p = kb; p <= last; ++p) issue(p, slot(p));
     }
@@ -379,9 +358,8 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
 
     // Planes k-1, k and k+1 must be resident while plane k is computed, so a
     // slot is refilled once the plane after next has been computed.
-    if (FUSED) __syncthreads();  // the pull info
-    bool fail = !mbar_wait_bounded(ring.bars + slot(kb), phase(kb), a.spin_ns);
-    if (!fail) fail = !mbar_wait_bounded(ring.bars + slot(kb + 1), phase(kb + 1), a.spin_ns);
+    bool fail = !mbar_wait_bounded(ring.bars + slot(kb), phase(kb), g.spin_ns);
+    if (!fail) fail = !mbar_wait_bounded(ring.bars + slot(kb + 1), phase(kb + 1), g.spin_ns);
     if (FUSED && !fail) {  // the first computed plane's x halo
         double *sl = ring.base + (size_t)slot(kb + 1) * SD;
         for (int t = pt; t < npatch; t += NT) {
@@ -390,7 +368,6 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
         }
     }
     if (__syncthreads_or(fail)) {
-        if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
         drain(kb);
         return false;
     }
@@ -407,7 +384,7 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
             xg = patch_src(pt, k + 1);
             if (xg) xv = *xg;
         }
-        fail = !mbar_wait_bounded(ring.bars + sl_p1, ph_p1, a.spin_ns);
+        fail = !mbar_wait_bounded(ring.bars + sl_p1, ph_p1, g.spin_ns);
         if (!fail) {
             const double *sd = ring.base + (size_t)sl_m1 * SD;
             const double *sc = ring.base + (size_t)sl_0 * SD;
@@ -439,7 +416,6 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
             }
         }
         if (__syncthreads_or(fail)) {
-            if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
             drain(k + 1);
             return false;
         }
@@ -504,18 +480,24 @@ __device__ __forceinline__ double update_cell_2d(double W, double E, double S, d
     }
 }
 
-template <int NT, int CPT, bool PUSH, int AM>
-__device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp, Ring &ring, PushInfo *pi,
-                                            int step, const Arith &ar) {
+// FUSED = true (the fused and persistent paths): the faces of neighbour
+// chares are read from their arrays in the source parity, as in run_tile --
+// a z-ghost row (the row above or below the chare) by the plane's bulk copy
+// from the neighbour's boundary row, an x-ghost cell of a computed row by a
+// plain load one row ahead -- and nothing is stored outside the chare.
+template <int NT, int CPT, bool FUSED, int AM>
+__device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp, Ring &ring, PullInfo *pi,
+                                            int step, const Arith &ar, const KArgs &g) {
     const TileDev T = a.tiles[tile_id];
     const ChareDev &C = a.ch[T.c];
     const int bx = C.bx, bz = C.bz, pitch = C.pitch;
     const int plane = pitch;
     const int dp = sp ^ 1;
-    const double *__restrict__ src = C.A[sp] + T.i0;  // column i0 of the lower ghost row
-    double *__restrict__ dst = C.A[dp] + T.i0;
-    const uint32_t run_bytes = (uint32_t)((T.ni + 3) & ~1) * 8u;
-    const int S = a.stages, SD = a.stage_doubles;
+    const int i0 = T.i0, ni = T.ni;
+    const double *__restrict__ src = C.A[sp] + i0;  // column i0 of the lower ghost row
+    double *__restrict__ dst = C.A[dp] + i0;
+    const uint32_t run_bytes = (uint32_t)((ni + 3) & ~1) * 8u;
+    const int S = g.stages, SD = g.stage_doubles;
     const int kb = T.k0 - 1, ke = T.k0 + T.nk;
     const int tid = threadIdx.x;
     const uint32_t seq0 = ring.seq;
@@ -525,114 +507,107 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
     auto issue = [&](int p, uint32_t s) {  // s = slot(p)
         uint64_t *bar = ring.bars + s;
         mbar_expect_tx(bar, run_bytes);
-        bulk_g2s(ring.base + (size_t)s * SD, src + (size_t)(p + 1) * plane, run_bytes, bar);
+        const double *from = src + (size_t)(p + 1) * plane;
+        if (FUSED && p < 0 && pi->zlo) from = pi->zlo;        // the z- neighbour's top row
+        if (FUSED && p >= bz && pi->zhi) from = pi->zhi;      // the z+ neighbour's bottom row
+        bulk_g2s(ring.base + (size_t)s * SD, from, run_bytes, bar);
     };
     int issued_hi = kb - 1;
     auto drain = [&](int from) {
         if (tid == 0)
-            for (int p = from; p <= issued_hi; ++p) mbar_wait_bounded(ring.bars + slot(p), phase(p), a.spin_ns);
+            for (int p = from; p <= issued_hi; ++p) mbar_wait_bounded(ring.bars + slot(p), phase(p), g.spin_ns);
         ring.seq = seq0 + (uint32_t)(issued_hi - kb + 1);
     };
 
+    if (FUSED && tid < 4) {  // the pull info, one face per thread (2D faces: x-, x+, z-, z+)
+        const int f = tid < 2 ? tid : tid + 2, n = C.nbr[f];
+        const ChareDev *N = n >= 0 ? &a.ch[n] : nullptr;
+        if (f == OD_FACE_XLO) {  // its column bx_n, when the segment starts at the chare's edge
+            pi->xlo = N && i0 == 0 ? N->A[sp] + N->bx : nullptr;
+            pi->xlo_plane = N ? N->pitch : 0;
+        } else if (f == OD_FACE_XHI) {  // its column 1
+            pi->xhi = N && i0 + ni == bx ? N->A[sp] + 1 : nullptr;
+            pi->xhi_plane = N ? N->pitch : 0;
+        } else if (f == OD_FACE_ZLO) {  // its row bz_n (same x extent, same pitch)
+            pi->zlo = N && kb < 0 ? N->A[sp] + (size_t)N->bz * plane + i0 : nullptr;
+        } else {  // its row 1
+            pi->zhi = N && ke >= bz ? N->A[sp] + plane + i0 : nullptr;
+        }
+    }
+    if (FUSED) __syncthreads();  // the pull info
     if (tid == 0) {
         const int last = min(ke, kb + S - 1);
         for (int p = kb; p <= last; ++p) issue(p, slot(p));
-        if (PUSH) {
-            PushInfo q;
-            q.xlo = q.xhi = q.ylo = q.yhi = q.zlo = q.zhi = nullptr;
-            q.xlo_pitch = q.xlo_plane = q.xhi_pitch = q.xhi_plane = q.ylo_plane = q.yhi_plane = 0;
-            if (C.nbr[OD_FACE_XLO] >= 0) {  // column 0 -> its ghost column bx_n+1
-                const ChareDev &N = a.ch[C.nbr[OD_FACE_XLO]];
-                q.xlo_plane = N.pitch;
-                q.xlo = N.A[dp] + (N.bx + 1);
-            }
-            if (C.nbr[OD_FACE_XHI] >= 0) {  // column bx-1 -> its ghost column 0
-                const ChareDev &N = a.ch[C.nbr[OD_FACE_XHI]];
-                q.xhi_plane = N.pitch;
-                q.xhi = N.A[dp];
-            }
-            if (C.nbr[OD_FACE_ZLO] >= 0) {  // row 0 -> its ghost row bz_n+1 (same bx, same pitch)
-                const ChareDev &N = a.ch[C.nbr[OD_FACE_ZLO]];
-                q.zlo = N.A[dp] + (size_t)(N.bz + 1) * plane + T.i0;
-            }
-            if (C.nbr[OD_FACE_ZHI] >= 0) q.zhi = a.ch[C.nbr[OD_FACE_ZHI]].A[dp] + T.i0;
-            *pi = q;
-        }
     }
     issued_hi = min(ke, kb + S - 1);
 
-    // this thread's cells q = tid + m*NT of the segment; a slot past its end
-    // repeats cell 0 (same value, same place, no flags)
-    uint32_t rf[CPT];
+    // this thread's cells q = tid + m*NT of the segment, as ring-slot offsets;
+    // a slot past its end repeats cell 0 (same value, same place)
+    int rf[CPT];
 #pragma unroll
     for (int m = 0; m < CPT; ++m) {
         const int q0 = tid + m * NT;
-        const bool valid = q0 < T.ni;
-        const int q = valid ? q0 : 0;
-        uint32_t w = (uint32_t)(q + 1);
-        if (valid) {
-            w |= kValid;
-            if (PUSH) {
-                if (T.i0 + q == 0 && C.nbr[OD_FACE_XLO] >= 0) w |= kXlo;
-                if (T.i0 + q == bx - 1 && C.nbr[OD_FACE_XHI] >= 0) w |= kXhi;
-            }
-        }
-        rf[m] = w;
+        rf[m] = (q0 < ni ? q0 : 0) + 1;
     }
+    // x-halo patches (fused only): thread 0 the x- ghost (slot offset 0),
+    // thread 1 the x+ ghost (offset ni + 1) of a computed row
+    auto patch_src = [&](int p) -> const double * {
+        if (!FUSED || tid > 1) return nullptr;
+        const double *base = tid ? pi->xhi : pi->xlo;
+        return base ? base + (size_t)(p + 1) * (tid ? pi->xhi_plane : pi->xlo_plane) : nullptr;
+    };
+    const int patch_dst = tid ? ni + 1 : 0;
 
-    bool fail = !mbar_wait_bounded(ring.bars + slot(kb), phase(kb), a.spin_ns);
-    if (!fail) fail = !mbar_wait_bounded(ring.bars + slot(kb + 1), phase(kb + 1), a.spin_ns);
+    bool fail = !mbar_wait_bounded(ring.bars + slot(kb), phase(kb), g.spin_ns);
+    if (!fail) fail = !mbar_wait_bounded(ring.bars + slot(kb + 1), phase(kb + 1), g.spin_ns);
+    if (FUSED && !fail) {  // the first computed row's x halo
+        const double *g = patch_src(kb + 1);
+        if (g) ring.base[(size_t)slot(kb + 1) * SD + patch_dst] = *g;
+    }
     if (__syncthreads_or(fail)) {
-        if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
         drain(kb);
         return false;
     }
 
-    auto compute_plane = [&](auto zp_tag, int k, double *zp, const double *sd, const double *sc,
-                             const double *su) {
-        constexpr bool ZP = decltype(zp_tag)::value;
-        double *dpl = dst + (size_t)(k + 1) * plane;
-        // no validity branch: a slot past the segment's end repeats its cell
-        // 0, so it stores the same value to the same place
-        auto store = [&](uint32_t w, int r, double v) {
-            dpl[r] = v;
-            if (PUSH) {
-                if (w & kXlo) pi->xlo[(size_t)(k + 1) * pi->xlo_plane] = v;
-                if (w & kXhi) pi->xhi[(size_t)(k + 1) * pi->xhi_plane] = v;
-                if (ZP) zp[r] = v;
-            }
-        };
-#pragma unroll
-        for (int m = 0; m < CPT; ++m) {
-            const uint32_t w = rf[m];
-            const int r = (int)(w & 0xFFFFu);
-            bool ok;
-            double v = update_cell_2d<AM>(sc[r - 1], sc[r + 1], sd[r], su[r], m, ar, ok);
-            if (!ok) v = update2d_slow(sc[r - 1], sc[r + 1], sd[r], su[r]);
-            store(w, r, v);
-        }
-    };
-
     uint32_t sl_m1 = slot(kb), sl_0 = slot(kb + 1), sl_p1 = slot(kb + 2), ph_p1 = phase(kb + 2);
     for (int k = T.k0; k < ke; ++k) {
-        fail = !mbar_wait_bounded(ring.bars + sl_p1, ph_p1, a.spin_ns);
+        // the next row's x halo, loaded while this row is computed
+        const double *xg = FUSED && k + 1 < ke ? patch_src(k + 1) : nullptr;
+        const double xv = xg ? *xg : 0.0;
+        fail = !mbar_wait_bounded(ring.bars + sl_p1, ph_p1, g.spin_ns);
         if (!fail) {
             const double *sd = ring.base + (size_t)sl_m1 * SD;
             const double *sc = ring.base + (size_t)sl_0 * SD;
-            const double *su = ring.base + (size_t)sl_p1 * SD;
-            double *z0 = (PUSH && k == 0) ? pi->zlo : nullptr;
-            double *z1 = (PUSH && k == bz - 1) ? pi->zhi : nullptr;
-            if (z0) compute_plane(std::true_type(), k, z0, sd, sc, su);
-            if (z1) compute_plane(std::true_type(), k, z1, sd, sc, su);
-            if (!z0 && !z1) compute_plane(std::false_type(), k, nullptr, sd, sc, su);
+            double *su = ring.base + (size_t)sl_p1 * SD;
+            double *dpl = dst + (size_t)(k + 1) * plane;
+            // no validity branch: a slot past the segment's end repeats its
+            // cell 0, so it stores the same value to the same place
+            uint32_t bad = 0;  // bit m: cell m left the integer routines' domain
+#pragma unroll
+            for (int m = 0; m < CPT; ++m) {
+                const int r = rf[m];
+                bool ok;
+                dpl[r] = update_cell_2d<AM>(sc[r - 1], sc[r + 1], sd[r], su[r], m, ar, ok);
+                bad |= (ok ? 0u : 1u) << m;
+            }
+            if (bad) {  // rare: recompute those cells with IEEE operations and store them again
+#pragma unroll
+                for (int m = 0; m < CPT; ++m) {
+                    const int r = rf[m];
+                    if (bad & (1u << m)) dpl[r] = update2d_slow(sc[r - 1], sc[r + 1], sd[r], su[r]);
+                }
+            }
+            if (xg) su[patch_dst] = xv;  // row k+1's x halo (its slot is only read at the cells above)
         }
         if (__syncthreads_or(fail)) {
-            if (tid == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile_id, step);
             drain(k + 1);
             return false;
         }
         if (k - 1 + S <= ke) {  // refilled from lane 0 of a different warp each plane
-            if (tid == (OD_ROTATE_ISSUE ? (k % (NT / 32)) << 5 : 0)) issue(k - 1 + S, sl_m1);
+            if (tid == (OD_ROTATE_ISSUE ? (k % (NT / 32)) << 5 : 0)) {
+                if (FUSED) fence_proxy_async_smem();  // after the halo's generic stores
+                issue(k - 1 + S, sl_m1);
+            }
             issued_hi = k - 1 + S;
         }
         sl_m1 = sl_0;
@@ -643,29 +618,34 @@ __device__ __forceinline__ bool run_tile_2d(const KArgs &a, int tile_id, int sp,
         }
     }
     ring.seq = seq0 + (uint32_t)(ke - kb + 1);
+    if (FUSED && tid == 0) fence_proxy_async_smem();  // before the next tile's copies into these slots
     return true;
 }
 
 // Stencil dispatch at compile time: ST = OD_STENCIL_3D7 or OD_STENCIL_2D5.
-// FUSED: the fused and persistent paths' tile (3D: halos pulled from the
-// neighbours; 2D: boundary values pushed into theirs).
+// FUSED: the fused and persistent paths' tile (halos read from the
+// neighbours).  g carries the launch's ring geometry and wait limit
+// (stages, stage_doubles, spin_ns): a kernel parameter, which the sweep
+// reads from the constant bank instead of holding it in registers -- the
+// tile's own arguments a may live in global memory (batched launches).
 template <int NT, int CPT, bool FUSED, int AM, int ST>
 __device__ __forceinline__ bool run_any_tile(const KArgs &a, int tile_id, int sp, Ring &ring, unsigned char *info,
-                                             int step, const Arith &ar) {
+                                             int step, const Arith &ar, const KArgs &g) {
     if constexpr (ST == OD_STENCIL_2D5)
-        return run_tile_2d<NT, CPT, FUSED, AM>(a, tile_id, sp, ring, reinterpret_cast<PushInfo *>(info), step, ar);
+        return run_tile_2d<NT, CPT, FUSED, AM>(a, tile_id, sp, ring, reinterpret_cast<PullInfo *>(info), step, ar,
+                                               g);
     else
-        return run_tile<NT, CPT, FUSED, AM>(a, tile_id, sp, ring, reinterpret_cast<PullInfo *>(info), step, ar);
+        return run_tile<NT, CPT, FUSED, AM>(a, tile_id, sp, ring, reinterpret_cast<PullInfo *>(info), step, ar, g);
 }
 
 template <int NT>
-__device__ __forceinline__ Ring ring_setup(const KArgs &a, unsigned char *smem) {
+__device__ __forceinline__ Ring ring_setup(const KArgs &g, unsigned char *smem) {
     Ring r;
     r.bars = reinterpret_cast<uint64_t *>(smem + kSmemBars);
     r.base = reinterpret_cast<double *>(smem + kSmemRing);
     r.seq = 0;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < a.stages; ++s) mbar_init(r.bars + s, 1);
+        for (int s = 0; s < g.stages; ++s) mbar_init(r.bars + s, 1);
         mbar_init_fence();
     }
     __syncthreads();
@@ -697,16 +677,20 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_tiles(const KArgs a)
     }
     const Arith ar = arith_setup<AM>(a);
     Ring ring = ring_setup<NT>(a, smem);
-    run_any_tile<NT, CPT, FUSED, AM, ST>(a, a.tile_begin + (int)blockIdx.x, a.parity, ring, smem + kSmemPush, -1, ar);
+    const int tile = a.tile_begin + (int)blockIdx.x;
+    if (!run_any_tile<NT, CPT, FUSED, AM, ST>(a, tile, a.parity, ring, smem + kSmemPush, -1, ar, a) &&
+        threadIdx.x == 0)
+        record_err(a.err, OD_ERR_TMA_TIMEOUT, tile, -1);
 }
 
 // Continuous batching: one fused step of several independent jobs in one
 // launch.  jobs[j] holds job j's tables and source parity; job j owns blocks
 // [first[j], first[j+1]); every block runs one tile of its job.  All jobs
-// share the launch's CTA shape, ring depth and slot size.
+// share the launch's CTA shape and ring geometry (geom: stages,
+// stage_doubles -- the largest slot of the launch's jobs -- and spin_ns).
 template <int NT, int CPT, int AM, int ST>
 __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_tiles_multi(const KArgs *jobs, const int32_t *first,
-                                                                   int32_t njobs) {
+                                                                   int32_t njobs, const KArgs geom) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int32_t s_job;
     if (threadIdx.x == 0) {
@@ -725,9 +709,36 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_tiles_multi(const KA
         return;
     }
     const Arith ar = arith_setup<AM>(a);
-    Ring ring = ring_setup<NT>(a, smem);
-    run_any_tile<NT, CPT, true, AM, ST>(a, (int)blockIdx.x - first[s_job], a.parity, ring, smem + kSmemPush, -1,
-                                        ar);
+    Ring ring = ring_setup<NT>(geom, smem);
+    const int tile = (int)blockIdx.x - first[s_job];
+    if (!run_any_tile<NT, CPT, true, AM, ST>(a, tile, a.parity, ring, smem + kSmemPush, -1, ar, geom) &&
+        threadIdx.x == 0)
+        record_err(a.err, OD_ERR_TMA_TIMEOUT, tile, -1);
+}
+
+// Wait, bounded, until every tile in `tile`'s dependency list has finished
+// `need` steps; each thread watches its own share of the list, so the waits
+// (and their load latencies) overlap.  Returns this thread's verdict (all
+// threads must then agree through a barrier); a wait that runs out records
+// the error.
+__device__ __forceinline__ int wait_deps(const KArgs &a, int tile, int32_t need, int step) {
+    int ok = 1;
+    const int q1 = a.dep_ptr[tile + 1];
+    for (int q = a.dep_ptr[tile] + (int)threadIdx.x; q < q1 && ok; q += (int)blockDim.x) {
+        const int32_t *e = a.epoch + a.dep_idx[q];
+        if (ld_acquire(e) >= need) continue;
+        const uint64_t t0 = now_ns();
+        while (ld_acquire(e) < need) {
+            if (ld_relaxed(&a.err->code) != 0) { ok = 0; break; }
+            if (now_ns() - t0 > a.spin_ns) {
+                record_err(a.err, OD_ERR_DEP_TIMEOUT, tile, step);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    return ok;
 }
 
 // Persistent kernel: CTAs take tickets in step-major order; ticket
@@ -747,11 +758,18 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_persistent(const KAr
     const Arith ar = arith_setup<AM>(a);
     Ring ring = ring_setup<NT>(a, smem);
     const int64_t total = (int64_t)a.iters * a.ntiles;
+    // thread 0 holds the next ticket, taken one tile ahead so the atomic's
+    // latency passes under the current tile (a CTA then holds two tickets;
+    // the smallest unfinished ticket is still always being run, so the waits
+    // cannot deadlock)
+    int32_t next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(a.queue, 1);
     for (;;) {
         if (threadIdx.x == 0) {
-            int32_t tk = atomicAdd(a.queue, 1);
+            int32_t tk = next;
             if (ld_relaxed(&a.err->code) != 0) tk = INT32_MAX;
             s_ticket = tk;
+            if ((int64_t)tk < total) next = atomicAdd(a.queue, 1);
         }
         __syncthreads();
         const int32_t tk = s_ticket;
@@ -759,29 +777,15 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_persistent(const KAr
         const int r = tk / a.ntiles, pos = tk - r * a.ntiles;
         const int step = a.t0 + r;
         const int tile = (a.order_mode == 1 && (r & 1)) ? a.order[a.ntiles - 1 - pos] : a.order[pos];
-        int ok = 1;
-        if (threadIdx.x == 0) {
-            const int q1 = a.dep_ptr[tile + 1];
-            for (int q = a.dep_ptr[tile]; q < q1 && ok; ++q) {
-                const int32_t *e = a.epoch + a.dep_idx[q];
-                if (ld_acquire(e) >= r) continue;
-                const uint64_t t0 = now_ns();
-                while (ld_acquire(e) < r) {
-                    if (ld_relaxed(&a.err->code) != 0) { ok = 0; break; }
-                    if (now_ns() - t0 > a.spin_ns) {
-                        record_err(a.err, OD_ERR_DEP_TIMEOUT, tile, step);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            // data written by other CTAs (generic proxy) is next read by bulk
-            // copies (async proxy)
-            fence_proxy_async();
-        }
+        const int ok = wait_deps(a, tile, r, step);
         if (!__syncthreads_and(ok)) break;
-        if (!run_any_tile<NT, CPT, true, AM, ST>(a, tile, step & 1, ring, smem + kSmemPush, step, ar)) break;
+        // data written by other CTAs (generic proxy) is next read by bulk
+        // copies (async proxy)
+        if (threadIdx.x == 0) fence_proxy_async();
+        if (!run_any_tile<NT, CPT, true, AM, ST>(a, tile, step & 1, ring, smem + kSmemPush, step, ar, a)) {
+            if (threadIdx.x == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile, step);
+            break;
+        }
         if (threadIdx.x == 0 && (int64_t)tile != a.stall_tile) {
             __threadfence();
             st_release(a.epoch + tile, r + 1);
@@ -800,33 +804,40 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST)) k_persistent(const KAr
 // waits until every tile it reads has finished t0+r steps.  As in
 // k_persistent, a waited-on ticket is always smaller than the waiter's, so
 // the waits cannot form a cycle.  Every job of a launch shares its CTA
-// shape, ring depth and slot size; queue is the launch's ticket counter
-// (zeroed before the launch).
+// shape and ring geometry (geom, as for k_tiles_multi); queue is the
+// launch's ticket counter (zeroed before the launch).
 template <int NT, int CPT, int AM, int ST>
 __global__ void __launch_bounds__(NT, min_blocks(NT, ST))
-    k_persistent_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int32_t S, int32_t *queue) {
+    k_persistent_multi(const KArgs *jobs, const int32_t *first, int32_t njobs, int32_t S, int32_t *queue,
+                       const KArgs geom) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int32_t s_ticket, s_job;
     if (blockDim.x != NT) {
         if (threadIdx.x == 0) record_err(jobs[0].err, OD_ERR_BAD_LAUNCH, -1, -1);
         return;
     }
-    Ring ring = ring_setup<NT>(jobs[0], smem);
+    Ring ring = ring_setup<NT>(geom, smem);
     const int32_t total = first[njobs];
     const int64_t tickets = (int64_t)S * total;
+    // the job owning tile position pos: the last one whose first position <= pos
+    auto job_of = [&](int32_t pos) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first[mid] <= pos) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    // thread 0 takes the next ticket one tile ahead (see k_persistent)
+    int32_t next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(queue, 1);
     for (;;) {
         if (threadIdx.x == 0) {
-            const int32_t tk = atomicAdd(queue, 1);
-            s_ticket = tk;
-            if ((int64_t)tk < tickets) {  // the job owning tile position tk % total
-                const int32_t pos = tk % total;
-                int lo = 0, hi = njobs - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (first[mid] <= pos) lo = mid;
-                    else hi = mid - 1;
-                }
-                s_job = lo;
+            s_ticket = next;
+            if ((int64_t)next < tickets) {
+                s_job = job_of(next % total);
+                next = atomicAdd(queue, 1);
             }
         }
         __syncthreads();
@@ -841,27 +852,13 @@ __global__ void __launch_bounds__(NT, min_blocks(NT, ST))
         }
         const int step = a.t0 + r;
         const Arith ar = arith_setup<AM>(a);
-        int ok = 1;
-        if (threadIdx.x == 0) {
-            const int q1 = a.dep_ptr[tile + 1];
-            for (int q = a.dep_ptr[tile]; q < q1 && ok; ++q) {
-                const int32_t *e = a.epoch + a.dep_idx[q];
-                if (ld_acquire(e) >= step) continue;
-                const uint64_t t0 = now_ns();
-                while (ld_acquire(e) < step) {
-                    if (ld_relaxed(&a.err->code) != 0) { ok = 0; break; }
-                    if (now_ns() - t0 > a.spin_ns) {
-                        record_err(a.err, OD_ERR_DEP_TIMEOUT, tile, step);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            fence_proxy_async();
-        }
+        const int ok = wait_deps(a, tile, step, step);
         if (!__syncthreads_and(ok)) break;
-        if (!run_any_tile<NT, CPT, true, AM, ST>(a, tile, step & 1, ring, smem + kSmemPush, step, ar)) break;
+        if (threadIdx.x == 0) fence_proxy_async();
+        if (!run_any_tile<NT, CPT, true, AM, ST>(a, tile, step & 1, ring, smem + kSmemPush, step, ar, geom)) {
+            if (threadIdx.x == 0) record_err(a.err, OD_ERR_TMA_TIMEOUT, tile, step);
+            break;
+        }
         if (threadIdx.x == 0) {
             __threadfence();
             st_release(a.epoch + tile, step + 1);
