@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serve: HBM budget")
     ap.add_argument("--batch-steps", type=int, default=0,
                     help="serve: steps of every running job per batched launch (0 = the server's default)")
+    ap.add_argument("--job-streams", type=int, default=-1,
+                    help="serve: 0 = batched launches, N > 0 = one persistent launch per job on N streams "
+                         "(-1 = the default)")
     ap.add_argument("--odf", type=int, default=4096)
     ap.add_argument("--edge", type=int, default=512)
     ap.add_argument("--edge2d", type=int, default=32768, help="jacobi2d: grid edge (the paper's 32768)")
@@ -176,8 +179,8 @@ def profiled_kernel(args, plan):
 
 
 # bumped whenever a tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 13     # 3D 7-point
-KERNEL_REV_2D = 14  # 2D 5-point
+KERNEL_REV = 14     # 3D 7-point
+KERNEL_REV_2D = 15  # 2D 5-point
 
 
 def combine_ranks(ms: float, updates: float, world: int, device: str):
@@ -626,8 +629,9 @@ def run_ours(args):
             legs[f"{key}_ms_per_step"] = ms_w
             legs[f"{key}_hbm_frac"] = info["bytes_per_step"] / (ms_w * 1e-3) / 1e9 / hbm_peak
             legs[f"{key}_arith"] = info["arith"]
-        r = serve_stream(pkg, dev, 150, 120.0, args.budget_gb)
-        legs.update({"serve_p50_ms": r["p50_s"] * 1e3, "serve_p99_ms": r["p99_s"] * 1e3,
+        r = serve_stream(pkg, dev, 150, 120.0, args.budget_gb, job_streams=serve_job_streams(args))
+        legs.update({"serve_job_streams": serve_job_streams(args),
+                     "serve_p50_ms": r["p50_s"] * 1e3, "serve_p99_ms": r["p99_s"] * 1e3,
                      "serve_updates_per_s": r["updates_per_s"], "serve_rate_per_s": r["rate_per_s"],
                      "serve_jobs": r["jobs"], "serve_device_busy_frac": r["device_busy_frac"],
                      "serve_offered_updates_per_s": r["offered_updates_per_s"]})
@@ -788,7 +792,8 @@ def run_shards(args, pkg, torch, rank, dev):
     return 0
 
 
-def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, arith=-1, batch_steps=0):
+def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, arith=-1, batch_steps=0,
+                 job_streams=0):
     """Poisson arrivals of independent jobs into one server: each a cubic
     grid with edge log-uniform in [64, 384], ODF in {8, 27, 64, 216} and
     10..200 iterations (seeded); returns aggregate updates/s and the job
@@ -797,7 +802,7 @@ def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, 
     jobs = inputs.serving_stream(n_jobs, rate, seed=6)
     budget = int(budget_gb * (1 << 30))
     srv = pkg.Server(budget, device=dev, threads=threads, cells_per_thread=cpt, stages=stages, arith=arith,
-                     batch_steps=batch_steps)
+                     batch_steps=batch_steps, job_streams=job_streams)
     # warm-up: one small job through the whole path
     w = srv.submit(64, 64, 64, 3, split=(2, 2, 2), seed=1)
     srv.wait(w, 60.0)
@@ -836,6 +841,13 @@ def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, 
             "jobs": n_jobs, "rate_per_s": rate}
 
 
+SERVE_JOB_STREAMS = 16  # the serving leg's default: one persistent launch per job on 16 streams
+
+
+def serve_job_streams(args):
+    return SERVE_JOB_STREAMS if args.job_streams < 0 else args.job_streams
+
+
 def run_serve(args, pkg, torch, rank, world, dev):
     """Serving stream: independent jobs arrive as a Poisson process (seeded),
     each a cubic grid with edge log-uniform in [64, 384], ODF in {8, 27, 64,
@@ -845,7 +857,7 @@ def run_serve(args, pkg, torch, rank, world, dev):
     clocks = ClockSampler(dev)
     clocks.start()
     r = serve_stream(pkg, dev, args.jobs, args.rate, args.budget_gb, args.threads, args.cpt, args.stages, args.arith,
-                     args.batch_steps)
+                     args.batch_steps, serve_job_streams(args))
     clk = clocks.stop()
     line = {"metric": METRIC, "value": r["updates_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.jobs,
             "warmup": 1, "ms_per_step": r["wall_s"] * 1e3 / args.jobs, "higher_is_better": True, "scaling": "weak",
@@ -853,6 +865,7 @@ def run_serve(args, pkg, torch, rank, world, dev):
             "config": {"workload": "jacobi3d-serving-poisson", "jobs": args.jobs, "rate_per_s": args.rate,
                        "edge": "log-uniform [64,384]", "odf": "{8,27,64,216}", "iters": "U[10,200]",
                        "budget_gb": args.budget_gb, "seed": 6, "batch_steps": args.batch_steps,
+                       "job_streams": serve_job_streams(args),
                        "note": "a step here is one job"},
             "latency_p50_s": r["p50_s"], "latency_p99_s": r["p99_s"], "latency_mean_s": r["mean_s"],
             "latency_max_s": r["max_s"], "wall_s": r["wall_s"], "launches": r["launches"],

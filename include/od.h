@@ -493,6 +493,13 @@ typedef struct od_server_config {
                                     (step, job, tile) tickets, so no step ends in a
                                     partial wave; jobs admitted meanwhile join the next
                                     launch.  1: one fused step per launch */
+    int32_t job_streams;         /* 0: the batched launches above.  N in [1, 64]: each
+                                    admitted job's whole run is one persistent launch
+                                    (od_step on the job's context, path persistent) on
+                                    the least-loaded of N streams, and the jobs' kernels
+                                    share the SMs as the hardware schedules them;
+                                    batch_steps is then unused.  od_server_config_default
+                                    sets 16 */
 } od_server_config;
 
 typedef struct od_job_info {

@@ -392,10 +392,12 @@ class Server:
 
     def __init__(self, hbm_budget_bytes: int, *, max_active: int = 0, device: int = 0, threads: int = 0,
                  cells_per_thread: int = 0, stages: int = 0, arith: int = -1, max_jobs_per_launch: int = 0,
-                 batch_steps: int = 0):
+                 batch_steps: int = 0, job_streams: int | None = None):
         cfg = _native.od_server_config()
         lib().od_server_config_default(ctypes.byref(cfg))
         cfg.batch_steps = int(batch_steps)
+        if job_streams is not None:  # else the library's default (one persistent launch per job)
+            cfg.job_streams = int(job_streams)
         cfg.hbm_budget_bytes = int(hbm_budget_bytes)
         cfg.max_active, cfg.device = int(max_active), int(device)
         cfg.threads, cfg.cells_per_thread, cfg.stages, cfg.arith = int(threads), int(cells_per_thread), \

@@ -61,7 +61,7 @@ class od_server_config(ctypes.Structure):
     _fields_ = [
         ("hbm_budget_bytes", _u64), ("max_active", _i32), ("max_jobs_per_launch", _i32), ("device", _i32),
         ("threads", _i32), ("cells_per_thread", _i32), ("stages", _i32), ("arith", _i32), ("pool", _vp),
-        ("batch_steps", _i32),
+        ("batch_steps", _i32), ("job_streams", _i32),
     ]
 
 

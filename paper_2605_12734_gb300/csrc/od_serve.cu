@@ -15,6 +15,12 @@
 //      and a finished job simply drops out of the next one;
 //   3. watches the events of launches in flight (at most two ahead) and marks
 //      a job done when the launch holding its last step has completed.
+// With job_streams = N > 0 the worker instead launches each admitted job's
+// whole run as its own persistent kernel (k_persistent, the job's arguments
+// in the kernel's parameters) on one of N streams, and the hardware runs the
+// jobs' kernels side by side: a job's CTAs start as others' leave, so a small
+// job fills the SMs a large one leaves idle.  A job is done when the event
+// after its kernel has completed.
 // A job's result stays on the device until the client fetches and releases
 // it.  Jobs never share memory, so each result is bit-identical to the same
 // job solved alone.
@@ -108,6 +114,10 @@ struct Job {
     int64_t cells = 0;
     int32_t threads = 0, cpt = 0;  // the job's CTA shape (from its plan)
     std::string err;
+    // stream mode: the job's stream, the events around its kernel once it is
+    // launched and the pinned slot its error record is copied into after it
+    int stream = -1, err_slot = -1;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 struct Batch {
@@ -130,6 +140,14 @@ struct od_server {
     int threads = 128, cpt = 4, stages = 4, arith = 2, smem_cap = 0;
     int batch_steps = 8, num_sms = 0;
     int32_t *d_queue = nullptr;  // ticket counters: [in-flight slot][shape group]
+    // stream mode (job_streams > 0): one persistent launch per job
+    std::vector<cudaStream_t> job_streams;
+    std::vector<int> stream_jobs;   // unfinished jobs assigned to each stream
+    ErrDev *h_err = nullptr;        // pinned error records, one slot per launched job
+    std::vector<int> free_err;      // free slots of h_err
+    cudaEvent_t base_ev = nullptr;  // device time origin of the jobs' kernels
+    std::vector<std::pair<double, double>> kernel_spans;  // [start, end] seconds after base_ev
+    std::vector<Job *> launched;    // running jobs whose kernel is in flight
     std::vector<cudaEvent_t> free_events;
     std::deque<Batch> inflight;
     int64_t next_batch = 0;
@@ -157,6 +175,7 @@ namespace {
 // CTA shapes the planner picks from; with per-job shapes a step runs at most
 // one batched launch for each.
 constexpr int kShapes = 4;
+constexpr int kErrSlots = 1024;  // stream mode: jobs whose kernels are in flight at once
 constexpr int32_t kAutoShapes[kShapes][2] = {{128, 4}, {128, 2}, {256, 4}, {256, 8}};
 
 od_config job_config(od_server *s, Job *j) {
@@ -167,7 +186,7 @@ od_config job_config(od_server *s, Job *j) {
         if (a == 1) c.cuts_y = p;
         if (a == 2) c.cuts_z = p;
     }
-    c.path = OD_PATH_FUSED;
+    c.path = s->job_streams.empty() ? OD_PATH_FUSED : OD_PATH_PERSISTENT;
     c.autotune = 0;
     c.threads = s->threads ? s->threads : j->threads;
     c.cells_per_thread = s->threads ? s->cpt : j->cpt;
@@ -175,7 +194,9 @@ od_config job_config(od_server *s, Job *j) {
     c.arith = s->arith;
     c.stream_pool = 1;
     c.device = s->device;
-    c.stream = s->admit;
+    // stream mode: the job's own stream, so its initialisation and its run
+    // queue behind no other job's kernel
+    c.stream = j->stream >= 0 ? s->job_streams[(size_t)j->stream] : s->admit;
     return c;
 }
 
@@ -191,6 +212,10 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
         s->queue.pop_front();
         j->admitting = true;
         j->off = off;
+        if (!s->job_streams.empty()) {  // stream mode: the stream with the fewest unfinished jobs
+            j->stream = (int)(std::min_element(s->stream_jobs.begin(), s->stream_jobs.end()) - s->stream_jobs.begin());
+            s->stream_jobs[(size_t)j->stream]++;
+        }
         od_config c = job_config(s, j);
         c.arena = s->pool_base + off;
         c.arena_bytes = j->bytes;
@@ -208,6 +233,7 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
             known_shape |= s->threads ? (ctx->plan.threads == s->threads && ctx->plan.cpt == s->cpt)
                                       : (ctx->plan.threads == kAutoShapes[g][0] && ctx->plan.cpt == kAutoShapes[g][1]);
         if (st != OD_OK || !known_shape || ctx->plan.stage_doubles * s->stages * 8 + 256 > s->smem_cap) {
+            if (j->stream >= 0) s->stream_jobs[(size_t)j->stream]--;
             if (ctx) od_destroy(ctx);
             s->pool.release(j->off, j->bytes);
             j->state = OD_JOB_FAILED;
@@ -221,6 +247,7 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
         j->ctx = ctx;
         j->t_admit = s->now();
         if (j->iters == 0) {  // nothing to run: done at admission
+            if (j->stream >= 0) s->stream_jobs[(size_t)j->stream]--;
             j->state = OD_JOB_DONE;
             j->t_done = j->t_admit;
             s->done++;
@@ -336,6 +363,7 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
         geom.stages = s->stages;
         geom.stage_doubles = max_sd[(size_t)g];
         geom.spin_ns = hk[(size_t)jo[(size_t)g]].spin_ns;
+        geom.one = 1;  // the arithmetic's opaque constant
         cudaError_t e;
         if (s->batch_steps > 1) {
             int bps = 0;
@@ -370,6 +398,97 @@ bool launch_batch(od_server *s, std::vector<KArgs> &hk, std::vector<int32_t> &hf
     return true;
 }
 
+// Stream mode (lock held): launch every running job that has no kernel yet,
+// its whole run as one persistent kernel on its own stream, between two
+// events.  Returns whether anything was launched.
+bool launch_jobs(od_server *s) {
+    bool any = false;
+    for (Job *j : s->running) {
+        if (j->ev1) continue;
+        if (s->free_err.empty()) break;  // every error slot is in flight: launch later
+        j->err_slot = s->free_err.back();
+        s->free_err.pop_back();
+        j->ev0 = take_event(s);
+        j->ev1 = take_event(s);
+        cudaEventRecord(j->ev0, j->ctx->stream);
+        od_status st = od_step(j->ctx, j->iters);
+        // the job's error record follows its kernel into pinned memory, so
+        // completion is read without a synchronising call
+        if (st == OD_OK && cudaMemcpyAsync(s->h_err + j->err_slot, j->ctx->d_err, sizeof(ErrDev),
+                                           cudaMemcpyDeviceToHost, j->ctx->stream) != cudaSuccess)
+            st = od::set_last_error(OD_ECUDA, "error record copy");
+        if (st != OD_OK) s->h_err[j->err_slot].code = -1;  // no copy queued: retired as failed
+        cudaEventRecord(j->ev1, j->ctx->stream);
+        s->launched.push_back(j);  // retired (done or failed) once ev1 has completed
+        if (st != OD_OK) {
+            s->worker_error = std::string("job launch: ") + od_last_error();
+            return any;
+        }
+        s->launches++;
+        any = true;
+    }
+    return any;
+}
+
+// Stream mode (lock held): mark done every job whose kernel has completed,
+// keeping its kernel's device interval for the busy time.
+void retire_jobs(od_server *s) {
+    bool any = false;
+    const double t = s->now();
+    for (size_t k = 0; k < s->launched.size();) {
+        Job *j = s->launched[k];
+        const cudaError_t q = cudaEventQuery(j->ev1);
+        if (q == cudaErrorNotReady) {
+            ++k;
+            continue;
+        }
+        float a = 0.f, b = 0.f;
+        if (q == cudaSuccess && cudaEventElapsedTime(&a, s->base_ev, j->ev0) == cudaSuccess &&
+            cudaEventElapsedTime(&b, s->base_ev, j->ev1) == cudaSuccess)
+            s->kernel_spans.emplace_back(a * 1e-3, b * 1e-3);
+        s->free_events.push_back(j->ev0);
+        s->free_events.push_back(j->ev1);
+        j->ev0 = j->ev1 = nullptr;
+        s->launched[k] = s->launched.back();
+        s->launched.pop_back();
+        const int32_t code = q == cudaSuccess ? s->h_err[j->err_slot].code : -1;
+        s->free_err.push_back(j->err_slot);
+        j->err_slot = -1;
+        s->stream_jobs[(size_t)j->stream]--;
+        if (code == 0) {
+            j->state = OD_JOB_DONE;
+            j->t_done = t;
+            s->done++;
+            s->updates_done += (double)j->cells * j->iters;
+        } else {
+            j->state = OD_JOB_FAILED;
+            j->err = q != cudaSuccess ? cudaGetErrorString(q) : "the job's kernel reported an error (timeout)";
+            s->failed++;
+        }
+        any = true;
+    }
+    if (any) s->cv_done.notify_all();
+}
+
+// Stream mode: the device's busy time, the union of the jobs' kernel
+// intervals (lock held).
+double busy_union(od_server *s) {
+    std::vector<std::pair<double, double>> v = s->kernel_spans;
+    std::sort(v.begin(), v.end());
+    double sum = 0, a = 0, b = -1;
+    for (const auto &iv : v) {
+        if (iv.first > b) {
+            if (b > a) sum += b - a;
+            a = iv.first;
+            b = iv.second;
+        } else {
+            b = std::max(b, iv.second);
+        }
+    }
+    if (b > a) sum += b - a;
+    return sum;
+}
+
 // Admission thread: creates the contexts of queued jobs (tables, initial
 // field) while the worker keeps the GPU busy with the running ones.
 void admitter_main(od_server *s) {
@@ -387,6 +506,18 @@ void worker_main(od_server *s) {
     std::vector<int32_t> hf;
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
+        if (!s->job_streams.empty()) {  // stream mode: poll the jobs' kernels
+            retire_jobs(s);
+            const size_t before = s->running.size();
+            s->running.erase(std::remove_if(s->running.begin(), s->running.end(),
+                                            [](Job *j) { return j->state != OD_JOB_RUNNING; }),
+                             s->running.end());
+            if (s->running.size() != before) s->cv_admit.notify_all();
+            if (s->worker_error.empty() && launch_jobs(s)) continue;
+            // a short wait: a kernel's completion is only seen by polling
+            s->cv_work.wait_for(lk, std::chrono::microseconds(s->launched.empty() ? 2000 : 100));
+            continue;
+        }
         retire(s);
         // drop finished jobs from the running set (their memory stays until release)
         const size_t before = s->running.size();
@@ -425,6 +556,7 @@ void od_server_config_default(od_server_config *c) {
     c->max_active = 0;
     c->max_jobs_per_launch = 256;
     c->arith = -1;
+    c->job_streams = 16;
 }
 
 od_status od_server_create(od_server **out, const od_server_config *cfg) {
@@ -445,6 +577,10 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
     if (cfg->batch_steps < 0 || cfg->batch_steps > 4096) {
         delete s;
         return fail(OD_EINVAL, "batch_steps must be in [0, 4096]");
+    }
+    if (cfg->job_streams < 0 || cfg->job_streams > 64) {
+        delete s;
+        return fail(OD_EINVAL, "job_streams must be in [0, 64]");
     }
     s->t0 = Clock::now();
     auto bail = [&](od_status st, const std::string &m) {
@@ -472,6 +608,23 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
     if (cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking) != cudaSuccess)
         return bail(OD_ECUDA, "cannot create streams");
+    for (int k = 0; k < cfg->job_streams; ++k) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(OD_ECUDA, "cannot create the job streams");
+        s->job_streams.push_back(st);
+        s->stream_jobs.push_back(0);
+    }
+    if (!s->job_streams.empty()) {
+        if (cudaHostAlloc(&s->h_err, kErrSlots * sizeof(ErrDev), cudaHostAllocDefault) != cudaSuccess) {
+            s->h_err = nullptr;
+            return bail(OD_ENOMEM, "cannot allocate the pinned error records");
+        }
+        for (int k = kErrSlots - 1; k >= 0; --k) s->free_err.push_back(k);
+        if (cudaEventCreate(&s->base_ev) != cudaSuccess || cudaEventRecord(s->base_ev, s->compute) != cudaSuccess ||
+            cudaEventSynchronize(s->base_ev) != cudaSuccess)
+            return bail(OD_ECUDA, "cannot record the time origin");
+    }
     for (int k = 0; k < 2; ++k)
         if (cudaMalloc(&s->d_jobs[k], (size_t)s->max_jobs * sizeof(KArgs)) != cudaSuccess ||
             cudaMalloc(&s->d_first[k], (size_t)(s->max_jobs + kShapes) * sizeof(int32_t)) != cudaSuccess)
@@ -634,7 +787,7 @@ od_status od_server_stats(od_server *s, od_server_stats_t *out) {
     out->pool_peak = s->pool.peak();
     out->seconds = s->now();
     out->admit_seconds = s->admit_seconds;
-    out->busy_seconds = s->busy_seconds;
+    out->busy_seconds = s->job_streams.empty() ? s->busy_seconds : busy_union(s);
     if (!s->worker_error.empty()) return fail(OD_ECUDA, s->worker_error);
     return OD_OK;
 }
@@ -651,8 +804,11 @@ od_status od_server_destroy(od_server *s) {
     if (s->admitter.joinable()) s->admitter.join();
     cudaSetDevice(s->device);
     if (s->compute) cudaStreamSynchronize(s->compute);
+    for (cudaStream_t st : s->job_streams) cudaStreamSynchronize(st);
     for (auto &kv : s->jobs) {
         if (kv.second->ctx) od_destroy(kv.second->ctx);
+        if (kv.second->ev0) cudaEventDestroy(kv.second->ev0);
+        if (kv.second->ev1) cudaEventDestroy(kv.second->ev1);
         delete kv.second;
     }
     for (auto &b : s->inflight) {
@@ -667,6 +823,9 @@ od_status od_server_destroy(od_server *s) {
     if (s->d_queue) cudaFree(s->d_queue);
     if (s->compute) cudaStreamDestroy(s->compute);
     if (s->admit) cudaStreamDestroy(s->admit);
+    for (cudaStream_t st : s->job_streams) cudaStreamDestroy(st);
+    if (s->base_ev) cudaEventDestroy(s->base_ev);
+    if (s->h_err) cudaFreeHost(s->h_err);
     if (s->own_pool && s->pool_base) cudaFree(s->pool_base);
     delete s;
     return OD_OK;

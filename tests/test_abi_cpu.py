@@ -49,6 +49,10 @@ def test_version_and_defaults(od):
     cfg = od._native.od_config()
     od.lib().od_config_default(ctypes.byref(cfg))
     assert (cfg.nx, cfg.px, cfg.path) == (64, 1, od._native.OD_PATH_FUSED)
+    srv = od._native.od_server_config()
+    od.lib().od_server_config_default(ctypes.byref(srv))
+    # serving defaults: one persistent launch per job on 16 streams, arith 12 (-1)
+    assert (srv.job_streams, srv.batch_steps, srv.arith, srv.max_jobs_per_launch) == (16, 0, -1, 256)
 
 
 @pytest.mark.parametrize("n,p", [(64, 2), (100, 6), (512, 16), (7, 7), (513, 8), (1, 1)])
@@ -268,3 +272,16 @@ def test_async_transfers_check_arguments_first(od):
     buf = (ctypes.c_double * 8)()
     assert L.od_write_async(None, buf) == od._native.OD_EINVAL
     assert L.od_read_async(None, buf) == od._native.OD_EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("batch_steps", -1), ("batch_steps", 4097), ("job_streams", -1),
+                                         ("job_streams", 65)])
+def test_server_config_checked_before_the_device(od, field, value):
+    # out-of-range serving options are refused before any device call
+    cfg = od._native.od_server_config()
+    od.lib().od_server_config_default(ctypes.byref(cfg))
+    cfg.hbm_budget_bytes = 1 << 30
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    assert od.lib().od_server_create(ctypes.byref(h), ctypes.byref(cfg)) == od._native.OD_EINVAL
+    assert not h.value

@@ -42,12 +42,13 @@ JOBS = [  # (edge, split, iters, seed, init_mode)
 ]
 
 
-@pytest.mark.parametrize("batch_steps", [0, 1, 3])
-def test_jobs_in_the_mix_match_alone_and_oracle(od, batch_steps):
+@pytest.mark.parametrize("batch_steps,job_streams", [(0, 0), (1, 0), (3, 0), (0, 2), (0, 8)])
+def test_jobs_in_the_mix_match_alone_and_oracle(od, batch_steps, job_streams):
     # 0: the default persistent batches of 8 steps; 1: one fused step per
-    # launch; 3: batches that end inside most jobs' step counts
+    # launch; 3: batches that end inside most jobs' step counts; job_streams:
+    # one persistent launch per job, on 2 streams (jobs share a stream) or 8
     results = {}
-    with od.Server(256 << 20, max_active=4, batch_steps=batch_steps) as srv:
+    with od.Server(256 << 20, max_active=4, batch_steps=batch_steps, job_streams=job_streams) as srv:
         ids = []
         for k, (e, sp, it, seed, mode) in enumerate(JOBS):
             ids.append(srv.submit(e, e, e, it, split=sp, seed=seed, init_mode=mode))
@@ -62,8 +63,11 @@ def test_jobs_in_the_mix_match_alone_and_oracle(od, batch_steps):
         st = srv.stats()
         assert st["done"] == len(JOBS) and st["failed"] == 0
         assert st["pool_used"] == 0
-        if batch_steps == 1:
+        if batch_steps == 1 and not job_streams:
             assert st["launches"] >= max(j[2] for j in JOBS)
+        if job_streams:  # one launch per job that has steps
+            assert st["launches"] == sum(1 for j in JOBS if j[2] > 0)
+        assert 0 < st["busy_seconds"] <= st["seconds"]
     for jid, (e, sp, it, seed, mode) in zip(ids, JOBS):
         want = oracle.solve(e, e, e, seed, mode, it)
         assert same(results[jid], want), (e, sp, it)
@@ -72,7 +76,8 @@ def test_jobs_in_the_mix_match_alone_and_oracle(od, batch_steps):
             assert same(results[jid], alone.read())
 
 
-def test_serving_stream_at_full_job_sizes(od):
+@pytest.mark.parametrize("job_streams", [0, 16])
+def test_serving_stream_at_full_job_sizes(od, job_streams):
     # jobs from the serving workload's own ranges -- edges up to 384, ODF up
     # to 216 with balanced splits that do not divide the edge (100 = 6 x 16 +
     # 4, 203 = 3 x 67 + 2, 250 = 4 x 62 + 2), 10..200 iterations -- submitted
@@ -80,7 +85,7 @@ def test_serving_stream_at_full_job_sizes(od):
     jobs = [(384, 6, 30, 61), (100, 6, 200, 62), (203, 3, 57, 63), (64, 2, 10, 64), (250, 4, 41, 65),
             (384, 2, 12, 66), (77, 3, 133, 67), (128, 6, 88, 68)]
     results = {}
-    with od.Server(24 << 30) as srv:
+    with od.Server(24 << 30, job_streams=job_streams) as srv:
         ids = []
         for k, (e, p, it, seed) in enumerate(jobs):
             ids.append(srv.submit(e, e, e, it, split=(p, p, p), seed=seed))
@@ -92,11 +97,17 @@ def test_serving_stream_at_full_job_sizes(od):
             srv.release(jid)
     threads = oracle.max_threads()
     for jid, (e, p, it, seed) in zip(ids, jobs):
-        want = oracle.solve(e, e, e, seed, 1, it, threads=threads)
-        assert same(results[jid], want), (e, p, it)
+        if (e, it, seed) not in _FULL_SIZE_WANT:  # the oracle's results, shared by both modes
+            _FULL_SIZE_WANT[(e, it, seed)] = oracle.solve(e, e, e, seed, 1, it, threads=threads)
+        assert same(results[jid], _FULL_SIZE_WANT[(e, it, seed)]), (e, p, it)
+        if job_streams:
+            continue  # the job alone: once
         with od.Jacobi3D(e, e, e, split=(p, p, p), seed=seed, init_mode=1, path="persistent") as alone:
             alone.step(it)
             assert same(results[jid], alone.read()), (e, p, it)
+
+
+_FULL_SIZE_WANT = {}
 
 
 @pytest.mark.parametrize("batch_steps", [0, 1])
@@ -108,7 +119,7 @@ def test_jobs_of_three_cta_shapes_in_one_step(od, batch_steps):
             ((600, 20, 16), (2, 1, 1), 4, 24)]
     for dims, sp, _, _ in jobs[:3]:
         assert od.plan(*dims, split=sp)["threads"] * od.plan(*dims, split=sp)["cells_per_thread"] in (256, 512, 1024)
-    with od.Server(1 << 30, batch_steps=batch_steps) as srv:
+    with od.Server(1 << 30, batch_steps=batch_steps, job_streams=0) as srv:
         ids = [srv.submit(*dims, it, split=sp, seed=seed) for dims, sp, it, seed in jobs]
         got = []
         for jid in ids:
