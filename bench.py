@@ -630,7 +630,11 @@ def run_ours(args):
             legs[f"{key}_hbm_frac"] = info["bytes_per_step"] / (ms_w * 1e-3) / 1e9 / hbm_peak
             legs[f"{key}_arith"] = info["arith"]
         r = serve_stream(pkg, dev, 150, 120.0, args.budget_gb, job_streams=serve_job_streams(args))
+        alone = jobs_alone_rate(pkg, dev, 150, 120.0)
         legs.update({"serve_job_streams": serve_job_streams(args),
+                     "serve_jobs_alone_updates_per_s": alone,
+                     # the server's rate while the device is busy, against the same jobs run alone
+                     "serve_busy_vs_jobs_alone": r["updates_per_s"] / max(r["device_busy_frac"], 1e-9) / alone,
                      "serve_p50_ms": r["p50_s"] * 1e3, "serve_p99_ms": r["p99_s"] * 1e3,
                      "serve_updates_per_s": r["updates_per_s"], "serve_rate_per_s": r["rate_per_s"],
                      "serve_jobs": r["jobs"], "serve_device_busy_frac": r["device_busy_frac"],
@@ -792,6 +796,30 @@ def run_shards(args, pkg, torch, rank, dev):
     return 0
 
 
+def jobs_alone_rate(pkg, dev, n_jobs, rate):
+    """The serving stream's jobs run one at a time, each alone on the GPU in
+    its own context (persistent path, the planner's shape): total updates
+    over the sum of the jobs' device times (CUDA events around each job's
+    steps).  The rate the server would reach if it only queued the jobs --
+    the yardstick for what running them side by side gains."""
+    import torch
+    from paper_2605_12734_gb300 import inputs
+    stream = torch.cuda.Stream(device=dev)
+    upd, ms = 0.0, 0.0
+    for j in inputs.serving_stream(n_jobs, rate, seed=6):
+        with pkg.Jacobi3D(j.edge, j.edge, j.edge, split=(j.p, j.p, j.p), seed=j.seed, init_mode=1,
+                          path="persistent", device=dev, stream=stream.cuda_stream) as s:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(j.iters)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            upd += j.updates
+    return upd / (ms * 1e-3)
+
+
 def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, arith=-1, batch_steps=0,
                  job_streams=0):
     """Poisson arrivals of independent jobs into one server: each a cubic
@@ -859,6 +887,7 @@ def run_serve(args, pkg, torch, rank, world, dev):
     r = serve_stream(pkg, dev, args.jobs, args.rate, args.budget_gb, args.threads, args.cpt, args.stages, args.arith,
                      args.batch_steps, serve_job_streams(args))
     clk = clocks.stop()
+    alone = jobs_alone_rate(pkg, dev, args.jobs, args.rate)
     line = {"metric": METRIC, "value": r["updates_per_s"], "unit": UNIT, "n_gpus": world, "steps": args.jobs,
             "warmup": 1, "ms_per_step": r["wall_s"] * 1e3 / args.jobs, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -870,7 +899,9 @@ def run_serve(args, pkg, torch, rank, world, dev):
             "latency_p50_s": r["p50_s"], "latency_p99_s": r["p99_s"], "latency_mean_s": r["mean_s"],
             "latency_max_s": r["max_s"], "wall_s": r["wall_s"], "launches": r["launches"],
             "pool_peak_gb": r["pool_peak_gb"], "offered_updates_per_s": r["offered_updates_per_s"],
-            "admit_seconds": r["admit_seconds"], "device_busy_frac": r["device_busy_frac"], "clocks": clk}
+            "admit_seconds": r["admit_seconds"], "device_busy_frac": r["device_busy_frac"],
+            "jobs_alone_updates_per_s": alone, "vs_jobs_alone": r["updates_per_s"] / alone,
+            "busy_vs_jobs_alone": r["updates_per_s"] / max(r["device_busy_frac"], 1e-9) / alone, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
