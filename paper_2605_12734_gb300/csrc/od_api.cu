@@ -847,7 +847,10 @@ od_status od_decompose(const od_config *cfg, int64_t *box, int32_t *nbr, int64_t
     return OD_OK;
 }
 
-od_status od_create(od_ctx **out, const od_config *cfg_in) {
+}  // extern "C"
+
+namespace od {
+od_status create_context(od_ctx **out, const od_config *cfg_in, bool sync) {
     if (!out || !cfg_in) return fail(OD_EINVAL, "null argument");
     *out = nullptr;
     od_config tuned = *cfg_in;
@@ -982,12 +985,17 @@ od_status od_create(od_ctx **out, const od_config *cfg_in) {
     // the exact arithmetic's window (od_write raises it for imported fields)
     const uint64_t vmax0 = 0x3FEFFFFFFFFFFFFFull;
     OD_TRY(cudaMemcpyAsync(c->d_vmax, &vmax0, sizeof vmax0, cudaMemcpyHostToDevice, c->stream));
-    OD_TRY(cudaStreamSynchronize(c->stream));
+    if (sync) OD_TRY(cudaStreamSynchronize(c->stream));
     c->ghosts_current = true;
 #undef OD_TRY
     *out = c;
     return OD_OK;
 }
+}  // namespace od
+
+extern "C" {
+
+od_status od_create(od_ctx **out, const od_config *cfg_in) { return od::create_context(out, cfg_in, true); }
 
 od_status od_step(od_ctx *c, int32_t iters) {
     if (!c) return fail(OD_EINVAL, "null context");

@@ -66,4 +66,9 @@ od_status set_last_error(od_status s, const std::string &msg);
 KArgs base_args(const od_ctx *c);
 // Synchronise the context's stream and turn a device error record into a status.
 od_status check_device_error(od_ctx *c);
+// od_create; with sync = false it returns once the initialisation is queued
+// on the context's stream (errors of the queued work surface at the next
+// synchronising call), so a caller that keeps its own stream order -- the
+// serving loop -- does not wait for the device.
+od_status create_context(od_ctx **out, const od_config *cfg, bool sync);
 }  // namespace od

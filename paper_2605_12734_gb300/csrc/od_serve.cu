@@ -222,7 +222,10 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
         lk.unlock();
         const double t_create = s->now();
         od_ctx *ctx = nullptr;
-        od_status st = od_create(&ctx, &c);
+        // stream mode: queue the job's initialisation on its stream and
+        // return (its kernel follows on the same stream); batched mode: wait,
+        // the batched launches run on another stream
+        od_status st = od::create_context(&ctx, &c, s->job_streams.empty());
         std::string msg = st == OD_OK ? "" : od_last_error();
         lk.lock();
         j->admitting = false;
@@ -234,6 +237,8 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
                                       : (ctx->plan.threads == kAutoShapes[g][0] && ctx->plan.cpt == kAutoShapes[g][1]);
         if (st != OD_OK || !known_shape || ctx->plan.stage_doubles * s->stages * 8 + 256 > s->smem_cap) {
             if (j->stream >= 0) s->stream_jobs[(size_t)j->stream]--;
+            // work queued by the creation (stream mode) may still write the arena
+            if (!s->job_streams.empty()) cudaStreamSynchronize((cudaStream_t)c.stream);
             if (ctx) od_destroy(ctx);
             s->pool.release(j->off, j->bytes);
             j->state = OD_JOB_FAILED;
