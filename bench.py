@@ -261,6 +261,28 @@ def oracle_cpu_baseline(edge: int, target_s: float = 10.0, e2e_out=None, e2e_ite
                      f"iterations in {dt:.1f} s",
            "single_core": {"value": ups1, "unit": UNIT, "cores": 1,
                            "sample": f"the same on one thread, the last {iters1} iterations in {dt1:.1f} s"}}
+    # the method itself on the CPU: the decomposed oracle (per-block arrays,
+    # explicit face copies, one thread) at ODF 4096 on the same field, and
+    # the small parity case (64^3, interior 0, in 1 or 8 blocks, 10 iterations)
+    ez = oracle.split(edge, 16)
+    upsd, itd, dtd = _time_oracle(lambda n: oracle.sweep_decomposed(P, ez, ez, ez, n), edge ** 3, target_s / 3)
+    out["decomposed_odf4096"] = {"value": upsd, "unit": UNIT, "cores": 1,
+                                 "sample": f"{edge}^3 in 16^3 blocks, decomposed C oracle on one thread, the last "
+                                           f"{itd} iterations in {dtd:.1f} s"}
+    P64 = oracle.init_padded(64, 64, 64, 1, inputs.INIT_ZERO_INTERIOR)
+    e64 = oracle.split(64, 2)
+    small = {}
+    for key, fn in (("odf1", lambda: oracle.sweep(P64, 10, 1)),
+                    ("odf8", lambda: oracle.sweep_decomposed(P64, e64, e64, e64, 10))):
+        best = float("inf")
+        for _ in range(5):
+            t0 = time.perf_counter()
+            fn()
+            best = min(best, time.perf_counter() - t0)
+        small[key] = 64 ** 3 * 10 / best
+    out["small_64cubed"] = {"odf1_updates_per_s": small["odf1"], "odf8_updates_per_s": small["odf8"], "cores": 1,
+                            "sample": "64^3 (interior 0, shell U[0,1) seed 1), 10 iterations, best of 5 calls "
+                                      "(one-off copy included)"}
     if e2e_out is not None:
         t0 = time.perf_counter()
         want = oracle.solve(edge, edge, edge, 2, inputs.INIT_UNIFORM, e2e_iters, threads)
