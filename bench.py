@@ -179,7 +179,7 @@ def profiled_kernel(args, plan):
 
 
 # bumped whenever a tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 14     # 3D 7-point
+KERNEL_REV = 15     # 3D 7-point
 KERNEL_REV_2D = 15  # 2D 5-point
 
 

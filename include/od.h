@@ -528,7 +528,9 @@ OD_API od_status od_server_create(od_server **out, const od_server_config *cfg);
 /* Queue a job: the decomposition and seed of *job (cut lists are copied;
  * path, tile shape, stream and arena fields are ignored) and its iteration
  * count.  OD_EBUDGET if the job alone exceeds the whole budget; OD_EINVAL for
- * a stencil other than OD_STENCIL_3D7 (a batched launch shares one kernel). */
+ * a stencil other than OD_STENCIL_3D7 with batched launches (job_streams = 0:
+ * a batched launch shares one kernel); per-job launches also take
+ * OD_STENCIL_2D5 jobs. */
 OD_API od_status od_server_submit(od_server *s, const od_config *job, int32_t iters, uint64_t *job_id);
 /* Wait up to timeout_s seconds for the job to be done or failed; *state is
  * its state on return (OD_OK also on timeout). */

@@ -235,7 +235,9 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
         for (int g = 0; st == OD_OK && g < kShapes; ++g)
             known_shape |= s->threads ? (ctx->plan.threads == s->threads && ctx->plan.cpt == s->cpt)
                                       : (ctx->plan.threads == kAutoShapes[g][0] && ctx->plan.cpt == kAutoShapes[g][1]);
-        if (st != OD_OK || !known_shape || ctx->plan.stage_doubles * s->stages * 8 + 256 > s->smem_cap) {
+        // (per-job launches use each job's own plan: shape and shared memory are its own)
+        const bool batched = s->job_streams.empty();
+        if (st != OD_OK || (batched && (!known_shape || ctx->plan.stage_doubles * s->stages * 8 + 256 > s->smem_cap))) {
             if (j->stream >= 0) s->stream_jobs[(size_t)j->stream]--;
             // work queued by the creation (stream mode) may still write the arena
             if (!s->job_streams.empty()) cudaStreamSynchronize((cudaStream_t)c.stream);
@@ -654,7 +656,10 @@ od_status od_server_create(od_server **out, const od_server_config *cfg) {
 od_status od_server_submit(od_server *s, const od_config *job, int32_t iters, uint64_t *job_id) {
     if (!s || !job || !job_id || iters < 0) return fail(OD_EINVAL, "bad arguments");
     // one batched launch shares one kernel, the 3D 7-point one
-    if (job->stencil != OD_STENCIL_3D7) return fail(OD_EINVAL, "the serving loop runs 3D 7-point jobs only");
+    // a batched launch shares one kernel, the 3D 7-point one; per-job launches
+    // run each job's own kernel, so they also take the 2D 5-point stencil
+    if (job->stencil != OD_STENCIL_3D7 && (s->job_streams.empty() || job->stencil != OD_STENCIL_2D5))
+        return fail(OD_EINVAL, "batched serving runs 3D 7-point jobs only (job_streams > 0 also runs 2D 5-point)");
     Job *j = new Job();
     j->cfg = *job;
     const int32_t *cp[3] = {job->cuts_x, job->cuts_y, job->cuts_z};

@@ -147,11 +147,36 @@ def test_2d_autotune(od, tmp_path, monkeypatch):
         assert s.stats()["tuned"] == 1
 
 
-def test_2d_server_rejects(od):
-    with od.Server(1 << 30) as srv:
+def test_2d_server_batched_rejects(od):
+    # a batched launch shares the 3D kernel: 2D jobs are refused there
+    with od.Server(1 << 30, job_streams=0) as srv:
         with pytest.raises(od.ODError) as ei:
             srv.submit(64, 64, 1, 5, stencil="2d5")
         assert ei.value.status == od._native.OD_EINVAL
+
+
+def test_2d_jobs_served_beside_3d(od):
+    # per-job launches (the default) run each job's own kernel: 2D jobs of the
+    # paper's application, uneven splits included, beside 3D jobs, each equal
+    # to the oracle
+    jobs2d = [((512, 384), (4, 3), 9, 31), ((1000, 130), (8, 2), 25, 32), ((96, 64), (1, 1), 4, 33)]
+    jobs3d = [((64, 64, 64), (2, 2, 2), 12, 34), ((100, 100, 100), (6, 6, 6), 7, 35)]
+    with od.Server(2 << 30) as srv:
+        ids2 = [srv.submit(nx, ny, 1, it, split=sp, seed=seed, stencil="2d5") for (nx, ny), sp, it, seed in jobs2d]
+        ids3 = [srv.submit(*dims, it, split=sp, seed=seed) for dims, sp, it, seed in jobs3d]
+        got2, got3 = [], []
+        for jid in ids2 + ids3:
+            assert srv.wait(jid, 120.0) == od._native.OD_JOB_DONE, srv.info(jid)
+        for jid, ((nx, ny), _, _, _) in zip(ids2, jobs2d):
+            got2.append(srv.fetch(jid, np.empty(nx * ny)))
+            srv.release(jid)
+        for jid in ids3:
+            got3.append(srv.fetch(jid))
+            srv.release(jid)
+    for res, ((nx, ny), sp, it, seed) in zip(got2, jobs2d):
+        assert_bitexact(res, oracle.solve_2d(nx, ny, seed, 1, it), f"2D {nx}x{ny} {sp}")
+    for res, (dims, sp, it, seed) in zip(got3, jobs3d):
+        assert_bitexact(res, oracle.solve(*dims, seed, 1, it), f"3D {dims} {sp}")
 
 
 # ------------------------------------------------------------------ full size
