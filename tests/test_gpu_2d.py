@@ -110,6 +110,29 @@ def test_2d_switching_paths_and_checkpoint(od):
         assert_bitexact(s.read(), want, "restore")
 
 
+@pytest.mark.parametrize("path", ["persistent", "per_chare"])
+@pytest.mark.parametrize("kind", ["large", "signed", "binades"])
+def test_2d_imported_fields_of_any_range(od, path, kind):
+    # the 2D sweep's anchored window follows the imported field's largest
+    # value; cells outside it take the IEEE form; every cell is the oracle's
+    nx, ny, seed, iters = 300, 170, 23, 11
+    rng = np.random.default_rng({"large": 51, "signed": 52, "binades": 53}[kind])
+    u = rng.random(nx * ny)
+    if kind == "large":
+        interior = u * 3e7
+    elif kind == "signed":
+        interior = u * 2.0 - 1.0
+    else:
+        interior = (1.0 + u) * np.exp2(rng.integers(-30, 31, nx * ny).astype(np.float64))
+    P = oracle.init_padded_2d(nx, ny, seed, 1)
+    P[1:-1, 1:-1] = interior.reshape(ny, nx)
+    want = np.ascontiguousarray(oracle.sweep_2d(P, iters)[1:-1, 1:-1]).ravel()
+    with od.Jacobi2D(nx, ny, split=(4, 3), seed=seed, init_mode=1, path=path) as s:
+        s.write(interior)
+        s.step(iters)
+        assert_bitexact(s.read(), want, f"imported {kind} 2D field, {path}")
+
+
 def test_2d_device_read_and_write(od):
     import torch
     nx, ny = 96, 80

@@ -131,6 +131,43 @@ def test_device_read_and_write(od):
         assert_bitexact(s.read(), want, "device write")
 
 
+def _imported_field(kind, n, rng):
+    """Interior values for an imported field: magnitudes far from the seeded
+    shell's [0, 1), signs, zeros and subnormals -- cells whose operands span
+    more binades than the exact arithmetic's window, or leave its domain."""
+    u = rng.random(n)
+    if kind == "large":        # 1e6 times the shell's values: the anchor moves up with the field
+        return u * 1e6
+    if kind == "signed":       # negative operands leave the window's domain
+        return u * 2.0 - 1.0
+    if kind == "tiny":         # zeros, subnormals and values far below the shell's
+        v = u * 1e-300
+        v[::7] = 0.0
+        v[3::11] = 5e-324
+        return v
+    # mixed binades: 2^k for k in [-40, 40] times U[1, 2)
+    return (1.0 + u) * np.exp2(rng.integers(-40, 41, n).astype(np.float64))
+
+
+@pytest.mark.parametrize("path", ["persistent", "fused", "per_chare"])
+@pytest.mark.parametrize("kind", ["large", "signed", "tiny", "binades"])
+def test_imported_fields_of_any_range(od, path, kind):
+    # od_write raises the field's largest value, which anchors the exact
+    # arithmetic's window; cells whose operands leave the window take the
+    # IEEE form.  Either way every cell equals the oracle's sweep of the same
+    # padded field (the imported interior inside the seeded shell).
+    nx, ny, nz, seed, iters = 40, 34, 29, 21, 9
+    rng = np.random.default_rng({"large": 41, "signed": 42, "tiny": 43, "binades": 44}[kind])
+    interior = _imported_field(kind, nx * ny * nz, rng)
+    P = oracle.init_padded(nx, ny, nz, seed, 1)
+    P[1:-1, 1:-1, 1:-1] = interior.reshape(nz, ny, nx)
+    want = oracle.interior(oracle.sweep(P, iters))
+    with od.Jacobi3D(nx, ny, nz, split=(3, 2, 2), seed=seed, init_mode=1, path=path) as s:
+        s.write(interior)
+        s.step(iters)
+        assert_bitexact(s.read(), want, f"imported {kind} field, {path}")
+
+
 @pytest.mark.parametrize("pe", [2, 3, 8])
 def test_per_chare_with_several_submitting_threads(od, pe):
     # the per-chare path submitted by several host threads (the paper's PEs)
