@@ -857,26 +857,50 @@ def serve_stream(pkg, dev, n_jobs, rate, budget_gb, threads=0, cpt=0, stages=0, 
     w = srv.submit(64, 64, 64, 3, split=(2, 2, 2), seed=1)
     srv.wait(w, 60.0)
     srv.release(w)
-    ids = {}
+    while srv.next_completion(0.0) is not None:  # the warm-up job's completion
+        pass
+    # the client releases every job as soon as it ends (the server's
+    # completion queue, drained by a second thread), as a serving client
+    # would, so finished jobs do not hold the HBM budget against new arrivals
+    ids, lock = {}, threading.Lock()
+    lat, upd, span, failed = [], [0.0], [None, 0.0], []
+
+    def reap():
+        left = n_jobs
+        while left:
+            jid = srv.next_completion(0.05)
+            if jid is None:
+                continue
+            with lock:
+                j = ids.pop(jid, None)
+            if j is None:  # not one of this stream's jobs: stop, the check below reports it
+                failed.append((jid, "unknown"))
+                return
+            info = srv.info(jid)
+            if info["state"] != 2:
+                failed.append((jid, info["state"]))
+            lat.append(info["t_done"] - info["t_submit"])
+            span[0] = info["t_submit"] if span[0] is None else min(span[0], info["t_submit"])
+            span[1] = max(span[1], info["t_done"])
+            upd[0] += j.updates
+            srv.release(jid)
+            left -= 1
+
+    reaper = threading.Thread(target=reap, daemon=True)
     t0 = time.perf_counter()
     busy0 = srv.stats()["busy_seconds"]
+    reaper.start()
     for j in jobs:
         delay = t0 + j.arrival_s - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        jid = srv.submit(j.edge, j.edge, j.edge, j.iters, split=(j.p, j.p, j.p), seed=j.seed)
-        ids[jid] = j
-    lat, upd, first_submit, last_done = [], 0.0, None, 0.0
-    for jid, j in ids.items():
-        st = srv.wait(jid, 600.0)
-        if st != 2:
-            raise SystemExit(f"job {jid} ended in state {st}")
-        info = srv.info(jid)
-        lat.append(info["t_done"] - info["t_submit"])
-        first_submit = info["t_submit"] if first_submit is None else min(first_submit, info["t_submit"])
-        last_done = max(last_done, info["t_done"])
-        upd += j.updates
-        srv.release(jid)
+        with lock:
+            jid = srv.submit(j.edge, j.edge, j.edge, j.iters, split=(j.p, j.p, j.p), seed=j.seed)
+            ids[jid] = j
+    reaper.join(timeout=1200.0)
+    if reaper.is_alive() or failed:
+        raise SystemExit(f"serving stream did not complete: {len(ids)} jobs unreaped, failed {failed[:5]}")
+    first_submit, last_done, upd = span[0], span[1], upd[0]
     st = srv.stats()
     srv.close()
     wall = last_done - first_submit

@@ -535,6 +535,12 @@ OD_API od_status od_server_submit(od_server *s, const od_config *job, int32_t it
 /* Wait up to timeout_s seconds for the job to be done or failed; *state is
  * its state on return (OD_OK also on timeout). */
 OD_API od_status od_server_wait(od_server *s, uint64_t job_id, double timeout_s, int32_t *state);
+/* The serving loop's completion queue: *job_id = the next job that ended
+ * (done or failed), in the order they ended, waiting up to timeout_s seconds
+ * for one; *job_id = 0 when none ended in time (OD_OK either way).  Each job
+ * is reported once, whether or not it was waited for; a client that releases
+ * jobs as they end keeps the budget free for new arrivals. */
+OD_API od_status od_server_next_completion(od_server *s, double timeout_s, uint64_t *job_id);
 OD_API od_status od_server_job_info(od_server *s, uint64_t job_id, od_job_info *out);
 /* Copy a done job's field (nx*ny*nz doubles, x fastest) to dst (device or host). */
 OD_API od_status od_server_fetch(od_server *s, uint64_t job_id, double *dst, int32_t dst_is_device);

@@ -427,6 +427,14 @@ class Server:
         check(lib().od_server_wait(self._h, job, float(timeout_s), ctypes.byref(st)), "od_server_wait")
         return st.value
 
+    def next_completion(self, timeout_s: float = 1.0) -> int | None:
+        """The next job that ended (done or failed), in the order they ended;
+        None if none ended within timeout_s (od_server_next_completion)."""
+        jid = ctypes.c_uint64()
+        check(lib().od_server_next_completion(self._h, float(timeout_s), ctypes.byref(jid)),
+              "od_server_next_completion")
+        return jid.value or None
+
     def info(self, job: int) -> dict:
         i = _native.od_job_info()
         check(lib().od_server_job_info(self._h, job, ctypes.byref(i)), "od_server_job_info")

@@ -112,6 +112,7 @@ SIGNATURES = {
     "od_server_create": (_i32, [ctypes.POINTER(_vp), ctypes.POINTER(od_server_config)]),
     "od_server_submit": (_i32, [_vp, ctypes.POINTER(od_config), _i32, ctypes.POINTER(_u64)]),
     "od_server_wait": (_i32, [_vp, _u64, ctypes.c_double, ctypes.POINTER(_i32)]),
+    "od_server_next_completion": (_i32, [_vp, ctypes.c_double, ctypes.POINTER(_u64)]),
     "od_server_job_info": (_i32, [_vp, _u64, ctypes.POINTER(od_job_info)]),
     "od_server_fetch": (_i32, [_vp, _u64, _vp, _i32]),
     "od_server_release": (_i32, [_vp, _u64]),

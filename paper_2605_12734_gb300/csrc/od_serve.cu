@@ -148,6 +148,7 @@ struct od_server {
     cudaEvent_t base_ev = nullptr;  // device time origin of the jobs' kernels
     std::vector<std::pair<double, double>> kernel_spans;  // [start, end] seconds after base_ev
     std::vector<Job *> launched;    // running jobs whose kernel is in flight
+    std::deque<uint64_t> completions;  // jobs that ended (done or failed), in the order they ended
     std::vector<cudaEvent_t> free_events;
     std::deque<Batch> inflight;
     int64_t next_batch = 0;
@@ -175,6 +176,9 @@ namespace {
 // CTA shapes the planner picks from; with per-job shapes a step runs at most
 // one batched launch for each.
 constexpr int kShapes = 4;
+
+// A job ended (done or failed): queue it for od_server_next_completion (lock held).
+void completed(od_server *s, Job *j) { s->completions.push_back(j->id); }
 constexpr int kErrSlots = 1024;  // stream mode: jobs whose kernels are in flight at once
 constexpr int32_t kAutoShapes[kShapes][2] = {{128, 4}, {128, 2}, {256, 4}, {256, 8}};
 
@@ -244,6 +248,7 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
             if (ctx) od_destroy(ctx);
             s->pool.release(j->off, j->bytes);
             j->state = OD_JOB_FAILED;
+            completed(s, j);
             j->err = st != OD_OK ? msg
                      : !known_shape ? "the planner chose a CTA shape the server does not launch"
                                     : "tile needs more shared memory than the server's launch shape";
@@ -257,6 +262,7 @@ bool admit(od_server *s, std::unique_lock<std::mutex> &lk) {
             if (j->stream >= 0) s->stream_jobs[(size_t)j->stream]--;
             j->state = OD_JOB_DONE;
             j->t_done = j->t_admit;
+            completed(s, j);
             s->done++;
             s->cv_done.notify_all();
             continue;
@@ -283,6 +289,7 @@ void retire(od_server *s) {
             if (j->state == OD_JOB_RUNNING && j->done_batch == b.index) {
                 j->state = OD_JOB_DONE;
                 j->t_done = t;
+                completed(s, j);
                 j->ctx->steps = j->iters;
                 s->done++;
                 s->updates_done += (double)j->cells * j->iters;
@@ -472,6 +479,7 @@ void retire_jobs(od_server *s) {
             j->err = q != cudaSuccess ? cudaGetErrorString(q) : "the job's kernel reported an error (timeout)";
             s->failed++;
         }
+        completed(s, j);
         any = true;
     }
     if (any) s->cv_done.notify_all();
@@ -712,6 +720,20 @@ od_status od_server_wait(od_server *s, uint64_t id, double timeout_s, int32_t *s
             return OD_OK;
         }
     }
+}
+
+od_status od_server_next_completion(od_server *s, double timeout_s, uint64_t *job_id) {
+    if (!s || !job_id) return fail(OD_EINVAL, "null argument");
+    *job_id = 0;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const auto until = Clock::now() + std::chrono::duration<double>(timeout_s < 0 ? 0 : timeout_s);
+    while (s->completions.empty())
+        if (s->cv_done.wait_until(lk, until) == std::cv_status::timeout) break;
+    if (!s->completions.empty()) {
+        *job_id = s->completions.front();
+        s->completions.pop_front();
+    }
+    return OD_OK;
 }
 
 od_status od_submit(od_server *s, const od_config *job, int32_t iters, uint64_t *job_id) {

@@ -134,6 +134,34 @@ def test_jobs_of_three_cta_shapes_in_one_step(od, batch_steps):
         assert same(res, oracle.solve(*dims, seed, 1, it)), dims
 
 
+@pytest.mark.parametrize("job_streams", [0, 4])
+def test_completion_queue_releases_as_jobs_end(od, job_streams):
+    # a budget for two jobs and six submitted at once: the client takes each
+    # ended job from the completion queue (every job exactly once, a 0-step
+    # job included) and releases it, which admits the next; results stay exact
+    e, sp = 48, (2, 2, 2)
+    need = od.plan(e, e, e, split=sp, path="persistent")["arena_bytes"]
+    jobs = [(11, 5), (12, 0), (13, 9), (14, 3), (15, 7), (16, 1)]
+    with od.Server(int(need * 2.5), job_streams=job_streams) as srv:
+        ids = {srv.submit(e, e, e, it, split=sp, seed=seed): (seed, it) for seed, it in jobs}
+        got, order = {}, []
+        t0 = time.time()
+        while len(order) < len(jobs):
+            assert time.time() - t0 < 120
+            jid = srv.next_completion(1.0)
+            if jid is None:
+                continue
+            assert jid in ids and jid not in got
+            assert srv.info(jid)["state"] == od._native.OD_JOB_DONE
+            got[jid] = srv.fetch(jid)
+            order.append(jid)
+            srv.release(jid)
+        assert srv.next_completion(0.0) is None
+        assert srv.stats()["pool_used"] == 0
+    for jid, (seed, it) in ids.items():
+        assert same(got[jid], oracle.solve(e, e, e, seed, 1, it)), (seed, it)
+
+
 def test_budget_admission_and_release(od):
     e, sp = 48, (2, 2, 2)
     need = od.plan(e, e, e, split=sp, threads=128, cells_per_thread=4, stages=4, arith=7)["arena_bytes"]
