@@ -387,8 +387,12 @@ class Comm:
 
 
 class Server:
-    """Serving loop (od_server): admits independent solves under an HBM budget,
-    keeps them resident and advances all running jobs together."""
+    """Serving loop (od_server): admits independent solves under an HBM budget
+    and keeps them resident until released.  By default each admitted job's
+    whole run is one persistent launch on one of 16 streams (job_streams), the
+    jobs' kernels sharing the SMs; job_streams=0 advances all running 3D jobs
+    together in batched launches of batch_steps steps.  next_completion()
+    hands out jobs as they end, so a client can release them at once."""
 
     def __init__(self, hbm_budget_bytes: int, *, max_active: int = 0, device: int = 0, threads: int = 0,
                  cells_per_thread: int = 0, stages: int = 0, arith: int = -1, max_jobs_per_launch: int = 0,
