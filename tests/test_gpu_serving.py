@@ -134,6 +134,26 @@ def test_jobs_of_three_cta_shapes_in_one_step(od, batch_steps):
         assert same(res, oracle.solve(*dims, seed, 1, it)), dims
 
 
+@pytest.mark.parametrize("job_streams", [0, 3])
+def test_jobs_with_uneven_cut_lists(od, job_streams):
+    # explicit cut lists (1-wide blocks, blocks of one plane, uneven edges),
+    # copied at submit: the caller's arrays are gone when the job is admitted
+    jobs = [((70, 45, 38), ([0, 13, 40, 70], [0, 24, 45], [0, 5, 6, 38]), 8, 71),
+            ((33, 31, 29), ([0, 1, 2, 32, 33], [0, 30, 31], [0, 14, 15, 29]), 13, 72),
+            ((96, 64, 48), ([0, 24, 25, 96], [0, 32, 64], [0, 1, 47, 48]), 5, 73)]
+    with od.Server(1 << 30, job_streams=job_streams) as srv:
+        ids = []
+        for dims, cuts, it, seed in jobs:
+            ids.append(srv.submit(*dims, it, cuts=tuple(list(c) for c in cuts), seed=seed))
+        got = []
+        for jid in ids:
+            assert srv.wait(jid, 120.0) == od._native.OD_JOB_DONE, srv.info(jid)
+            got.append(srv.fetch(jid))
+            srv.release(jid)
+    for res, (dims, cuts, it, seed) in zip(got, jobs):
+        assert same(res, oracle.solve(*dims, seed, 1, it)), (dims, cuts)
+
+
 @pytest.mark.parametrize("job_streams", [0, 4])
 def test_completion_queue_releases_as_jobs_end(od, job_streams):
     # a budget for two jobs and six submitted at once: the client takes each
