@@ -243,55 +243,93 @@ __global__ void k_read_cells(const double *const *addr, int64_t n, double *out) 
         out[i] = *addr[i];
 }
 
-// A11: interiors of parity p -> global x-fastest array.  One warp per
-// interior row (coalesced on both sides), one 32-bit division per row.
+// Rows a warp moves per pass of the gather and scatter: the loads of all of
+// them are in flight before the first store, so a warp keeps several memory
+// requests outstanding (one row at a time left both kernels latency-bound
+// on 32-cell rows).
+constexpr int kIoRows = 4;
+
+// A11: interiors of parity p -> global x-fastest array.  Each warp moves
+// kIoRows interior rows per pass (coalesced on both sides), one 32-bit
+// division per row.
 __global__ void k_gather(const ChareDev *ch, int nch, int p, int64_t nx, int64_t ny, double *g) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
-        const int nrow = C.by * C.bz;
+        const int nrow = C.by * C.bz, bx = C.bx;
         const int64_t plane = (int64_t)C.rows * C.pitch;
-        for (int rr = blockIdx.x * nwarps + warp; rr < nrow; rr += gridDim.x * nwarps) {
-            const int k = rr / C.by, j = rr - k * C.by;
-            const double *src = C.A[p] + (k + 1) * plane + (int64_t)(j + C.row0) * C.pitch + 1;
-            double *dst = g + ((C.z0 + k) * ny + C.y0 + j) * nx + C.x0;
-            for (int i = lane; i < C.bx; i += 32) dst[i] = src[i];
+        for (int r0 = (blockIdx.x * nwarps + warp) * kIoRows; r0 < nrow; r0 += gridDim.x * nwarps * kIoRows) {
+            const double *src[kIoRows];
+            double *dst[kIoRows];
+#pragma unroll
+            for (int u = 0; u < kIoRows; ++u) {
+                const int rr = r0 + u < nrow ? r0 + u : r0;  // past the end: repeat the first row
+                const int k = rr / C.by, j = rr - k * C.by;
+                src[u] = C.A[p] + (k + 1) * plane + (int64_t)(j + C.row0) * C.pitch + 1;
+                dst[u] = g + ((C.z0 + k) * ny + C.y0 + j) * nx + C.x0;
+            }
+            for (int i = lane; i < bx; i += 32) {
+                double v[kIoRows];
+#pragma unroll
+                for (int u = 0; u < kIoRows; ++u) v[u] = src[u][i];
+#pragma unroll
+                for (int u = 0; u < kIoRows; ++u) dst[u][i] = v[u];  // a repeated row stores the same value
+            }
         }
     }
 }
 
 // Import: global x-fastest interior -> interiors and internal ghost cells of
 // parity p (ghosts on the context's own boundary keep their values: the
-// Dirichlet shell, or a shard's imported faces).  One warp per padded row;
-// edge and corner ghosts (never read) are skipped.
+// Dirichlet shell, or a shard's imported faces).  Each warp moves kIoRows
+// padded rows per pass; edge and corner ghosts (never read) are skipped.
 // The largest positive finite value written goes into *vmax (its bit
 // pattern, atomic maximum: positive doubles order like their bit patterns),
-// which anchors the exact arithmetic's window (od_arith.cuh); one atomic per
-// warp.
+// which anchors the exact arithmetic's window (od_arith.cuh); at most one
+// atomic per warp.
 __global__ void k_scatter(const ChareDev *ch, int nch, int p, int64_t nx, int64_t ny, int64_t nz,
                           const double *g, unsigned long long *vmax) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     unsigned long long vm = 0;
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
-        const int nrow = C.rows * (C.bz + 2);
-        for (int rr = blockIdx.x * nwarps + warp; rr < nrow; rr += gridDim.x * nwarps) {
-            const int kp = rr / C.rows, rp = rr - kp * C.rows;
-            const int jp = rp + 1 - C.row0;  // padded y index (a 2D chare's single row is row 1)
-            const bool gy_ghost = jp == 0 || jp == C.by + 1, gz_ghost = kp == 0 || kp == C.bz + 1;
-            if (gy_ghost && gz_ghost) continue;
-            const int64_t gy = C.y0 + jp, gz = C.z0 + kp;
-            if (gy == 0 || gy == ny + 1 || gz == 0 || gz == nz + 1) continue;
-            double *dst = C.A[p] + (int64_t)rr * C.pitch;
-            const double *src = g + ((gz - 1) * ny + (gy - 1)) * nx - 1;
-            for (int cp = lane; cp < C.bx + 2; cp += 32) {
-                if ((gy_ghost || gz_ghost) && (cp == 0 || cp == C.bx + 1)) continue;
+        const int nrow = C.rows * (C.bz + 2), bx = C.bx;
+        for (int r0 = (blockIdx.x * nwarps + warp) * kIoRows; r0 < nrow; r0 += gridDim.x * nwarps * kIoRows) {
+            // per row: whether it is written at all, whether only its x
+            // ghosts are skipped (a y or z ghost row), and its two addresses
+            bool live[kIoRows], ghost[kIoRows];
+            double *dst[kIoRows];
+            const double *src[kIoRows];
+#pragma unroll
+            for (int u = 0; u < kIoRows; ++u) {
+                const int rr = r0 + u;
+                const int kp = rr / C.rows, rp = rr - kp * C.rows;
+                const int jp = rp + 1 - C.row0;  // padded y index (a 2D chare's single row is row 1)
+                const bool gy_ghost = jp == 0 || jp == C.by + 1, gz_ghost = kp == 0 || kp == C.bz + 1;
+                const int64_t gy = C.y0 + jp, gz = C.z0 + kp;
+                live[u] = rr < nrow && !(gy_ghost && gz_ghost) && gy != 0 && gy != ny + 1 && gz != 0 &&
+                          gz != nz + 1;
+                ghost[u] = gy_ghost || gz_ghost;
+                dst[u] = C.A[p] + (int64_t)rr * C.pitch;
+                src[u] = g + ((gz - 1) * ny + (gy - 1)) * nx - 1;
+            }
+            for (int cp = lane; cp < bx + 2; cp += 32) {
                 const int64_t gx = C.x0 + cp;
-                if (gx == 0 || gx == nx + 1) continue;
-                const double v = src[gx];
-                dst[cp] = v;
-                const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-                if (b < 0x7FF0000000000000ull && b > vm) vm = b;  // positive and finite
+                const bool xin = gx != 0 && gx != nx + 1, xedge = cp == 0 || cp == bx + 1;
+                bool take[kIoRows];
+                double v[kIoRows];
+#pragma unroll
+                for (int u = 0; u < kIoRows; ++u) {
+                    take[u] = live[u] && xin && !(ghost[u] && xedge);
+                    v[u] = take[u] ? src[u][gx] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kIoRows; ++u) {
+                    if (!take[u]) continue;
+                    dst[u][cp] = v[u];
+                    const unsigned long long b = (unsigned long long)__double_as_longlong(v[u]);
+                    if (b < 0x7FF0000000000000ull && b > vm) vm = b;  // positive and finite
+                }
             }
         }
     }
@@ -300,7 +338,9 @@ __global__ void k_scatter(const ChareDev *ch, int nch, int p, int64_t nx, int64_
         const unsigned long long w = __shfl_xor_sync(0xFFFFFFFFu, vm, o);
         vm = w > vm ? w : vm;
     }
-    if (lane == 0 && vm != 0 && vmax) atomicMax(vmax, vm);
+    // the word only grows: a warp whose maximum is not above it skips the
+    // atomic (a field within the initial bound [0, 1) then issues none)
+    if (lane == 0 && vm != 0 && vmax && vm > *(volatile unsigned long long *)vmax) atomicMax(vmax, vm);
 }
 
 // Arithmetic self-test: op 0 div6, 1 add (integer pipes); 2 division by 6,
