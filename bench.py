@@ -505,9 +505,11 @@ def run_ours(args):
 
     # end to end through the public API with pinned host buffers: each e2e
     # step is a whole solve of 100 iterations from the config's initial
-    # field: import it (H2D), iterate, export the result (D2H).  Two contexts
-    # run as a pipeline, as a serving loop would: one job's copies (copy
-    # engines) run under the other job's iterations.  A job's iterations
+    # field: import it (H2D), iterate, export the result (D2H).  Three
+    # contexts run as a pipeline, as a serving loop would: one job's copies
+    # (copy engines) run under another job's iterations, and the host waits
+    # only for the job three back, so a stall of the (shared) host or host
+    # link up to two jobs long leaves the device busy.  A job's iterations
     # start after the previous job's gather kernel (an event), so that short
     # kernel is not left queued behind a whole persistent launch.  Every job
     # computes u^100 of the same field, which the CPU baseline's oracle solve
@@ -516,14 +518,15 @@ def run_ours(args):
     if not args.no_e2e:
         import numpy as np
         n = plan["cells"]
+        depth = 3                          # contexts in the pipeline
         host_in = torch.empty(n, dtype=torch.float64, pin_memory=True)
-        host_out = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        outs = [torch.empty(n, dtype=torch.float64, pin_memory=True) for _ in range(depth)]
         iters_job = 100
         reps = 16                          # the pipeline's fill and drain amortised over 16 jobs
-        stream2 = torch.cuda.Stream(dev)
-        twin = make(args.path, stream=stream2.cuda_stream, **tune_kw)
-        twin.read(host_in.numpy())         # the initial field u^0
-        ctx, strm = (solver, twin), (stream, stream2)
+        strm = [stream] + [torch.cuda.Stream(dev) for _ in range(depth - 1)]
+        twins = [make(args.path, stream=st.cuda_stream, **tune_kw) for st in strm[1:]]
+        twins[0].read(host_in.numpy())     # the initial field u^0
+        ctx = [solver] + twins
         # the host link's bandwidth right now (the host is shared): one copy each way
         probe = torch.empty(min(n, 1 << 27), dtype=torch.float64, device=dev)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -531,55 +534,58 @@ def run_ours(args):
             ev[0].record(stream)
             probe.copy_(host_in[:probe.numel()], non_blocking=True)
             ev[1].record(stream)
-            host_out[:probe.numel()].copy_(probe, non_blocking=True)
+            outs[0][:probe.numel()].copy_(probe, non_blocking=True)
             ev[2].record(stream)
         ev[2].synchronize()
         link = (probe.numel() * 8 / (ev[0].elapsed_time(ev[1]) * 1e-3) / 1e9,
                 probe.numel() * 8 / (ev[1].elapsed_time(ev[2]) * 1e-3) / 1e9)
         del probe
         first = None
-        for c in ctx:                      # warm-up job on each context
+        for c, o in zip(ctx, outs):        # warm-up job on each context
             c.write_async(host_in)
             c.step(iters_job)
-            c.read_async(host_out)
+            c.read_async(o)
             c.sync()
             if first is None:
-                first = host_out.numpy().copy()
+                first = o.numpy().copy()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         ctx[0].write_async(host_in)
         ctx[0].step(iters_job)
         spans = []                         # each job's iterations, as the device ran them
-        marks = [t0]                       # host time as each job's result arrived
         for j in range(1, reps):
-            cur, prev = ctx[j % 2], ctx[(j - 1) % 2]
+            cur, prev = ctx[j % depth], ctx[(j - 1) % depth]
+            if j >= depth:
+                cur.sync()                 # this context's job j - depth: exported
             cur.write_async(host_in)
-            prev.read_async(host_out)
+            prev.read_async(outs[(j - 1) % depth])
             gathered = torch.cuda.Event()
-            gathered.record(strm[(j - 1) % 2])
-            strm[j % 2].wait_event(gathered)
+            gathered.record(strm[(j - 1) % depth])
+            strm[j % depth].wait_event(gathered)
             k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            k0.record(strm[j % 2])
+            k0.record(strm[j % depth])
             cur.step(iters_job)
-            k1.record(strm[j % 2])
+            k1.record(strm[j % depth])
             spans.append((k0, k1))
-            prev.sync()
-            marks.append(time.perf_counter())
-        ctx[(reps - 1) % 2].read_async(host_out)
-        ctx[(reps - 1) % 2].sync()
+        last = (reps - 1) % depth
+        ctx[last].read_async(outs[last])
+        for c in ctx:
+            c.sync()
         dt = time.perf_counter() - t0
-        e2e_last = host_out.numpy().copy()
+        e2e_last = outs[last].numpy().copy()
         same = bool(np.array_equal(e2e_last.view(np.uint64), first.view(np.uint64)))
-        twin.close()
+        for t in twins:
+            t.close()
         it_ms = sum(a.elapsed_time(b) for a, b in spans) / len(spans)
-        gaps = np.diff(marks) * 1e3
+        # the device's job intervals: from one job's end of iterations to the next one's
+        gaps = np.array([spans[q][1].elapsed_time(spans[q + 1][1]) for q in range(len(spans) - 1)])
         e2e = {"value": n * iters_job * reps * world / dt, "unit": UNIT,
                "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
-               "iters_per_step": iters_job, "jobs": reps, "results_identical": same,
+               "iters_per_step": iters_job, "jobs": reps, "results_identical": same, "pipeline_contexts": depth,
                "job_intervals_ms": [round(float(g), 2) for g in gaps],
                "iterations_ms": [round(a.elapsed_time(b), 2) for a, b in spans],
                "note": "e2e step = od_write_async(pinned host u^0) + od_step(100) + od_read_async(pinned host); "
-                       "two contexts pipelined, so one job's host copies overlap the other's iterations"}
+                       "three contexts pipelined, so one job's host copies overlap another's iterations"}
         e2e_flat = {"e2e_host_link_h2d_gbps": round(link[0], 1), "e2e_host_link_d2h_gbps": round(link[1], 1),
                     "e2e_iterations_ms_per_job": round(it_ms, 3), "e2e_wall_ms_per_job": round(dt / reps * 1e3, 3),
                     "e2e_job_interval_median_ms": round(float(np.median(gaps)), 3),
