@@ -1123,7 +1123,7 @@ od_status od_write(od_ctx *c, const double *src, int32_t src_is_device) {
         g = c->d_stage;
     }
     OD_CUDA(od::launch_scatter(c->d_ch, (int)p.ch.size(), par, p.nx, p.ny, p.nz, g, c->d_vmax, c->stream));
-    c->ghosts_current = true;  // the scatter writes every internal ghost cell too
+    c->ghosts_current = false;  // the scatter writes interiors only
     if (!src_is_device) OD_CUDA(cudaStreamSynchronize(c->stream));
     return OD_OK;
 }
@@ -1139,7 +1139,7 @@ od_status od_write_async(od_ctx *c, const double *src) {
     OD_CUDA(cudaMemcpyAsync(c->d_stage, src, (size_t)p.cells * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     OD_CUDA(od::launch_scatter(c->d_ch, (int)p.ch.size(), (int)(c->steps & 1), p.nx, p.ny, p.nz, c->d_stage,
                                c->d_vmax, c->stream));
-    c->ghosts_current = true;
+    c->ghosts_current = false;  // interiors only
     return OD_OK;
 }
 

@@ -27,7 +27,7 @@ struct od_ctx {
             *d_order = nullptr;
     uint64_t *d_vmax = nullptr;       // largest value of the field (bits), in the arena's queue block
     bool ghosts_current = true;       // internal ghost layers of the current parity hold the
-                                      // neighbours' faces (false after a fused step)
+                                      // neighbours' faces (false after a fused step or an import)
     std::vector<ChareDev> h_ch;       // host copy (device pointers)
     double *d_stage = nullptr;        // lazily allocated host-transfer staging
     // od_read_async: the device-to-host copy of the staging buffer runs on

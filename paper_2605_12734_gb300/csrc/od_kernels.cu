@@ -279,10 +279,12 @@ __global__ void k_gather(const ChareDev *ch, int nch, int p, int64_t nx, int64_t
     }
 }
 
-// Import: global x-fastest interior -> interiors and internal ghost cells of
-// parity p (ghosts on the context's own boundary keep their values: the
-// Dirichlet shell, or a shard's imported faces).  Each warp moves kIoRows
-// padded rows per pass; edge and corner ghosts (never read) are skipped.
+// Import: global x-fastest interior -> interiors of parity p, the mirror of
+// k_gather (kIoRows rows per warp pass).  Ghost layers are left alone: the
+// fused and persistent sweeps read their neighbours' faces from the
+// neighbours' arrays, and the per-chare flow refreshes its internal ghost
+// layers before its next step (od_write marks them stale); Dirichlet and
+// imported domain faces keep their values.
 // The largest positive finite value written goes into *vmax (its bit
 // pattern, atomic maximum: positive doubles order like their bit patterns),
 // which anchors the exact arithmetic's window (od_arith.cuh); at most one
@@ -293,46 +295,32 @@ __global__ void k_scatter(const ChareDev *ch, int nch, int p, int64_t nx, int64_
     unsigned long long vm = 0;
     for (int c = blockIdx.y; c < nch; c += gridDim.y) {
         const ChareDev &C = ch[c];
-        const int nrow = C.rows * (C.bz + 2), bx = C.bx;
+        const int nrow = C.by * C.bz, bx = C.bx;
+        const int64_t plane = (int64_t)C.rows * C.pitch;
         for (int r0 = (blockIdx.x * nwarps + warp) * kIoRows; r0 < nrow; r0 += gridDim.x * nwarps * kIoRows) {
-            // per row: whether it is written at all, whether only its x
-            // ghosts are skipped (a y or z ghost row), and its two addresses
-            bool live[kIoRows], ghost[kIoRows];
-            double *dst[kIoRows];
             const double *src[kIoRows];
+            double *dst[kIoRows];
 #pragma unroll
             for (int u = 0; u < kIoRows; ++u) {
-                const int rr = r0 + u;
-                const int kp = rr / C.rows, rp = rr - kp * C.rows;
-                const int jp = rp + 1 - C.row0;  // padded y index (a 2D chare's single row is row 1)
-                const bool gy_ghost = jp == 0 || jp == C.by + 1, gz_ghost = kp == 0 || kp == C.bz + 1;
-                const int64_t gy = C.y0 + jp, gz = C.z0 + kp;
-                live[u] = rr < nrow && !(gy_ghost && gz_ghost) && gy != 0 && gy != ny + 1 && gz != 0 &&
-                          gz != nz + 1;
-                ghost[u] = gy_ghost || gz_ghost;
-                dst[u] = C.A[p] + (int64_t)rr * C.pitch;
-                src[u] = g + ((gz - 1) * ny + (gy - 1)) * nx - 1;
+                const int rr = r0 + u < nrow ? r0 + u : r0;  // past the end: repeat the first row
+                const int k = rr / C.by, j = rr - k * C.by;
+                dst[u] = C.A[p] + (k + 1) * plane + (int64_t)(j + C.row0) * C.pitch + 1;
+                src[u] = g + ((C.z0 + k) * ny + C.y0 + j) * nx + C.x0;
             }
-            for (int cp = lane; cp < bx + 2; cp += 32) {
-                const int64_t gx = C.x0 + cp;
-                const bool xin = gx != 0 && gx != nx + 1, xedge = cp == 0 || cp == bx + 1;
-                bool take[kIoRows];
+            for (int i = lane; i < bx; i += 32) {
                 double v[kIoRows];
 #pragma unroll
-                for (int u = 0; u < kIoRows; ++u) {
-                    take[u] = live[u] && xin && !(ghost[u] && xedge);
-                    v[u] = take[u] ? src[u][gx] : 0.0;
-                }
+                for (int u = 0; u < kIoRows; ++u) v[u] = src[u][i];
 #pragma unroll
                 for (int u = 0; u < kIoRows; ++u) {
-                    if (!take[u]) continue;
-                    dst[u][cp] = v[u];
+                    dst[u][i] = v[u];  // a repeated row stores the same value
                     const unsigned long long b = (unsigned long long)__double_as_longlong(v[u]);
                     if (b < 0x7FF0000000000000ull && b > vm) vm = b;  // positive and finite
                 }
             }
         }
     }
+    (void)nz;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long w = __shfl_xor_sync(0xFFFFFFFFu, vm, o);
