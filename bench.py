@@ -179,8 +179,8 @@ def profiled_kernel(args, plan):
 
 
 # bumped whenever a tile kernel changes, so stale profiler counters are not reused
-KERNEL_REV = 15     # 3D 7-point
-KERNEL_REV_2D = 15  # 2D 5-point
+KERNEL_REV = 16     # 3D 7-point
+KERNEL_REV_2D = 16  # 2D 5-point
 
 
 def combine_ranks(ms: float, updates: float, world: int, device: str):

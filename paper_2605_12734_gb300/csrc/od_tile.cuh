@@ -133,7 +133,10 @@ __device__ __forceinline__ void record_err(ErrDev *e, int code, int tile, int st
 // integer routines' domain.  Kept out of line so the compiler cannot merge it
 // with (or speculate it beside) the fast form in the hot loop.
 static __device__ __noinline__ double update_slow(double W, double E, double S, double N, double D, double U) {
-    return jacobi_update_ieee<false>(W, E, S, N, D, U);
+    // IEEE adds, the division by 6 on the integer pipes (exact for every
+    // input): the FP64 pipe's division sequence made each such cell cost
+    // more than twice as much on that pipe
+    return jacobi_update_ieee<true>(W, E, S, N, D, U);
 }
 
 // Which thread refills a ring slot: lane 0 of a different warp each plane
@@ -456,7 +459,7 @@ __device__ __forceinline__ bool run_tile(const KArgs &a, int tile_id, int sp, Ri
 
 // IEEE form of the 2D update (out of line, as update_slow).
 static __device__ __noinline__ double update2d_slow(double W, double E, double S, double N) {
-    return jacobi2d_update_ieee<false>(W, E, S, N);
+    return jacobi2d_update_ieee<true>(W, E, S, N);  // the division by 4 as an exponent step where exact
 }
 
 // The 2D 5-point sweep (the paper's Jacobi2D, Sec. V) on the internal grid
