@@ -457,11 +457,13 @@ OD_API od_status od_bench_launch_rate(int32_t device, int32_t host_threads, int3
 
 /* ------------------------------------------------------------------ serving
  *
- * A server admits independent solves as they arrive, keeps their state
- * resident in one device pool of hbm_budget_bytes and advances every running
- * job by batch_steps iterations per batched launch (continuous batching:
- * jobs that arrive while others run join the next launch, finished jobs drop
- * out).  Admission is first come, first served, while a slot is free
+ * A server admits independent solves as they arrive and keeps their state
+ * resident in one device pool of hbm_budget_bytes.  By default (job_streams
+ * > 0) each admitted job's whole run is one persistent launch on its own
+ * stream and the jobs' kernels share the SMs; with job_streams = 0 it
+ * advances every running job by batch_steps iterations per batched launch
+ * (continuous batching: jobs that arrive while others run join the next
+ * launch, finished jobs drop out).  Admission is first come, first served, while a slot is free
  * (max_active, 0 = no limit) and the pool has room for the job's arena.  A
  * worker thread inside the server drives the device; every call below is
  * thread-safe.  Each job's result is bit-identical to the same job solved
@@ -478,13 +480,13 @@ typedef struct od_server od_server;
 typedef struct od_server_config {
     uint64_t hbm_budget_bytes;   /* device memory for all resident jobs */
     int32_t max_active;          /* jobs resident at once (0 = no limit) */
-    int32_t max_jobs_per_launch; /* batch table size (0 = 256) */
+    int32_t max_jobs_per_launch; /* batched mode: batch table size (0 = 256) */
     int32_t device;
     int32_t threads, cells_per_thread, stages; /* CTA shape for every job; threads and
                                     cells_per_thread both 0: the planner picks
-                                    each job's shape (as od_config) and each
-                                    step runs one batched launch per shape in
-                                    use; stages 0 = 4 */
+                                    each job's shape (as od_config; batched mode
+                                    runs one launch per shape in use); stages
+                                    0 = 4 */
     int32_t arith;               /* as od_config.arith (-1 = 12) */
     void *pool;                  /* caller device memory of hbm_budget_bytes, 256-byte
                                     aligned, or NULL: the server allocates it once */
